@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the multi-hypothesis collision-criticality hot path on GB300.
+
+One step = the whole hot path on one 11-object intersection (7 cars x 441 hypotheses + 4 pedestrians
+x 121, 30 steps of 0.1 s, every object pair: 1.70e8 pose-pair tests): trajectory generation, collision
+recognition and risk assessment, all through the C ABI, inputs resident in HBM.  The L2 cache is
+flushed (256 MiB write) before every timed step, outside the step's CUDA events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mhc|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one process per GPU) every rank runs its own
+scenario replica (independent placements, weak scaling) and the time is the maximum over ranks.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pose-pair tests/s"
+UNIT = "tests/s"
+PROFILE_NOTE = os.path.join(ROOT, "profiles", "collide_kernel_intersection11.md")
+COLLIDE_SRC = os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", "collide.cu")
+# algorithmic FP32-pipe lane instructions per unit of collision work (roofline section)
+OPS_PER_BROAD_TEST = 3.0      # 2 FFMA (expanded squared distance) + 1 compare
+OPS_PER_NARROW_TEST = 30.0    # separating-axis test of two rectangles, worst shape combination
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="mhc", choices=["mhc", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(rank: int = 0):
+    from paper_2005_06773_gb300 import scenarios as S
+    return S.intersection11(2 + rank)
+
+
+def config_of(sc, rank0_seed=2):
+    return {
+        "workload": "intersection11: 7 cars (4.5x1.8 m, 441 hypotheses = 21 accel x 21 steer) + 4 pedestrians "
+                    "(r 0.4 m, 121 = 11 speeds x 11 headings), 30 steps of 0.1 s (5 sub-steps), all 55 object pairs",
+        "seed": rank0_seed,
+        "tests_per_step": sc.n_tests(),
+        "trajectory_pairs_per_step": sc.n_traj_pairs(),
+        "hypotheses": sum(sc.hyp_counts),
+        "l2": "flushed before every timed step (256 MiB write, outside the step's events)",
+    }
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_from_profile():
+    """DRAM bytes per collide launch from the committed ncu summary, if it was taken on this source."""
+    try:
+        text = open(PROFILE_NOTE).read()
+        sha = hashlib.sha256(open(COLLIDE_SRC, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m_sha = re.search(r"collide_source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) around the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for r in csv.reader(f):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+        os.unlink(self.tmp.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = {5: "hw_slowdown", 6: "hw_thermal_slowdown", 7: "sw_thermal_slowdown", 8: "sw_power_cap"}
+        for r in rows:
+            for col, name in names.items():
+                if r[col].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if re.match(r"^[0-9.]+$", r[3])), default=None)}
+
+
+def pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    return v[min(len(v) - 1, int(math.ceil(q / 100.0 * len(v))) - 1)]
+
+
+def cpu_baseline(sc, budget_s: float):
+    """The FP64 oracle, as it stands, on whole passes of the same scene (single thread)."""
+    from oracle import oracle
+    oracle.build()
+    passes, t0 = 0, time.perf_counter()
+    while True:
+        out = oracle.run(sc)
+        passes += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    assert out["table"].size == sc.n_traj_pairs()
+    return {"value": passes * sc.n_tests() / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{passes} full pass(es) of the 11-object scene (generate + table + risk, "
+                      f"{sc.n_tests():.3e} tests each) in {dt:.1f} s on 1 host thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, each step a bounded random sample of the
+    scene's trajectory pairs (plus the full trajectory generation)."""
+    import numpy as np
+    from oracle import oracle
+    from paper_2005_06773_gb300 import scenarios as S
+    oracle.build()
+    sc = workload(0)
+    off = oracle.traj_offsets(sc)
+    pairs = oracle.pair_list(sc)
+    h = np.diff(off)
+    sizes = np.array([h[a] * h[b] for a, b in pairs], dtype=np.float64)
+    rng = np.random.default_rng(12345)
+
+    def draw(n):
+        q = rng.choice(len(pairs), size=n, p=sizes / sizes.sum())
+        pa = np.array([pairs[x][0] for x in q]); pb = np.array([pairs[x][1] for x in q])
+        i = (rng.random(n) * h[pa]).astype(np.int64); j = (rng.random(n) * h[pb]).astype(np.int64)
+        return pa, off[pa] + i, pb, off[pb] + j
+
+    poses = oracle.generate(sc)
+    t0 = time.perf_counter()
+    oracle.first_steps(sc, poses, *draw(20000))
+    rate = 20000 / max(time.perf_counter() - t0, 1e-6)          # trajectory pairs per second
+    per_step = max(0.05, 120.0 / max(1, args.steps + args.warmup))
+    n = int(max(2000, min(rate * per_step, sc.n_traj_pairs())))
+    samples = [draw(n) for _ in range(args.steps + args.warmup)]
+    times = []
+    for s in range(args.steps + args.warmup):
+        t = time.perf_counter()
+        p = oracle.generate(sc)
+        oracle.first_steps(sc, p, *samples[s])
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    tests = n * sc.n_steps
+    total = sum(times)
+    value = tests * len(times) / total
+    sample = (f"each step: full trajectory generation + first-collision steps of {n} random trajectory pairs "
+              f"({tests:.3e} pose tests) of the 11-object scene, 1 host thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(sc),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_mhc(args):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2005_06773_gb300 import mhc
+
+    sc = workload(rank)
+    cs = mhc.as_c(sc)
+    lay = mhc.layout(cs)
+    ctx = mhc.Context(local, 512 << 20)
+    poses = mhc.alloc_poses(sc, dev)
+    table = torch.empty(lay["n_entries"], dtype=torch.int16, device=dev)
+    risk = mhc.alloc_risk(cs, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        mhc.generate(ctx, cs, poses, stream=stream)
+        mhc.detect(ctx, cs, poses, table, stream=stream)
+        mhc.assess(ctx, cs, table, out=risk, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.counters(reset=True)
+    ctx.profile_read(reset=True)
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        step()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    prof = ctx.profile_read(reset=True)
+    executed, narrow = ctx.counters(reset=True)
+    t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    tests_all = sc.n_tests() * args.steps * world
+    value = tests_all / t_max
+
+    # end to end through mhc_run: host scenario in, host (pinned) risk out, copies inside the timed region
+    host_out = mhc.alloc_risk(cs, device="cpu", pin=True)
+    e2e_ctx = mhc.Context(local, max(lay["run_bytes"] + (64 << 20), 256 << 20))
+    for _ in range(3):
+        mhc.run(e2e_ctx, cs, out=host_out, stream=stream)
+    e2e_ms = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mhc.run(e2e_ctx, cs, out=host_out, stream=stream)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h2d, d2h = e2e_ctx.transfer_bytes()
+    e2e_ctx.close()
+    te = torch.tensor([sum(e2e_ms) / 1e3], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = sc.n_tests() * args.e2e_steps * world / float(te.item())
+
+    coll_ms, coll_n = prof["collide"]
+    avg_coll_s = coll_ms / 1e3 / max(coll_n, 1)
+    ops_per_launch = (OPS_PER_BROAD_TEST * executed + OPS_PER_NARROW_TEST * narrow) / max(coll_n, 1)
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    achieved = ops_per_launch / avg_coll_s / 1e12
+    traffic = traffic_from_profile()
+    launches = sum(n for _, n in prof.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(sc),
+        "latency_ms": {"scene_device_p50": pct(step_ms, 50), "scene_device_p99": pct(step_ms, 99),
+                       "scene_e2e_p50": pct(e2e_ms, 50), "scene_e2e_p99": pct(e2e_ms, 99)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "mhc_run: host scenario -> device -> host risk outputs (pinned), stream synchronised"},
+        "gpu_launches": launches,
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "collision_work": {"nominal_tests_per_launch": sc.n_tests(), "executed_tests_per_launch": executed / max(coll_n, 1),
+                           "narrow_tests_per_launch": narrow / max(coll_n, 1),
+                           "nominal_tests_per_s_collide_only": sc.n_tests() / avg_coll_s},
+        "roofline": {"bound": "alu", "kernel": "collide_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "T FP32-lane-instr/s", "frac": achieved / peak, "traffic": traffic,
+                     "avg_launch_ms": 1e3 * avg_coll_s, "ops_per_launch": ops_per_launch,
+                     "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
+                                    "(sm_max_mhz of MEASURED_PEAKS.json)"},
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args)
+        return
+    run_mhc(args)
+
+
+if __name__ == "__main__":
+    main()

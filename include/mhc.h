@@ -1,0 +1,243 @@
+/*
+ * mhc.h -- C ABI of the GB300 (sm_103a) multi-hypothesis collision-criticality library.
+ *
+ * The library implements the data-parallel hot path of "Parallel Multi-Hypothesis Algorithm for
+ * Criticality Estimation in Traffic and Collision Avoidance" (arXiv 2005.06773):
+ *   trajectory generation (Section IV-B)  ->  collision recognition (Section IV-C)  ->  risk (Section IV-D).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an mhc_status (0 = MHC_OK, negative = error); nothing crosses the ABI as an
+ *     exception.  mhc_status_string() names a code; mhc_last_error() gives a one-line reason for the
+ *     most recent failure on the calling thread.
+ *   - "host" pointers are read during the call only; the library copies what it needs.  "device"
+ *     pointers are global-memory pointers of the context's device; they are owned by the caller, must
+ *     stay valid until the work enqueued on `stream` has completed, and must not overlap each other.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is enqueued
+ *     asynchronously; the caller synchronises.  Calls on one context may use different streams: the
+ *     library orders its internal scratch memory between them on the device.
+ *   - One host thread at a time may call into a given context (except mhc_poll, see below).
+ *   - Invalid arguments return MHC_E_INVALID before any work is enqueued; CUDA failures return MHC_E_CUDA.
+ */
+#ifndef MHC_H
+#define MHC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MHC_OK = 0,
+    MHC_PENDING = 1,        /* mhc_poll: the request has not finished yet */
+    MHC_E_INVALID = -1,     /* malformed scenario, sizes out of range, bad weights */
+    MHC_E_NOMEM = -2,       /* the context's arena or a host allocation is too small */
+    MHC_E_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    MHC_E_TIMEOUT = -4,     /* a bounded device-side wait gave up / a request missed its deadline */
+    MHC_E_BUSY = -5,        /* mhc_submit: queue full */
+    MHC_E_NOTFOUND = -6     /* unknown ticket */
+} mhc_status;
+
+enum { MHC_VEHICLE = 0, MHC_PEDESTRIAN = 1 };     /* object kinds: rectangle / disc */
+enum { MHC_ALL_PAIRS = 0, MHC_EGO_ONLY = 1 };     /* which object pairs are tested */
+enum { MHC_MODEL_OT = 0, MHC_MODEL_KIN = 1 };     /* vehicle motion model */
+#define MHC_PED_ACCEL_GRID 1                       /* object flag: pedestrian grid_a holds accelerations */
+#define MHC_MAX_STEPS 32767                        /* first-collision steps are stored as int16 */
+#define MHC_MAX_OBJECTS 4096
+
+/*
+ * One traffic object and the control grid of its hypotheses (Section IV-B; a hypothesis is one
+ * acceleration profile combined with one path, Section III).
+ *   kind MHC_VEHICLE: rectangle length x width centred on the pose point, body axis along psi.
+ *       Hypothesis h = i_a * n_b + i_b drives with constant acceleration grid_a[i_a] (m/s^2) and constant
+ *       front steering angle grid_b[i_b] (rad) through the one-track model (Eq. onetrack) integrated
+ *       by Eq. (EulerVelocity); model MHC_MODEL_KIN uses the kinematic bicycle instead.
+ *   kind MHC_PEDESTRIAN: disc of `radius` moving by Eq. (pedestrianmotion) with constant heading
+ *       psi0 + grid_b[i_b]; grid_a holds initial speeds (m/s) or, with flag MHC_PED_ACCEL_GRID,
+ *       accelerations from initial speed v0, the speed then limited to [0, v_max] (v_max <= 0: no cap).
+ *   veh_params: host pointer to {m, I_z, l_f, l_r, c_af, c_ar} (kg, kg m^2, m, m, N/rad, N/rad), or NULL
+ *       for {1500, 2500, 1.2, 1.5, 80000, 80000}.  grid_a / grid_b are host pointers.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t flags;
+    float length, width, radius;
+    float x0, y0, psi0, v0;
+    float v_max;
+    int32_t n_a, n_b;
+    const float *grid_a;
+    const float *grid_b;
+    const float *veh_params;
+} mhc_object;
+
+/*
+ * A scenario: objects, horizon and pairing.  tau is the output time step (s); each step is integrated
+ * in `substeps` equal sub-steps; output step k (0 <= k < n_steps) is the pose at time (k + 1) tau.
+ * pair_mode MHC_ALL_PAIRS tests every object pair (a, b), a < b; MHC_EGO_ONLY tests (ego, b) for every
+ * b != ego (the paper's choice, Section IV-C.1).  `ego` is the EGO object for the risk measures.
+ */
+typedef struct {
+    int32_t n_objects;
+    const mhc_object *objects;    /* host */
+    float tau;
+    int32_t n_steps;
+    int32_t substeps;
+    int32_t pair_mode;
+    int32_t ego;
+    int32_t model;
+} mhc_scenario;
+
+/*
+ * Device pose planes (FP32): x, y (m) and c = cos(psi), s = sin(psi) of the body axis.  Each plane holds
+ * n_steps * n_traj values laid out [object][step][hypothesis]: the pose of hypothesis i of object a at
+ * step k is at index n_steps * traj_off[a] + k * h_a + i, where traj_off is the prefix sum of the
+ * objects' hypothesis counts h_a = n_a * n_b (Eq. threads:traj counts them).
+ */
+typedef struct {
+    float *x, *y, *c, *s;
+} mhc_poses;
+
+/*
+ * Risk outputs (Section IV-D).  For mhc_assess_risk they are device pointers, for mhc_run host pointers.
+ * Any pointer may be NULL to skip that output.  n_pairs / h_e / N / n_objects as in mhc_layout.
+ *   per object pair p (table order):
+ *     count[p]   int64  number of colliding trajectory combinations
+ *     count_k    int64  [n_pairs][N] of them first colliding at step k
+ *     P[p]       double sum over colliding combinations of p_a[i] p_b[j]  (Eq. totalCrashProb per pair)
+ *     H          double [n_pairs][N] the same split by first-collision step
+ *   per EGO hypothesis i (h_e of them):
+ *     naive[i]   double sum over colliding (CO b, j) of p_b[j]
+ *     cond[i]    double chronologically scaled collision probability (Eq. p21): the colliding entries
+ *                (b, j, k) in ascending (k, b, j) order each contribute S p_b[j] with S the product of
+ *                (1 - p) over the earlier ones
+ *     indep[i]   double 1 - prod_b (1 - sum_j [collide] p_b[j])  (COs independent)
+ *     hits[i]    int32  number of colliding (b, j)
+ *   attr_obj     double [n_objects] sum_i p_e[i] * (share of cond[i] due to object b)
+ *   attr_step    double [N] the same per step
+ *   scalars      double [4]: p_cra (Eq. totalCrashProb), p_cra_cond = sum_i p_e[i] cond[i],
+ *                            p_cra_indep = sum_i p_e[i] indep[i], 0
+ *   escape       int32 [h_e] collision-free EGO hypotheses, most probable first, ties by index (Section VI-A)
+ *   n_escape     int32 [1] their number
+ */
+typedef struct {
+    int64_t *count;
+    int64_t *count_k;
+    double *P;
+    double *H;
+    double *naive;
+    double *cond;
+    double *indep;
+    int32_t *hits;
+    double *attr_obj;
+    double *attr_step;
+    double *scalars;
+    int32_t *escape;
+    int32_t *n_escape;
+} mhc_risk;
+
+typedef struct mhc_ctx mhc_ctx;
+
+/* Human-readable name of a status code (static string). */
+const char *mhc_status_string(int status);
+/* One-line reason for the last error returned on the calling thread ("" if none). */
+const char *mhc_last_error(void);
+/* Library version string. */
+const char *mhc_version(void);
+
+/*
+ * Create a context on CUDA device `device`.  `arena` is a device buffer of `arena_bytes` bytes owned by the
+ * caller (e.g. a framework allocation) that the library sub-allocates scratch from; with arena == NULL the
+ * library allocates `arena_bytes` itself with cudaMalloc and frees it in mhc_destroy.
+ * Errors: MHC_E_INVALID (bad device, arena_bytes < 1 MiB), MHC_E_CUDA, MHC_E_NOMEM.
+ */
+int mhc_create(mhc_ctx **out, int device, void *arena, size_t arena_bytes);
+/* Wait for the context's outstanding work and release it (and the arena if the library allocated it). */
+void mhc_destroy(mhc_ctx *ctx);
+
+/* Context options (mhc_set_option).
+ *   MHC_OPT_CULL  1 (default): the collision kernel skips whole steps of a 64 x 64 hypothesis tile when the
+ *                 bounding boxes of the two tiles' pose centres, grown by both circumradii, do not meet.
+ *                 The table is identical either way; 0 tests every step (used to check that). */
+#define MHC_OPT_CULL 1
+int mhc_set_option(mhc_ctx *ctx, int option, long long value);
+
+/* Work counters of the collision kernel since the last reset, summed over calls on this context:
+   out[0] = pose-pair broad-phase tests executed (after culling, 64 x 64 per tile step), out[1] = exact
+   narrow-phase tests.  Synchronises `stream`; reset != 0 zeroes them afterwards. */
+int mhc_collision_counters(mhc_ctx *ctx, uint64_t out[2], int reset, void *stream);
+
+/* Kernel timing (mhc_set_option(ctx, MHC_OPT_PROFILE, 1)): the library records a CUDA event pair on the
+   launching stream around every kernel it launches.  mhc_profile_read synchronises those events and
+   returns, per kernel class (MHC_K_GENERATE, MHC_K_BOUNDS, MHC_K_COLLIDE, MHC_K_RISK: the risk chain of
+   four kernels counts as one class with four launches), the summed milliseconds and the launch counts
+   since the last reset; reset != 0 clears them.  Disabled by default (no events recorded). */
+#define MHC_OPT_PROFILE 2
+enum { MHC_K_GENERATE = 0, MHC_K_BOUNDS = 1, MHC_K_COLLIDE = 2, MHC_K_RISK = 3, MHC_K_COUNT = 4 };
+int mhc_profile_read(mhc_ctx *ctx, double ms[4], int64_t launches[4], int reset);
+
+/* Bytes the most recent call on this context copied host->device (descriptors, weights) and
+   device->host (mhc_run outputs). */
+int mhc_transfer_bytes(mhc_ctx *ctx, int64_t *h2d, int64_t *d2h);
+
+/*
+ * Sizes of a scenario's buffers (host only, no GPU work).  Any output pointer may be NULL.
+ *   n_traj     total hypotheses sum_a h_a (Eq. threads:traj); each pose plane holds n_steps * n_traj floats
+ *   n_pairs    object pairs tested
+ *   n_entries  trajectory combinations sum_p h_a h_b (Eq. threads:coll); the table holds that many int16
+ *   h_ego      hypotheses of the EGO object
+ *   scratch    arena bytes a call on this scenario needs (mhc_run needs poses + table on top, reported
+ *              by mhc_run_bytes)
+ * Errors: MHC_E_INVALID with the reason in mhc_last_error().
+ */
+int mhc_layout(const mhc_scenario *scen, int64_t *n_traj, int32_t *n_pairs, int64_t *n_entries,
+               int32_t *h_ego, size_t *scratch);
+
+/* Pair list in table order: pair_a[n_pairs], pair_b[n_pairs] object indices and pair_off[n_pairs + 1]
+   int64 offsets of each pair's h_a x h_b block (row i = hypothesis of a, column j = hypothesis of b). */
+int mhc_pair_table(const mhc_scenario *scen, int32_t *pair_a, int32_t *pair_b, int64_t *pair_off);
+
+/*
+ * Trajectory generation (Section IV-B, Eqs. onetrack, EulerVelocity, pedestrianmotion): one thread per
+ * hypothesis integrates its n_steps * substeps sub-steps in order and writes the FP32 pose planes `out`
+ * (device, layout above).  Errors: MHC_E_INVALID, MHC_E_NOMEM (arena), MHC_E_CUDA.
+ */
+int mhc_generate_trajectories(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *out, void *stream);
+
+/*
+ * Collision recognition (Section IV-C): for every listed object pair (a, b) and every hypothesis pair
+ * (i, j) writes table[pair_off[p] + i * h_b + j] = the first step k at which the closed shapes of a and b
+ * overlap (touching counts), or -1 if they never do within the horizon.  `poses` is the device output of
+ * mhc_generate_trajectories (or any poses in that layout); `table` is a device int16 buffer of n_entries.
+ * Errors: MHC_E_INVALID, MHC_E_NOMEM (arena), MHC_E_CUDA.
+ */
+int mhc_detect_collisions(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses, int16_t *table,
+                          void *stream);
+
+/*
+ * Risk assessment (Section IV-D) from a device first-collision table.  traj_weights: host array of
+ * n_objects host pointers to each object's h_a non-negative FP32 weights, L1-normalised per object into
+ * occurrence probabilities (Section IV-D.1); traj_weights == NULL or a NULL entry means uniform.
+ * Outputs (mhc_risk) are device pointers.  Errors: MHC_E_INVALID (negative weights or a zero sum),
+ * MHC_E_NOMEM (arena), MHC_E_CUDA.
+ */
+int mhc_assess_risk(mhc_ctx *ctx, const mhc_scenario *scen, const int16_t *table,
+                    const float *const *traj_weights, const mhc_risk *out, void *stream);
+
+/* Arena bytes mhc_run needs for this scenario (poses + table + scratch). */
+int mhc_run_bytes(const mhc_scenario *scen, size_t *bytes);
+
+/*
+ * The whole method for one scenario from host inputs to host outputs: uploads the scenario, runs
+ * generation, collision recognition and risk in the context's arena, copies the risk outputs (host
+ * pointers in `out`) back and synchronises `stream`.  Poses and table live in the arena and are
+ * overwritten by the next call.  Errors as above.
+ */
+int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, const mhc_risk *out,
+            void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHC_H */

@@ -360,6 +360,24 @@ int orc_table(int n_obj, const int *kind, const double *length, const double *wi
     return 0;
 }
 
+/* First-collision step of selected trajectory pairs (same definition as orc_table):
+   out[q] for trajectories ta[q] (object oa[q]) and tb[q] (object ob[q]). */
+int orc_first(const int *kind, const double *length, const double *width, const double *radius, int n_steps,
+              const double *px, const double *py, const double *pc, const double *ps,
+              long n_q, const int *oa, const long *ta, const int *ob, const long *tb, int16_t *out) {
+    for (long q = 0; q < n_q; ++q) {
+        int a = oa[q], b = ob[q], first = -1;
+        for (int k = 0; k < n_steps; ++k) {
+            long ia = ta[q] * n_steps + k, ib = tb[q] * n_steps + k;
+            shape sa = make_shape(kind[a], length[a], width[a], radius[a], px[ia], py[ia], pc[ia], ps[ia]);
+            shape sb = make_shape(kind[b], length[b], width[b], radius[b], px[ib], py[ib], pc[ib], ps[ib]);
+            if (shape_overlap(&sa, &sb)) { first = k; break; }
+        }
+        out[q] = (int16_t)first;
+    }
+    return 0;
+}
+
 /* Per-step signed margins of selected trajectory pairs (for borderline accounting).
    For q < n_q: margins[q * n_steps + k] of trajectories ta[q], tb[q] (objects oa[q], ob[q]). */
 int orc_margins(const int *kind, const double *length, const double *width, const double *radius, int n_steps,

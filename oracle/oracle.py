@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-D_DEFAULT_SOURCE", "-shared", "-fPIC",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -159,6 +159,20 @@ def margins(sc, poses, oa, ta, ob_, tb) -> np.ndarray:
     L.orc_margins(_p(ob["kind"], _ip), _p(ob["length"], _dp), _p(ob["width"], _dp), _p(ob["radius"], _dp),
                   ctypes.c_int(N), _p(px, _dp), _p(py, _dp), _p(pc, _dp), _p(ps, _dp),
                   ctypes.c_long(oa.size), _p(oa, _ip), _p(ta, _lp), _p(ob_, _ip), _p(tb, _lp), _p(out, _dp))
+    return out
+
+
+def first_steps(sc, poses, oa, ta, ob_, tb) -> np.ndarray:
+    """First-collision step (or -1) of the listed trajectory pairs, same definition as table()."""
+    L = lib()
+    ob = _objects(sc)
+    oa, ob_ = _i32(oa), _i32(ob_)
+    ta, tb = _i64(ta), _i64(tb)
+    out = np.empty(oa.size, np.int16)
+    px, py, pc, ps = (_f64(poses[k]) for k in ("x", "y", "c", "s"))
+    L.orc_first(_p(ob["kind"], _ip), _p(ob["length"], _dp), _p(ob["width"], _dp), _p(ob["radius"], _dp),
+                ctypes.c_int(int(sc.n_steps)), _p(px, _dp), _p(py, _dp), _p(pc, _dp), _p(ps, _dp),
+                ctypes.c_long(oa.size), _p(oa, _ip), _p(ta, _lp), _p(ob_, _ip), _p(tb, _lp), _p(out, _sp))
     return out
 
 

@@ -1,0 +1,677 @@
+// api.cu -- host runtime behind the C ABI of mhc.h: scenario validation and layout, the context arena,
+// descriptor upload through a ring of pinned staging buffers, and the launch sequence of each entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mhc.h"
+#include "mhc_internal.cuh"
+
+using namespace mhc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &why) {
+    g_err = why;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(MHC_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MHC_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr size_t kReserved = 4096;    // persistent words at the start of the arena (counters)
+constexpr int kSlots = 4;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+bool finite(float v) { return std::isfinite(v); }
+
+// Host-side layout of a scenario: every descriptor the kernels read.
+struct Layout {
+    int n_obj = 0, N = 0, K = 0, model = 0, pair_mode = 0, ego = 0;
+    float tau = 0.f;
+    std::vector<ObjDesc> objs;
+    std::vector<PairDesc> pairs;
+    std::vector<float> grids;
+    std::vector<int> warp_obj, warp_first;
+    long long n_traj = 0, n_entries = 0, n_tiles = 0;
+    int n_tiles32 = 0, h_e = 0;
+};
+
+int build_layout(const mhc_scenario *sc, Layout &L) {
+    if (!sc) return fail(MHC_E_INVALID, "scenario is NULL");
+    if (sc->n_objects < 1 || sc->n_objects > MHC_MAX_OBJECTS || !sc->objects)
+        return fail(MHC_E_INVALID, "n_objects must be in [1, 4096] with a non-NULL objects array");
+    if (sc->n_steps < 1 || sc->n_steps > MHC_MAX_STEPS) return fail(MHC_E_INVALID, "n_steps must be in [1, 32767]");
+    if (sc->substeps < 1 || (long long)sc->n_steps * sc->substeps > (1LL << 31))
+        return fail(MHC_E_INVALID, "substeps must be >= 1 with n_steps * substeps <= 2^31");
+    if (!(sc->tau > 0.f) || !finite(sc->tau)) return fail(MHC_E_INVALID, "tau must be positive and finite");
+    if (sc->pair_mode != MHC_ALL_PAIRS && sc->pair_mode != MHC_EGO_ONLY) return fail(MHC_E_INVALID, "bad pair_mode");
+    if (sc->ego < 0 || sc->ego >= sc->n_objects) return fail(MHC_E_INVALID, "ego out of range");
+    if (sc->model != MHC_MODEL_OT && sc->model != MHC_MODEL_KIN) return fail(MHC_E_INVALID, "bad model");
+    if (sc->pair_mode == MHC_EGO_ONLY && sc->n_objects < 2) return fail(MHC_E_INVALID, "EGO_ONLY needs 2 objects");
+    L.n_obj = sc->n_objects; L.N = sc->n_steps; L.K = sc->substeps; L.model = sc->model;
+    L.pair_mode = sc->pair_mode; L.ego = sc->ego; L.tau = sc->tau;
+    L.objs.resize(L.n_obj);
+    static const float kDefault[6] = {1500.f, 2500.f, 1.2f, 1.5f, 80000.f, 80000.f};
+    long long traj = 0;
+    int tiles32 = 0;
+    for (int o = 0; o < L.n_obj; ++o) {
+        const mhc_object &src = sc->objects[o];
+        ObjDesc &d = L.objs[o];
+        std::memset(&d, 0, sizeof d);
+        char where[64];
+        std::snprintf(where, sizeof where, "object %d: ", o);
+        if (src.kind != MHC_VEHICLE && src.kind != MHC_PEDESTRIAN) return fail(MHC_E_INVALID, std::string(where) + "bad kind");
+        if (src.n_a < 1 || src.n_b < 1 || !src.grid_a || !src.grid_b)
+            return fail(MHC_E_INVALID, std::string(where) + "grids must be non-empty and non-NULL");
+        if ((long long)src.n_a * src.n_b > (1LL << 30)) return fail(MHC_E_INVALID, std::string(where) + "too many hypotheses");
+        if (!finite(src.x0) || !finite(src.y0) || !finite(src.psi0) || !finite(src.v0) || !(src.v0 >= 0.f))
+            return fail(MHC_E_INVALID, std::string(where) + "initial state must be finite with v0 >= 0");
+        d.kind = src.kind; d.flags = src.flags; d.n_a = src.n_a; d.n_b = src.n_b; d.h = src.n_a * src.n_b;
+        d.grid_off = (int)L.grids.size();
+        for (int q = 0; q < src.n_a; ++q) {
+            if (!finite(src.grid_a[q])) return fail(MHC_E_INVALID, std::string(where) + "grid_a not finite");
+            if (src.kind == MHC_PEDESTRIAN && !(src.flags & MHC_PED_ACCEL_GRID) && src.grid_a[q] < 0.f)
+                return fail(MHC_E_INVALID, std::string(where) + "pedestrian speeds must be >= 0");
+            L.grids.push_back(src.grid_a[q]);
+        }
+        for (int q = 0; q < src.n_b; ++q) {
+            if (!finite(src.grid_b[q])) return fail(MHC_E_INVALID, std::string(where) + "grid_b not finite");
+            L.grids.push_back(src.grid_b[q]);
+        }
+        d.traj_off = traj;
+        d.pose_base = traj * (long long)L.N;
+        traj += d.h;
+        d.tile_base = tiles32;
+        d.n_tiles32 = (d.h + kBoundTile - 1) / kBoundTile;
+        tiles32 += d.n_tiles32;
+        d.x0 = src.x0; d.y0 = src.y0; d.psi0 = src.psi0; d.v0 = src.v0; d.v_max = src.v_max;
+        if (src.kind == MHC_VEHICLE) {
+            if (!(src.length > 0.f) || !(src.width > 0.f) || !finite(src.length) || !finite(src.width))
+                return fail(MHC_E_INVALID, std::string(where) + "vehicle needs positive length and width");
+            const float *pp = src.veh_params ? src.veh_params : kDefault;
+            for (int q = 0; q < 6; ++q)
+                if (!(pp[q] > 0.f) || !finite(pp[q])) return fail(MHC_E_INVALID, std::string(where) + "vehicle parameters must be positive");
+            d.m = pp[0]; d.Iz = pp[1]; d.lf = pp[2]; d.lr = pp[3]; d.caf = pp[4]; d.car = pp[5];
+            d.hl = 0.5f * src.length; d.hw = 0.5f * src.width; d.rad = 0.f;
+            d.circ = (float)std::sqrt((double)d.hl * d.hl + (double)d.hw * d.hw);
+        } else {
+            if (!(src.radius > 0.f) || !finite(src.radius)) return fail(MHC_E_INVALID, std::string(where) + "pedestrian needs a positive radius");
+            d.rad = src.radius; d.circ = src.radius;
+        }
+        for (int q = 0; q < d.n_tiles32; ++q) { L.warp_obj.push_back(o); L.warp_first.push_back(q * kBoundTile); }
+    }
+    L.n_traj = traj;
+    L.n_tiles32 = tiles32;
+    L.h_e = L.objs[L.ego].h;
+    auto add_pair = [&](int a, int b) {
+        PairDesc p;
+        std::memset(&p, 0, sizeof p);
+        const ObjDesc &A = L.objs[a], &B = L.objs[b];
+        p.a = a; p.b = b;
+        p.tiles_a = (A.h + kTile - 1) / kTile;
+        p.tiles_b = (B.h + kTile - 1) / kTile;
+        p.off = L.n_entries;
+        p.tile_start = L.n_tiles;
+        const double R = (double)A.circ + (double)B.circ;
+        p.rc2 = (float)(R * R * (1.0 + 1e-6));
+        p.r_cull = (float)(R * (1.0 + 1e-6) + 1e-3);
+        p.combo = (A.kind == MHC_VEHICLE ? 0 : 2) + (B.kind == MHC_VEHICLE ? 0 : 1);
+        p.ego_side = a == L.ego ? 0 : (b == L.ego ? 1 : -1);
+        L.n_entries += (long long)A.h * B.h;
+        L.n_tiles += (long long)p.tiles_a * p.tiles_b;
+        L.pairs.push_back(p);
+    };
+    if (L.pair_mode == MHC_EGO_ONLY) {
+        for (int b = 0; b < L.n_obj; ++b) if (b != L.ego) add_pair(L.ego, b);
+    } else {
+        for (int a = 0; a < L.n_obj; ++a) for (int b = a + 1; b < L.n_obj; ++b) add_pair(a, b);
+    }
+    if (L.n_tiles > 0x7fffffffLL) return fail(MHC_E_INVALID, "too many collision tiles for one launch");
+    return MHC_OK;
+}
+
+// Device scratch each call needs (besides caller buffers).
+struct Scratch {
+    size_t desc = 0, bounds = 0, prob = 0, acc = 0, weights = 0, total = 0;
+    long long acc_words = 0;
+};
+
+Scratch scratch_of(const Layout &L, bool with_weights) {
+    Scratch s;
+    s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
+             align_up(sizeof(float) * L.grids.size()) + 2 * align_up(sizeof(int) * L.warp_obj.size());
+    s.bounds = align_up(sizeof(float4) * (size_t)L.n_tiles32 * L.N);
+    s.prob = align_up(sizeof(double) * (size_t)L.n_traj);
+    s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
+    const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+    s.acc_words = np + np * N + np + np * N + he + he + he * N * no + he * no + no + N + 4;
+    s.acc = align_up(8 * (size_t)s.acc_words);
+    s.total = s.desc + s.weights + s.bounds + s.prob + s.acc;
+    return s;
+}
+
+}  // namespace
+
+struct mhc_ctx {
+    int device = 0;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    bool owns = false;
+    void *stage[kSlots] = {};
+    size_t stage_cap[kSlots] = {};
+    cudaEvent_t stage_ev[kSlots] = {};
+    int slot = 0;
+    cudaEvent_t done_ev = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool has_last = false;
+    int cull = 1;
+    unsigned long long *counters = nullptr;
+    // kernel timing
+    bool profile = false;
+    struct Timed { cudaEvent_t a, b; int kind; int launches; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[MHC_K_COUNT] = {};
+    long long prof_n[MHC_K_COUNT] = {};
+    long long h2d = 0, d2h = 0;
+};
+
+namespace {
+
+cudaEvent_t pooled_event(mhc_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records an event pair around the launches made in its scope when profiling is on.
+struct TimedScope {
+    mhc_ctx *ctx;
+    cudaStream_t st;
+    int kind, launches;
+    cudaEvent_t a = nullptr;
+    TimedScope(mhc_ctx *c, cudaStream_t s, int k, int n) : ctx(c), st(s), kind(k), launches(n) {
+        if (ctx->profile && (a = pooled_event(ctx))) cudaEventRecord(a, st);
+    }
+    ~TimedScope() {
+        if (!a) return;
+        cudaEvent_t b = pooled_event(ctx);
+        if (!b) { ctx->ev_pool.push_back(a); return; }
+        cudaEventRecord(b, st);
+        ctx->timed.push_back({a, b, kind, launches});
+    }
+};
+
+// Bump allocator over the arena for one call.
+struct Bump {
+    char *base;
+    size_t cap, off;
+    void *take(size_t n) {
+        n = align_up(n);
+        if (off + n > cap) return nullptr;
+        void *p = base + off;
+        off += n;
+        return p;
+    }
+};
+
+// Order this call after the context's previous call when it used another stream.
+int begin_call(mhc_ctx *ctx, cudaStream_t st) {
+    MHC_CUDA(cudaSetDevice(ctx->device));
+    if (ctx->has_last && ctx->last_stream != st) MHC_CUDA(cudaStreamWaitEvent(st, ctx->done_ev, 0));
+    return MHC_OK;
+}
+
+int end_call(mhc_ctx *ctx, cudaStream_t st) {
+    MHC_CUDA(cudaEventRecord(ctx->done_ev, st));
+    ctx->last_stream = st;
+    ctx->has_last = true;
+    return MHC_OK;
+}
+
+// Pack the descriptors into a pinned staging slot and copy them to `dev` on `st`.
+struct DevDesc {
+    ObjDesc *objs;
+    PairDesc *pairs;
+    float *grids;
+    int *warp_obj, *warp_first;
+    float *weights;
+};
+
+int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, char *dev, cudaStream_t st,
+           DevDesc &out) {
+    std::vector<std::pair<const void *, size_t>> parts = {
+        {L.objs.data(), sizeof(ObjDesc) * L.objs.size()},
+        {L.pairs.data(), sizeof(PairDesc) * L.pairs.size()},
+        {L.grids.data(), sizeof(float) * L.grids.size()},
+        {L.warp_obj.data(), sizeof(int) * L.warp_obj.size()},
+        {L.warp_first.data(), sizeof(int) * L.warp_first.size()},
+    };
+    size_t caps[5] = {align_up(parts[0].second), align_up(sizeof(PairDesc) * (L.pairs.size() + 1)),
+                      align_up(parts[2].second), align_up(parts[3].second), align_up(parts[4].second)};
+    size_t total = 0;
+    for (size_t c : caps) total += c;
+    const size_t wbytes = weights ? align_up(sizeof(float) * weights->size()) : 0;
+    total += wbytes;
+    const int s = ctx->slot;
+    ctx->slot = (ctx->slot + 1) % kSlots;
+    MHC_CUDA(cudaEventSynchronize(ctx->stage_ev[s]));
+    if (ctx->stage_cap[s] < total) {
+        if (ctx->stage[s]) MHC_CUDA(cudaFreeHost(ctx->stage[s]));
+        ctx->stage[s] = nullptr;
+        ctx->stage_cap[s] = 0;
+        size_t cap = total < (1u << 20) ? (1u << 20) : total * 2;
+        MHC_CUDA(cudaHostAlloc(&ctx->stage[s], cap, cudaHostAllocDefault));
+        ctx->stage_cap[s] = cap;
+    }
+    char *h = static_cast<char *>(ctx->stage[s]);
+    size_t off = 0;
+    char *ptrs[6];
+    for (int q = 0; q < 5; ++q) {
+        if (parts[q].second) std::memcpy(h + off, parts[q].first, parts[q].second);
+        ptrs[q] = dev + off;
+        off += caps[q];
+    }
+    ptrs[5] = dev + off;
+    if (weights && !weights->empty()) std::memcpy(h + off, weights->data(), sizeof(float) * weights->size());
+    off += wbytes;
+    MHC_CUDA(cudaMemcpyAsync(dev, h, off, cudaMemcpyHostToDevice, st));
+    MHC_CUDA(cudaEventRecord(ctx->stage_ev[s], st));
+    ctx->h2d = (long long)off;
+    ctx->d2h = 0;
+    out.objs = reinterpret_cast<ObjDesc *>(ptrs[0]);
+    out.pairs = reinterpret_cast<PairDesc *>(ptrs[1]);
+    out.grids = reinterpret_cast<float *>(ptrs[2]);
+    out.warp_obj = reinterpret_cast<int *>(ptrs[3]);
+    out.warp_first = reinterpret_cast<int *>(ptrs[4]);
+    out.weights = weights ? reinterpret_cast<float *>(ptrs[5]) : nullptr;
+    return MHC_OK;
+}
+
+int check_ctx(mhc_ctx *ctx) { return ctx ? MHC_OK : fail(MHC_E_INVALID, "context is NULL"); }
+
+// Validated host weights (ones where a pointer is NULL); empty when all uniform.
+int gather_weights(const Layout &L, const float *const *w, std::vector<float> &out) {
+    out.clear();
+    if (!w) return MHC_OK;
+    bool any = false;
+    for (int o = 0; o < L.n_obj; ++o) any |= w[o] != nullptr;
+    if (!any) return MHC_OK;
+    out.resize((size_t)L.n_traj);
+    for (int o = 0; o < L.n_obj; ++o) {
+        const ObjDesc &d = L.objs[o];
+        double sum = 0.0;
+        for (int i = 0; i < d.h; ++i) {
+            const float v = w[o] ? w[o][i] : 1.0f;
+            if (!(v >= 0.f) || !finite(v)) {
+                char msg[96];
+                std::snprintf(msg, sizeof msg, "object %d: weights must be finite and non-negative", o);
+                return fail(MHC_E_INVALID, msg);
+            }
+            out[(size_t)d.traj_off + i] = v;
+            sum += v;
+        }
+        if (!(sum > 0.0)) {
+            char msg[96];
+            std::snprintf(msg, sizeof msg, "object %d: weights sum to zero", o);
+            return fail(MHC_E_INVALID, msg);
+        }
+    }
+    return MHC_OK;
+}
+
+int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, const mhc_poses *gen_out,
+               const mhc_poses *coll_in, int16_t *table, bool risk, const mhc_risk *rout, cudaStream_t st) {
+    if (gen_out) {
+        GenArgs g;
+        g.objs = D.objs; g.grids = D.grids; g.warp_obj = D.warp_obj; g.warp_first = D.warp_first;
+        g.n_warps = (int)L.warp_obj.size(); g.n_steps = L.N; g.substeps = L.K; g.model = L.model;
+        g.tau = L.tau; g.tau_d = (double)L.tau;
+        g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
+        TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
+        cudaError_t e = launch_generate(g, st);
+        if (e != cudaSuccess) return cuda_fail(e, "generation kernel launch");
+    }
+    if (coll_in) {
+        float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_tiles32 * L.N));
+        if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
+        if (ctx->cull) {
+            BoundsArgs b;
+            b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
+            b.n_warps = (int)L.warp_obj.size(); b.n_steps = L.N; b.x = coll_in->x; b.y = coll_in->y; b.bounds = bounds;
+            TimedScope ts(ctx, st, MHC_K_BOUNDS, 1);
+            cudaError_t e = launch_bounds(b, st);
+            if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
+        }
+        CollideArgs c;
+        c.objs = D.objs; c.pairs = D.pairs; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
+        c.n_steps = L.N; c.cull = ctx->cull;
+        c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
+        c.bounds = bounds; c.table = table; c.counters = ctx->counters;
+        TimedScope ts(ctx, st, MHC_K_COLLIDE, 1);
+        cudaError_t e = launch_collide(c, st);
+        if (e != cudaSuccess) return cuda_fail(e, "collision kernel launch");
+    }
+    if (risk) {
+        RiskArgs r;
+        std::memset(&r, 0, sizeof r);
+        r.objs = D.objs; r.pairs = D.pairs; r.n_pairs = (int)L.pairs.size(); r.n_obj = L.n_obj;
+        r.n_steps = L.N; r.ego = L.ego; r.h_e = L.h_e; r.n_tiles = L.n_tiles; r.table = table;
+        r.weights = D.weights;
+        r.prob = static_cast<double *>(bump.take(sizeof(double) * (size_t)L.n_traj));
+        const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+        const long long words = np + np * N + np + np * N + he + he + he * N * no + he * no + no + N + 4;
+        unsigned long long *w = static_cast<unsigned long long *>(bump.take(8 * (size_t)words));
+        if (!r.prob || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
+        RiskScratch &A = r.acc;
+        A.base = w; A.n_words = words;
+        A.count = w; w += np;
+        A.count_k = w; w += np * N;
+        A.P = reinterpret_cast<double *>(w); w += np;
+        A.H = reinterpret_cast<double *>(w); w += np * N;
+        A.naive = reinterpret_cast<double *>(w); w += he;
+        A.hits = w; w += he;
+        A.logq = reinterpret_cast<double *>(w); w += he * N * no;
+        A.mass = reinterpret_cast<double *>(w); w += he * no;
+        A.attr_obj = reinterpret_cast<double *>(w); w += no;
+        A.attr_step = reinterpret_cast<double *>(w); w += N;
+        A.scalars = reinterpret_cast<double *>(w);
+        r.count = reinterpret_cast<long long *>(rout->count);
+        r.count_k = reinterpret_cast<long long *>(rout->count_k);
+        r.P = rout->P; r.H = rout->H; r.naive = rout->naive; r.cond = rout->cond; r.indep = rout->indep;
+        r.hits = rout->hits; r.attr_obj = rout->attr_obj; r.attr_step = rout->attr_step;
+        r.scalars = rout->scalars; r.escape = rout->escape; r.n_escape = rout->n_escape;
+        TimedScope ts(ctx, st, MHC_K_RISK, 4);
+        cudaError_t e = launch_risk(r, st);
+        if (e != cudaSuccess) return cuda_fail(e, "risk kernel launch");
+    }
+    return MHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mhc_status_string(int s) {
+    switch (s) {
+        case MHC_OK: return "MHC_OK";
+        case MHC_PENDING: return "MHC_PENDING";
+        case MHC_E_INVALID: return "MHC_E_INVALID";
+        case MHC_E_NOMEM: return "MHC_E_NOMEM";
+        case MHC_E_CUDA: return "MHC_E_CUDA";
+        case MHC_E_TIMEOUT: return "MHC_E_TIMEOUT";
+        case MHC_E_BUSY: return "MHC_E_BUSY";
+        case MHC_E_NOTFOUND: return "MHC_E_NOTFOUND";
+        default: return "MHC_E_UNKNOWN";
+    }
+}
+
+const char *mhc_last_error(void) { return g_err.c_str(); }
+
+const char *mhc_version(void) { return "mhc 0.1 sm_103a"; }
+
+int mhc_create(mhc_ctx **out, int device, void *arena, size_t arena_bytes) {
+    if (!out) return fail(MHC_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (arena_bytes < (1u << 20)) return fail(MHC_E_INVALID, "arena_bytes must be at least 1 MiB");
+    int n = 0;
+    MHC_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(MHC_E_INVALID, "device out of range");
+    MHC_CUDA(cudaSetDevice(device));
+    mhc_ctx *c = new mhc_ctx();
+    c->device = device;
+    c->arena_bytes = arena_bytes;
+    if (arena) {
+        c->arena = static_cast<char *>(arena);
+    } else {
+        cudaError_t e = cudaMalloc(&c->arena, arena_bytes);
+        if (e != cudaSuccess) { delete c; return fail(MHC_E_NOMEM, "cudaMalloc of the arena failed"); }
+        c->owns = true;
+    }
+    for (int s = 0; s < kSlots; ++s) {
+        cudaError_t e = cudaEventCreateWithFlags(&c->stage_ev[s], cudaEventDisableTiming);
+        if (e != cudaSuccess) { mhc_destroy(c); return cuda_fail(e, "cudaEventCreate"); }
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { mhc_destroy(c); return cuda_fail(e, "cudaEventCreate"); }
+    c->counters = reinterpret_cast<unsigned long long *>(c->arena);
+    e = cudaMemset(c->counters, 0, kReserved);
+    if (e != cudaSuccess) { mhc_destroy(c); return cuda_fail(e, "cudaMemset"); }
+    *out = c;
+    return MHC_OK;
+}
+
+void mhc_destroy(mhc_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (int s = 0; s < kSlots; ++s) {
+        if (c->stage_ev[s]) cudaEventDestroy(c->stage_ev[s]);
+        if (c->stage[s]) cudaFreeHost(c->stage[s]);
+    }
+    if (c->done_ev) cudaEventDestroy(c->done_ev);
+    for (auto &t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->owns && c->arena) cudaFree(c->arena);
+    delete c;
+}
+
+int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
+    if (int r = check_ctx(ctx)) return r;
+    if (option == MHC_OPT_CULL) { ctx->cull = value != 0; return MHC_OK; }
+    if (option == MHC_OPT_PROFILE) { ctx->profile = value != 0; return MHC_OK; }
+    return fail(MHC_E_INVALID, "unknown option");
+}
+
+int mhc_profile_read(mhc_ctx *ctx, double ms[4], int64_t launches[4], int reset) {
+    if (int r = check_ctx(ctx)) return r;
+    MHC_CUDA(cudaSetDevice(ctx->device));
+    for (auto &t : ctx->timed) {
+        MHC_CUDA(cudaEventSynchronize(t.b));
+        float v = 0.f;
+        MHC_CUDA(cudaEventElapsedTime(&v, t.a, t.b));
+        ctx->prof_ms[t.kind] += v;
+        ctx->prof_n[t.kind] += t.launches;
+        ctx->ev_pool.push_back(t.a);
+        ctx->ev_pool.push_back(t.b);
+    }
+    ctx->timed.clear();
+    for (int k = 0; k < MHC_K_COUNT; ++k) {
+        if (ms) ms[k] = ctx->prof_ms[k];
+        if (launches) launches[k] = ctx->prof_n[k];
+        if (reset) { ctx->prof_ms[k] = 0.0; ctx->prof_n[k] = 0; }
+    }
+    return MHC_OK;
+}
+
+int mhc_transfer_bytes(mhc_ctx *ctx, int64_t *h2d, int64_t *d2h) {
+    if (int r = check_ctx(ctx)) return r;
+    if (h2d) *h2d = ctx->h2d;
+    if (d2h) *d2h = ctx->d2h;
+    return MHC_OK;
+}
+
+int mhc_collision_counters(mhc_ctx *ctx, uint64_t out[2], int reset, void *stream) {
+    if (int r = check_ctx(ctx)) return r;
+    if (!out) return fail(MHC_E_INVALID, "out is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MHC_CUDA(cudaSetDevice(ctx->device));
+    MHC_CUDA(cudaMemcpyAsync(out, ctx->counters, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    MHC_CUDA(cudaStreamSynchronize(st));
+    if (reset) {
+        MHC_CUDA(cudaMemsetAsync(ctx->counters, 0, 2 * sizeof(uint64_t), st));
+        MHC_CUDA(cudaStreamSynchronize(st));
+    }
+    return MHC_OK;
+}
+
+int mhc_layout(const mhc_scenario *scen, int64_t *n_traj, int32_t *n_pairs, int64_t *n_entries, int32_t *h_ego,
+               size_t *scratch) {
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    if (n_traj) *n_traj = L.n_traj;
+    if (n_pairs) *n_pairs = (int32_t)L.pairs.size();
+    if (n_entries) *n_entries = L.n_entries;
+    if (h_ego) *h_ego = L.h_e;
+    if (scratch) *scratch = kReserved + scratch_of(L, true).total;
+    return MHC_OK;
+}
+
+int mhc_pair_table(const mhc_scenario *scen, int32_t *pair_a, int32_t *pair_b, int64_t *pair_off) {
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    for (size_t p = 0; p < L.pairs.size(); ++p) {
+        if (pair_a) pair_a[p] = L.pairs[p].a;
+        if (pair_b) pair_b[p] = L.pairs[p].b;
+        if (pair_off) pair_off[p] = L.pairs[p].off;
+    }
+    if (pair_off) pair_off[L.pairs.size()] = L.n_entries;
+    return MHC_OK;
+}
+
+int mhc_generate_trajectories(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *out, void *stream) {
+    if (int r = check_ctx(ctx)) return r;
+    if (!out || !out->x || !out->y || !out->c || !out->s) return fail(MHC_E_INVALID, "pose planes must be non-NULL");
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch S = scratch_of(L, false);
+    Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
+    char *dev = static_cast<char *>(bump.take(S.desc));
+    if (!dev) return fail(MHC_E_NOMEM, "arena too small for the descriptors");
+    if (int r = begin_call(ctx, st)) return r;
+    DevDesc D;
+    if (int r = upload(ctx, L, nullptr, dev, st, D)) return r;
+    if (int r = launch_all(ctx, L, D, bump, out, nullptr, nullptr, false, nullptr, st)) return r;
+    return end_call(ctx, st);
+}
+
+int mhc_detect_collisions(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses, int16_t *table,
+                          void *stream) {
+    if (int r = check_ctx(ctx)) return r;
+    if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table)
+        return fail(MHC_E_INVALID, "poses and table must be non-NULL");
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch S = scratch_of(L, false);
+    Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
+    char *dev = static_cast<char *>(bump.take(S.desc));
+    if (!dev) return fail(MHC_E_NOMEM, "arena too small for the descriptors");
+    if (int r = begin_call(ctx, st)) return r;
+    DevDesc D;
+    if (int r = upload(ctx, L, nullptr, dev, st, D)) return r;
+    if (int r = launch_all(ctx, L, D, bump, nullptr, poses, table, false, nullptr, st)) return r;
+    return end_call(ctx, st);
+}
+
+int mhc_assess_risk(mhc_ctx *ctx, const mhc_scenario *scen, const int16_t *table, const float *const *traj_weights,
+                    const mhc_risk *out, void *stream) {
+    if (int r = check_ctx(ctx)) return r;
+    if (!table || !out) return fail(MHC_E_INVALID, "table and out must be non-NULL");
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    std::vector<float> w;
+    if (int r = gather_weights(L, traj_weights, w)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch S = scratch_of(L, !w.empty());
+    Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
+    char *dev = static_cast<char *>(bump.take(S.desc + S.weights));
+    if (!dev) return fail(MHC_E_NOMEM, "arena too small for the descriptors");
+    if (int r = begin_call(ctx, st)) return r;
+    DevDesc D;
+    if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
+    if (int r = launch_all(ctx, L, D, bump, nullptr, nullptr, const_cast<int16_t *>(table), true, out, st)) return r;
+    return end_call(ctx, st);
+}
+
+int mhc_run_bytes(const mhc_scenario *scen, size_t *bytes) {
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    if (!bytes) return fail(MHC_E_INVALID, "bytes is NULL");
+    const size_t poses = 4 * align_up(sizeof(float) * (size_t)L.n_traj * L.N);
+    const size_t table = align_up(sizeof(int16_t) * (size_t)L.n_entries);
+    const size_t np = L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+    const size_t outs = align_up(8 * (np + np * N + np + np * N + 3 * he + no + N + 4)) + 2 * align_up(4 * he) + kAlign;
+    *bytes = kReserved + scratch_of(L, true).total + poses + table + outs;
+    return MHC_OK;
+}
+
+int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, const mhc_risk *out,
+            void *stream) {
+    if (int r = check_ctx(ctx)) return r;
+    if (!out) return fail(MHC_E_INVALID, "out is NULL");
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    std::vector<float> w;
+    if (int r = gather_weights(L, traj_weights, w)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch S = scratch_of(L, !w.empty());
+    Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
+    char *dev = static_cast<char *>(bump.take(S.desc + S.weights));
+    const size_t plane = sizeof(float) * (size_t)L.n_traj * L.N;
+    mhc_poses P;
+    P.x = static_cast<float *>(bump.take(plane));
+    P.y = static_cast<float *>(bump.take(plane));
+    P.c = static_cast<float *>(bump.take(plane));
+    P.s = static_cast<float *>(bump.take(plane));
+    int16_t *table = static_cast<int16_t *>(bump.take(sizeof(int16_t) * (size_t)L.n_entries));
+    const size_t np = L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+    mhc_risk R;
+    std::memset(&R, 0, sizeof R);
+    R.count = static_cast<int64_t *>(bump.take(8 * np));
+    R.count_k = static_cast<int64_t *>(bump.take(8 * np * N));
+    R.P = static_cast<double *>(bump.take(8 * np));
+    R.H = static_cast<double *>(bump.take(8 * np * N));
+    R.naive = static_cast<double *>(bump.take(8 * he));
+    R.cond = static_cast<double *>(bump.take(8 * he));
+    R.indep = static_cast<double *>(bump.take(8 * he));
+    R.hits = static_cast<int32_t *>(bump.take(4 * he));
+    R.attr_obj = static_cast<double *>(bump.take(8 * no));
+    R.attr_step = static_cast<double *>(bump.take(8 * N));
+    R.scalars = static_cast<double *>(bump.take(8 * 4));
+    R.escape = static_cast<int32_t *>(bump.take(4 * he));
+    R.n_escape = static_cast<int32_t *>(bump.take(4));
+    if (!dev || !P.x || !P.y || !P.c || !P.s || !table || !R.count || !R.count_k || !R.P || !R.H || !R.naive ||
+        !R.cond || !R.indep || !R.hits || !R.attr_obj || !R.attr_step || !R.scalars || !R.escape || !R.n_escape)
+        return fail(MHC_E_NOMEM, "arena too small for mhc_run (see mhc_run_bytes)");
+    if (int r = begin_call(ctx, st)) return r;
+    DevDesc D;
+    if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
+    if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st)) return r;
+    struct Cp { void *dst; const void *src; size_t n; } cps[] = {
+        {out->count, R.count, 8 * np}, {out->count_k, R.count_k, 8 * np * N}, {out->P, R.P, 8 * np},
+        {out->H, R.H, 8 * np * N}, {out->naive, R.naive, 8 * he}, {out->cond, R.cond, 8 * he},
+        {out->indep, R.indep, 8 * he}, {out->hits, R.hits, 4 * he}, {out->attr_obj, R.attr_obj, 8 * no},
+        {out->attr_step, R.attr_step, 8 * N}, {out->scalars, R.scalars, 8 * 4}, {out->escape, R.escape, 4 * he},
+        {out->n_escape, R.n_escape, 4}};
+    for (const Cp &c : cps) {
+        if (!c.dst) continue;
+        MHC_CUDA(cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, st));
+        ctx->d2h += (long long)c.n;
+    }
+    if (int r = end_call(ctx, st)) return r;
+    MHC_CUDA(cudaStreamSynchronize(st));
+    return MHC_OK;
+}
+
+}  // extern "C"

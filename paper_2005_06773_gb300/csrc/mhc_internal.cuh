@@ -1,0 +1,125 @@
+// mhc_internal.cuh -- device descriptors and launch interfaces shared by the library's translation units.
+//
+// Layouts (all in the context arena unless the caller passes buffers):
+//   poses   SoA planes x, y, c, s; pose (object a, step k, hypothesis i) at N * traj_off[a] + k * h_a + i.
+//   table   int16, pair p block of h_a x h_b at pair_off[p], row-major (row = hypothesis of a).
+//   bounds  per 32-hypothesis tile of an object and per step: float4 {xmin, ymin, xmax, ymax} of the
+//           tile's pose centres, at (tile_base[a] + tile) * N + k.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mhc {
+
+constexpr int kVehicle = 0;
+constexpr int kPedestrian = 1;
+constexpr int kModelOT = 0;
+constexpr int kModelKin = 1;
+constexpr int kPedAccelGrid = 1;
+constexpr float kVMin = 2.0f;      // below this speed the one-track model gives way to its kinematic limit
+constexpr double kVMinD = 2.0;
+
+constexpr int kTile = 64;          // collision tile edge (hypotheses per side)
+constexpr int kBoundTile = 32;     // hypotheses per bounding-box tile (one warp)
+constexpr int16_t kNoHit = 0x7fff; // in-kernel sentinel, stored as -1
+
+// Per-object descriptor (device).
+struct ObjDesc {
+    int kind, flags, n_a, n_b;
+    int h;              // hypotheses n_a * n_b
+    int grid_off;       // grid_a at grids[grid_off], grid_b right after
+    int tile_base;      // first 32-wide bound tile of this object
+    int n_tiles32;
+    long long traj_off; // global index of hypothesis 0
+    long long pose_base;// n_steps * traj_off
+    float hl, hw, rad;  // half length, half width, disc radius
+    float circ;         // circumradius about the pose point
+    float x0, y0, psi0, v0, v_max;
+    float m, Iz, lf, lr, caf, car;
+};
+
+// Per-object-pair descriptor (device).
+struct PairDesc {
+    int a, b;
+    int tiles_a, tiles_b;     // 64-wide tiles along each side
+    long long off;            // table offset of the pair's block
+    long long tile_start;     // first global collision tile of this pair
+    float rc2;                // (R_a + R_b)^2, R = circumradius about the pose point
+    float r_cull;             // R_a + R_b plus a margin, for bounding-box culling
+    int combo;                // 0 rect-rect, 1 rect(a)-disc(b), 2 disc(a)-rect(b), 3 disc-disc
+    int ego_side;             // 0: a is the EGO object, 1: b is, -1: neither
+};
+
+struct GenArgs {
+    const ObjDesc *objs;
+    const float *grids;
+    const int *warp_obj;      // object of each 32-hypothesis warp task
+    const int *warp_first;    // first hypothesis of each warp task
+    int n_warps;
+    int n_steps, substeps, model;
+    float tau;
+    double tau_d;
+    float *x, *y, *c, *s;
+};
+
+struct BoundsArgs {
+    const ObjDesc *objs;
+    const int *warp_obj, *warp_first;
+    int n_warps, n_steps;
+    const float *x, *y;
+    float4 *bounds;
+};
+
+struct CollideArgs {
+    const ObjDesc *objs;
+    const PairDesc *pairs;
+    int n_pairs;
+    long long n_tiles;        // total collision tiles over all pairs
+    int n_steps;
+    int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
+    const float *x, *y, *c, *s;
+    const float4 *bounds;
+    int16_t *table;
+    unsigned long long *counters;  // optional: [0] broad-phase tests executed, [1] narrow-phase tests
+};
+
+// Risk accumulators: one contiguous block of 8-byte words, zeroed before every assessment.
+struct RiskScratch {
+    unsigned long long *count;     // [n_pairs]
+    unsigned long long *count_k;   // [n_pairs * N]
+    double *P, *H;                 // [n_pairs], [n_pairs * N]
+    double *naive;                 // [h_e]
+    unsigned long long *hits;      // [h_e]
+    double *logq;                  // [h_e * N * n_obj]: sum of log(1 - p_b[j]) over entries (i, b, j) at step k
+    double *mass;                  // [h_e * n_obj]:     sum of p_b[j] over colliding entries (i, b, j)
+    double *attr_obj, *attr_step;  // [n_obj], [N]
+    double *scalars;               // [4]
+    unsigned long long *base;      // first word of the block
+    long long n_words;             // words to zero
+};
+
+struct RiskArgs {
+    const ObjDesc *objs;
+    const PairDesc *pairs;
+    int n_pairs, n_obj, n_steps, ego, h_e;
+    long long n_tiles;
+    const int16_t *table;
+    const float *weights;          // [n_traj] raw non-negative weights, or null for uniform
+    double *prob;                  // [n_traj] normalised probabilities (scratch)
+    RiskScratch acc;
+    // outputs (device); any may be null
+    long long *count, *count_k;
+    double *P, *H;
+    double *naive, *cond, *indep;
+    int *hits;
+    double *attr_obj, *attr_step, *scalars;
+    int *escape, *n_escape;
+};
+
+cudaError_t launch_generate(const GenArgs &a, cudaStream_t st);
+cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st);
+cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);
+cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st);
+
+}  // namespace mhc

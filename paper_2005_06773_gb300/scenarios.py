@@ -198,15 +198,22 @@ _ARMS = (  # (unit vector from centre to arm, heading toward centre, lateral uni
 
 def _place_cars(rng: SplitMix64, n: int, per_arm: Optional[int], d_lo: float, d_hi: float,
                 spacing: float, v_lo: float, v_hi: float):
-    """Cars queued on the four approach arms, heading to the centre, centre-to-centre spacing >= spacing."""
+    """Cars queued on the four approach arms, heading to the centre, centre-to-centre spacing >= spacing.
+    A car whose drawn arm has no room left goes to the emptiest arm that has."""
     arms: List[List[float]] = [[], [], [], []]
     out = []
     for c in range(n):
-        arm = (c % 4) if per_arm is not None else rng.randint(0, 3)
-        hi = d_hi + (spacing * len(arms[arm]) if per_arm is not None else 0.0)
-        for _ in range(10000):
-            d = rng.uniform(d_lo, hi)
-            if all(abs(d - e) >= spacing for e in arms[arm]):
+        first = (c % 4) if per_arm is not None else rng.randint(0, 3)
+        order = [first] + sorted((q for q in range(4) if q != first), key=lambda q: (len(arms[q]), q))
+        for arm in order:
+            hi = d_hi + (spacing * len(arms[arm]) if per_arm is not None else 0.0)
+            d = None
+            for _ in range(10000):
+                cand = rng.uniform(d_lo, hi)
+                if all(abs(cand - e) >= spacing for e in arms[arm]):
+                    d = cand
+                    break
+            if d is not None:
                 break
         else:
             raise RuntimeError("placement failed")

@@ -1,0 +1,110 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/mhc.h; host-side
+layout and validation behave as documented.  No GPU is touched."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2005_06773_gb300 import build as B
+from paper_2005_06773_gb300 import scenarios as S
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mhc.h")
+
+
+@pytest.fixture(scope="module")
+def mhc():
+    B.build()
+    from paper_2005_06773_gb300 import mhc as m
+    return m
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mhc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(mhc):
+    names = declared_functions()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(B.LIB)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(mhc):
+    assert mhc.lib.mhc_status_string(-1) == b"MHC_E_INVALID"
+    assert mhc.lib.mhc_status_string(0) == b"MHC_OK"
+    assert b"sm_103a" in mhc.lib.mhc_version()
+
+
+def test_layout_counts(mhc):
+    lay = mhc.layout(S.intersection11(2))
+    assert lay["n_traj"] == 3571 and lay["n_pairs"] == 55 and lay["n_entries"] == 5_666_055 and lay["h_ego"] == 441
+    big = mhc.layout(S.stress32(4))
+    assert big["n_entries"] == 496 * 2048 * 2048
+    s2 = S.paper_s1s2(10, 6)
+    lay = mhc.layout(s2)
+    assert lay["n_entries"] == 864_360 and lay["n_traj"] == 2478 and lay["n_pairs"] == 10
+
+
+def test_pair_table_matches_oracle(mhc, orc):
+    for sc in (S.intersection11(2), S.paper_s1s2(3, 5), S.stress32(4)):
+        pa, pb, poff = mhc.pair_table(sc)
+        assert list(zip(pa.tolist(), pb.tolist())) == orc.pair_list(sc)
+        assert np.array_equal(poff, orc.pair_offsets(sc))
+    sc = S.intersection11(3)
+    sc.pair_mode, sc.ego = S.EGO_ONLY, 4
+    pa, pb, _ = mhc.pair_table(sc)
+    assert set(pa.tolist()) == {4} and 4 not in pb.tolist() and len(pb) == 10
+
+
+def _bad(mutate):
+    sc = S.tiny_crossing(1)
+    mutate(sc)
+    return sc
+
+
+BAD = {
+    "zero_steps": lambda s: setattr(s, "n_steps", 0),
+    "too_many_steps": lambda s: setattr(s, "n_steps", 40000),
+    "zero_tau": lambda s: setattr(s, "tau", 0.0),
+    "nan_tau": lambda s: setattr(s, "tau", float("nan")),
+    "zero_substeps": lambda s: setattr(s, "substeps", 0),
+    "bad_pair_mode": lambda s: setattr(s, "pair_mode", 5),
+    "bad_model": lambda s: setattr(s, "model", 3),
+    "ego_out_of_range": lambda s: setattr(s, "ego", 2),
+    "bad_kind": lambda s: setattr(s.objects[0], "kind", 7),
+    "empty_grid": lambda s: setattr(s.objects[0], "grid_a", np.zeros(0, np.float32)),
+    "nan_grid": lambda s: s.objects[1].grid_b.__setitem__(0, np.nan),
+    "zero_length": lambda s: setattr(s.objects[0], "length", 0.0),
+    "negative_speed": lambda s: setattr(s.objects[0], "v0", -1.0),
+    "negative_param": lambda s: setattr(s.objects[0], "params", -S.DEFAULT_VEH_PARAMS),
+    "inf_position": lambda s: setattr(s.objects[1], "x0", float("inf")),
+}
+
+
+@pytest.mark.parametrize("case", list(BAD))
+def test_invalid_scenarios_rejected(mhc, case):
+    sc = _bad(BAD[case])
+    with pytest.raises(mhc.MhcError) as e:
+        mhc.layout(sc)
+    assert e.value.code == -1
+
+
+def test_invalid_pedestrian_and_pairing(mhc):
+    ped = S.Obj(S.PEDESTRIAN, 0, 0, 0.4, 0, 0, 0, 0, np.array([-1.0]), np.array([0.0]))
+    car = S.tiny_crossing(1).objects[0]
+    with pytest.raises(mhc.MhcError):
+        mhc.layout(S.Scenario([car, ped]))
+    ped0 = S.Obj(S.PEDESTRIAN, 0, 0, 0.0, 0, 0, 0, 0, np.array([1.0]), np.array([0.0]))
+    with pytest.raises(mhc.MhcError):
+        mhc.layout(S.Scenario([car, ped0]))
+    with pytest.raises(mhc.MhcError):
+        mhc.layout(S.Scenario([car], pair_mode=S.EGO_ONLY))
+    # a single object with all pairs is valid: no pairs, an empty table
+    lay = mhc.layout(S.Scenario([car]))
+    assert lay["n_pairs"] == 0 and lay["n_entries"] == 0

@@ -1,0 +1,260 @@
+"""GPU parity: every kernel of the hot path, called through the C ABI, against the FP64 oracle on the
+same seeded inputs (element by element), plus full-size checks of the 11-object intersection and a
+sampled check of the 32-vehicle stress scenario."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2005_06773_gb300 import scenarios as S
+from parity_util import POSE_TOL, check_risk, check_table, corner_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mhc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_06773_gb300 import mhc as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mhc):
+    c = mhc.Context(0, 1 << 30)
+    yield c
+    c.close()
+
+
+def _ragged():
+    """Hypothesis counts that straddle tile edges (1, 33, 65, 127) and all four shape combinations."""
+    objs = [
+        S.Obj(S.VEHICLE, 4.5, 1.8, 0, -20.0, -1.75, 0.0, 11.0, S.accel_grid_paper(5, -8, 3), S.linspace(-0.3, 0.3, 13),
+              S.DEFAULT_VEH_PARAMS),                                           # 65
+        S.Obj(S.PEDESTRIAN, 0, 0, 0.4, 6.0, -6.0, math.pi / 2, 0.0, S.linspace(0, 3, 3), S.linspace(-1, 1, 11)),  # 33
+        S.Obj(S.VEHICLE, 3.13, 1.46, 0, 1.75, -25.0, math.pi / 2, 9.0, np.array([0.0]), np.array([0.0]),
+              S.DEFAULT_VEH_PARAMS),                                           # 1
+        S.Obj(S.VEHICLE, 5.0, 2.0, 0, 25.0, 1.75, math.pi, 12.0, S.accel_grid_paper(127, -8, 3), np.array([0.02]),
+              S.DEFAULT_VEH_PARAMS),                                           # 127
+        S.Obj(S.PEDESTRIAN, 0, 0, 0.5, -6.0, 6.0, -math.pi / 2, 0.0, S.linspace(0.5, 2.5, 4), S.linspace(-0.5, 0.5, 8)),  # 32
+    ]
+    return S.Scenario(objs, tau=0.1, n_steps=37, substeps=5, ego=3, name="ragged")
+
+
+def _ped_accel():
+    sc = S.intersection11(9, n_steps=25, n_acc=6, n_str=6, n_ped_v=5, n_ped_h=7)
+    for o in sc.objects:
+        if o.kind == S.PEDESTRIAN:
+            o.flags = S.PED_ACCEL_GRID
+            o.v0 = float(np.float32(1.2))
+            o.v_max = float(np.float32(2.7))
+            o.grid_a = S.linspace(-12, 12, 5)
+    sc.name = "ped_accel"
+    return sc
+
+
+def _scenes():
+    out = {
+        "tiny": S.tiny_crossing(1),
+        "tiny_near": S.tiny_crossing(1, 15.0),
+        "mixed_small": S.intersection11(5, n_steps=40, n_acc=9, n_str=7, n_ped_v=5, n_ped_h=9),
+        "ragged": _ragged(),
+        "ped_accel": _ped_accel(),
+        "paper_s1": S.paper_s1s2(3, 6),
+    }
+    sc = S.intersection11(6, n_steps=70, n_acc=5, n_str=9, n_ped_v=4, n_ped_h=6)
+    sc.pair_mode, sc.ego, sc.name = S.EGO_ONLY, 2, "ego_only_ego2_n70"
+    out[sc.name] = sc
+    sc = S.intersection11(7, n_steps=30, n_acc=6, n_str=8, n_ped_v=3, n_ped_h=3)
+    sc.model, sc.name = S.MODEL_KIN, "kinematic"
+    out[sc.name] = sc
+    sc = S.intersection11(8, n_steps=1, n_acc=4, n_str=4, n_ped_v=3, n_ped_h=3)
+    sc.name = "one_step"
+    out[sc.name] = sc
+    return out
+
+
+_CACHE = {}
+SCENE_NAMES = ["tiny", "tiny_near", "mixed_small", "ragged", "ped_accel", "paper_s1", "ego_only_ego2_n70",
+               "kinematic", "one_step"]
+
+
+def scene(name):
+    if not _CACHE:
+        _CACHE.update(_scenes())
+    return _CACHE[name]
+
+
+@pytest.mark.parametrize("name", SCENE_NAMES)
+def test_generation_matches_oracle(mhc, ctx, orc, name):
+    sc = scene(name)
+    ref = orc.generate(sc)
+    p = mhc.generate(ctx, sc)
+    torch.cuda.synchronize()
+    g = {k: mhc.poses_by_trajectory(sc, p[k]).astype(np.float64) for k in ("x", "y", "c", "s")}
+    err = corner_error(sc, ref, g["x"], g["y"], g["c"], g["s"])
+    assert err < POSE_TOL, err
+
+
+def _oracle_poses_f32(orc, sc):
+    """Oracle poses rounded to FP32 (the GPU's storage format), as FP64 arrays for the oracle."""
+    ref = orc.generate(sc)
+    return {k: ref[k].astype(np.float32).astype(np.float64) for k in ("x", "y", "c", "s")}
+
+
+@pytest.mark.parametrize("name", SCENE_NAMES)
+def test_collision_kernel_on_oracle_poses(mhc, ctx, orc, name):
+    """The collision kernel alone: same FP32 poses on both sides; culled and unculled tables identical."""
+    sc = scene(name)
+    p32 = _oracle_poses_f32(orc, sc)
+    dev = {k: mhc.poses_to_device(sc, p32[k]) for k in p32}
+    tab_o, poff, pairs = orc.table(sc, p32)
+    ctx.set_option(mhc.MHC_OPT_CULL, 1)
+    t1 = mhc.detect(ctx, sc, dev).cpu().numpy()
+    ctx.set_option(mhc.MHC_OPT_CULL, 0)
+    t0 = mhc.detect(ctx, sc, dev).cpu().numpy()
+    ctx.set_option(mhc.MHC_OPT_CULL, 1)
+    assert np.array_equal(t0, t1)
+    check_table(orc, sc, t1, tab_o, p32, pairs, poff)
+
+
+@pytest.mark.parametrize("name", SCENE_NAMES)
+def test_pipeline_matches_oracle(mhc, ctx, orc, name):
+    """Generation + collision on the GPU against generation + table in the oracle."""
+    sc = scene(name)
+    ref = orc.generate(sc)
+    tab_o, poff, pairs = orc.table(sc, ref)
+    p = mhc.generate(ctx, sc)
+    t = mhc.detect(ctx, sc, p).cpu().numpy()
+    check_table(orc, sc, t, tab_o, ref, pairs, poff)
+
+
+@pytest.mark.parametrize("name", SCENE_NAMES)
+@pytest.mark.parametrize("weighted", [False, True])
+def test_risk_kernels_on_oracle_table(mhc, ctx, orc, name, weighted):
+    sc = scene(name)
+    ref = orc.generate(sc)
+    tab_o, poff, pairs = orc.table(sc, ref)
+    w = S.random_weights(sc, 77) if weighted else None
+    r_o = orc.risk(sc, tab_o, pairs, w)
+    dev_tab = torch.from_numpy(tab_o).cuda()
+    r_g = mhc.assess(ctx, sc, dev_tab, weights=w)
+    torch.cuda.synchronize()
+    check_risk(r_g, r_o, mhc.layout(sc)["h_ego"])
+
+
+def test_run_equals_separate_calls(mhc, ctx, orc):
+    sc = scene("mixed_small")
+    w = S.random_weights(sc, 5)
+    p = mhc.generate(ctx, sc)
+    t = mhc.detect(ctx, sc, p)
+    r1 = mhc.assess(ctx, sc, t, weights=w)
+    torch.cuda.synchronize()
+    r2 = mhc.run(ctx, sc, weights=w)
+    for k in r1:
+        a, b = r1[k].cpu().numpy(), r2[k].numpy()
+        if a.dtype.kind == "f":   # FP64 sums built with atomics: order-dependent in the last bits
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-18, err_msg=k)
+        else:
+            np.testing.assert_array_equal(a, b, err_msg=k)
+
+
+def test_deterministic_and_stream_independent(mhc, ctx):
+    sc = scene("mixed_small")
+    s2 = torch.cuda.Stream()
+    p = mhc.generate(ctx, sc)
+    t1 = mhc.detect(ctx, sc, p).clone()
+    with torch.cuda.stream(s2):
+        p2 = mhc.generate(ctx, sc, stream=s2)
+        t2 = mhc.detect(ctx, sc, p2, stream=s2)
+    s2.synchronize()
+    torch.cuda.synchronize()
+    for k in p:
+        assert torch.equal(p[k], p2[k])
+    assert torch.equal(t1, t2)
+
+
+def test_full_intersection11(mhc, ctx, orc):
+    """The 11-object intersection at full size (the benchmarked workload): the whole table and the risk
+    measures against the oracle."""
+    sc = S.intersection11(2)
+    ref = orc.generate(sc)
+    p = mhc.generate(ctx, sc)
+    torch.cuda.synchronize()
+    g = {k: mhc.poses_by_trajectory(sc, p[k]).astype(np.float64) for k in ("x", "y", "c", "s")}
+    assert corner_error(sc, ref, g["x"], g["y"], g["c"], g["s"]) < POSE_TOL
+    tab_o, poff, pairs = orc.table(sc, ref)
+    t = mhc.detect(ctx, sc, p)
+    t_host = t.cpu().numpy()
+    check_table(orc, sc, t_host, tab_o, ref, pairs, poff, n_tests=sc.n_tests())
+    r_g = mhc.assess(ctx, sc, torch.from_numpy(tab_o).cuda())
+    torch.cuda.synchronize()
+    check_risk(r_g, orc.risk(sc, tab_o, pairs), mhc.layout(sc)["h_ego"])
+    # and the GPU's own table through the GPU risk kernels equals the oracle risk when the tables agree
+    if np.array_equal(t_host, tab_o):
+        r_self = mhc.assess(ctx, sc, t)
+        torch.cuda.synchronize()
+        check_risk(r_self, orc.risk(sc, tab_o, pairs), mhc.layout(sc)["h_ego"])
+
+
+def test_stress32_sampled(mhc, orc):
+    """32 vehicles x 2048 hypotheses x 50 steps (1.04e11 pose tests, 4.2 GB table): sampled rows of every
+    object pair against the oracle."""
+    sc = S.stress32(4)
+    lay = mhc.layout(sc)
+    c = mhc.Context(0, 256 << 20)
+    try:
+        p = mhc.generate(c, sc)
+        table = torch.empty(lay["n_entries"], dtype=torch.int16, device="cuda")
+        mhc.detect(c, sc, p, table)
+        torch.cuda.synchronize()
+        ref = orc.generate(sc)
+        g = {k: mhc.poses_by_trajectory(sc, p[k]).astype(np.float64) for k in ("x", "y", "c", "s")}
+        assert corner_error(sc, ref, g["x"], g["y"], g["c"], g["s"]) < POSE_TOL
+        pairs = orc.pair_list(sc)
+        poff = orc.pair_offsets(sc)
+        off = orc.traj_offsets(sc)
+        rng = S.SplitMix64(99)
+        idx, oa, ta, ob, tb = [], [], [], [], []
+        for q, (a, b) in enumerate(pairs):
+            for _ in range(3):          # 3 sampled rows per object pair, every column
+                i = rng.randint(0, 2047)
+                cols = np.arange(2048)
+                idx.append(poff[q] + i * 2048 + cols)
+                oa.append(np.full(2048, a)); ob.append(np.full(2048, b))
+                ta.append(np.full(2048, off[a] + i)); tb.append(off[b] + cols)
+        idx = np.concatenate(idx)
+        tg = table[torch.from_numpy(idx).cuda()].cpu().numpy()
+        to = orc.first_steps(sc, ref, np.concatenate(oa), np.concatenate(ta), np.concatenate(ob), np.concatenate(tb))
+        check_table(orc, sc, tg, to, ref, pairs, poff, idx=idx)
+        assert (to >= 0).sum() > 0
+        del table
+    finally:
+        c.close()
+        torch.cuda.empty_cache()
+
+
+def test_counters_and_culling_work(mhc, ctx):
+    sc = S.intersection11(2)
+    p = mhc.generate(ctx, sc)
+    ctx.counters(reset=True)
+    mhc.detect(ctx, sc, p)
+    executed, narrow = ctx.counters(reset=True)
+    nominal = sc.n_tests()
+    assert 0 < narrow < executed < nominal
+
+
+def test_errors_leave_context_usable(mhc, ctx):
+    sc = scene("tiny")
+    bad = S.tiny_crossing(1)
+    bad.n_steps = 0
+    with pytest.raises(mhc.MhcError):
+        mhc.generate(ctx, bad, poses=mhc.alloc_poses(sc))
+    with pytest.raises(mhc.MhcError):
+        mhc.assess(ctx, sc, torch.zeros(256, dtype=torch.int16, device="cuda"),
+                   weights=[np.zeros(16), np.ones(16)])
+    p = mhc.generate(ctx, sc)
+    assert torch.isfinite(p["x"]).all()
