@@ -236,6 +236,25 @@ int mhc_run_bytes(const mhc_scenario *scen, size_t *bytes);
 int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, const mhc_risk *out,
             void *stream);
 
+/*
+ * Collision recognition without any allocation (no counterpart in the paper: it serves deployment).
+ * Same result as mhc_detect_collisions (same kernels, culling on) for callers that may not allocate memory
+ * while running -- real-time or safety controllers with a memory plan fixed at start-up, where an
+ * allocation can block, synchronise the device or fail at a deadline, and plugins whose host framework
+ * owns all device memory.  It takes no context and calls no cudaMalloc, cudaFree, cudaHostAlloc or host
+ * heap allocation.  Its scratch (scenario descriptors and per-tile bounding boxes) is one static device
+ * array of 8 MiB, created when the library is loaded and held by every GPU that loads it until the process
+ * exits.  Limits: at most 64 objects and 524,288 hypotheses, and descriptors + n_steps x
+ * ceil(h_a / 32) summed over objects x 16 bytes must fit in the 8 MiB; larger scenarios return
+ * MHC_E_INVALID with the needed size in mhc_last_error().  The device is the calling thread's current one;
+ * the first call on each device looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  Every call shares the one array (nothing in it needs to start at
+ * zero; each call rewrites what it reads): calls whose work overlaps on the GPU -- different streams
+ * without ordering, or several host threads -- race, and one host thread at a time may call it.
+ * poses / table / stream as for mhc_detect_collisions.
+ */
+int mhc_detect_collisions_static(const mhc_scenario *scen, const mhc_poses *poses, int16_t *table, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -409,6 +409,11 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
 
 }  // namespace
 
+namespace mhc {
+// Records the reason of a failure for mhc_last_error() (used by entry points in other files).
+void set_last_error(const char *why) { g_err = why ? why : ""; }
+}  // namespace mhc
+
 extern "C" {
 
 const char *mhc_status_string(int s) {
