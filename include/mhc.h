@@ -169,8 +169,8 @@ int mhc_collision_counters(mhc_ctx *ctx, uint64_t out[2], int reset, void *strea
 
 /* Kernel timing (mhc_set_option(ctx, MHC_OPT_PROFILE, 1)): the library records a CUDA event pair on the
    launching stream around every kernel it launches.  mhc_profile_read synchronises those events and
-   returns, per kernel class (MHC_K_GENERATE, MHC_K_BOUNDS, MHC_K_COLLIDE, MHC_K_RISK: the risk chain of
-   four kernels counts as one class with four launches), the summed milliseconds and the launch counts
+   returns, per kernel class (MHC_K_GENERATE; MHC_K_BOUNDS = the table fill and the tile-bounds kernel;
+   MHC_K_COLLIDE; MHC_K_RISK = the risk chain of four kernels), the summed milliseconds and the launch counts
    since the last reset; reset != 0 clears them.  Disabled by default (no events recorded). */
 #define MHC_OPT_PROFILE 2
 enum { MHC_K_GENERATE = 0, MHC_K_BOUNDS = 1, MHC_K_COLLIDE = 2, MHC_K_RISK = 3, MHC_K_COUNT = 4 };

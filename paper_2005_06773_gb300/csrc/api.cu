@@ -45,7 +45,9 @@ struct Layout {
     std::vector<ObjDesc> objs;
     std::vector<PairDesc> pairs;
     std::vector<float> grids;
-    std::vector<int> warp_obj, warp_first;
+    std::vector<int> warp_obj, warp_first;          // 32-hypothesis bound tiles
+    std::vector<int> gen_obj, gen_first;            // generation warp tasks of gen_lanes hypotheses
+    int gen_lanes = 32;
     long long n_traj = 0, n_entries = 0, n_tiles = 0;
     int n_tiles32 = 0, h_e = 0;
 };
@@ -55,8 +57,8 @@ int build_layout(const mhc_scenario *sc, Layout &L) {
     if (sc->n_objects < 1 || sc->n_objects > MHC_MAX_OBJECTS || !sc->objects)
         return fail(MHC_E_INVALID, "n_objects must be in [1, 4096] with a non-NULL objects array");
     if (sc->n_steps < 1 || sc->n_steps > MHC_MAX_STEPS) return fail(MHC_E_INVALID, "n_steps must be in [1, 32767]");
-    if (sc->substeps < 1 || (long long)sc->n_steps * sc->substeps > (1LL << 31))
-        return fail(MHC_E_INVALID, "substeps must be >= 1 with n_steps * substeps <= 2^31");
+    if (sc->substeps < 1 || (long long)sc->n_steps * sc->substeps >= (1LL << 31))
+        return fail(MHC_E_INVALID, "substeps must be >= 1 with n_steps * substeps < 2^31");
     if (!(sc->tau > 0.f) || !finite(sc->tau)) return fail(MHC_E_INVALID, "tau must be positive and finite");
     if (sc->pair_mode != MHC_ALL_PAIRS && sc->pair_mode != MHC_EGO_ONLY) return fail(MHC_E_INVALID, "bad pair_mode");
     if (sc->ego < 0 || sc->ego >= sc->n_objects) return fail(MHC_E_INVALID, "ego out of range");
@@ -144,6 +146,19 @@ int build_layout(const mhc_scenario *sc, Layout &L) {
     return MHC_OK;
 }
 
+// Generation warp tasks: a hypothesis is a sequential chain of sub-steps, so with fewer hypotheses than
+// warp schedulers (4 per SM) each warp takes fewer of them (down to 4) to occupy every scheduler.
+void plan_generation(Layout &L, int n_sm) {
+    const long long schedulers = 4LL * (n_sm > 0 ? n_sm : 152);
+    int lanes = 32;
+    while (lanes > 4 && (L.n_traj + lanes - 1) / lanes < schedulers) lanes >>= 1;
+    L.gen_lanes = lanes;
+    L.gen_obj.clear();
+    L.gen_first.clear();
+    for (int o = 0; o < L.n_obj; ++o)
+        for (int q = 0; q < L.objs[o].h; q += lanes) { L.gen_obj.push_back(o); L.gen_first.push_back(q); }
+}
+
 // Device scratch each call needs (besides caller buffers).
 struct Scratch {
     size_t desc = 0, bounds = 0, prob = 0, acc = 0, weights = 0, total = 0;
@@ -152,13 +167,15 @@ struct Scratch {
 
 Scratch scratch_of(const Layout &L, bool with_weights) {
     Scratch s;
+    const size_t gen_tasks = (size_t)L.n_traj / 4 + L.objs.size();   // the most generation tasks (4 lanes)
     s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
-             align_up(sizeof(float) * L.grids.size()) + 2 * align_up(sizeof(int) * L.warp_obj.size());
+             align_up(sizeof(float) * L.grids.size()) + 2 * align_up(sizeof(int) * L.warp_obj.size()) +
+             2 * align_up(sizeof(int) * gen_tasks);
     s.bounds = align_up(sizeof(float4) * (size_t)L.n_tiles32 * L.N);
-    s.prob = align_up(sizeof(double) * (size_t)L.n_traj);
+    s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj);
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
     const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
-    s.acc_words = np + np * N + np + np * N + he + he + he * N * no + he * no + no + N + 4;
+    s.acc_words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4;
     s.acc = align_up(8 * (size_t)s.acc_words);
     s.total = s.desc + s.weights + s.bounds + s.prob + s.acc;
     return s;
@@ -179,6 +196,7 @@ struct mhc_ctx {
     cudaStream_t last_stream = nullptr;
     bool has_last = false;
     int cull = 1;
+    int n_sm = 152;
     unsigned long long *counters = nullptr;
     // kernel timing
     bool profile = false;
@@ -254,6 +272,7 @@ struct DevDesc {
     PairDesc *pairs;
     float *grids;
     int *warp_obj, *warp_first;
+    int *gen_obj, *gen_first;
     float *weights;
 };
 
@@ -265,9 +284,12 @@ int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, cha
         {L.grids.data(), sizeof(float) * L.grids.size()},
         {L.warp_obj.data(), sizeof(int) * L.warp_obj.size()},
         {L.warp_first.data(), sizeof(int) * L.warp_first.size()},
+        {L.gen_obj.data(), sizeof(int) * L.gen_obj.size()},
+        {L.gen_first.data(), sizeof(int) * L.gen_first.size()},
     };
-    size_t caps[5] = {align_up(parts[0].second), align_up(sizeof(PairDesc) * (L.pairs.size() + 1)),
-                      align_up(parts[2].second), align_up(parts[3].second), align_up(parts[4].second)};
+    size_t caps[7] = {align_up(parts[0].second), align_up(sizeof(PairDesc) * (L.pairs.size() + 1)),
+                      align_up(parts[2].second), align_up(parts[3].second), align_up(parts[4].second),
+                      align_up(parts[5].second), align_up(parts[6].second)};
     size_t total = 0;
     for (size_t c : caps) total += c;
     const size_t wbytes = weights ? align_up(sizeof(float) * weights->size()) : 0;
@@ -285,13 +307,13 @@ int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, cha
     }
     char *h = static_cast<char *>(ctx->stage[s]);
     size_t off = 0;
-    char *ptrs[6];
-    for (int q = 0; q < 5; ++q) {
+    char *ptrs[8];
+    for (int q = 0; q < 7; ++q) {
         if (parts[q].second) std::memcpy(h + off, parts[q].first, parts[q].second);
         ptrs[q] = dev + off;
         off += caps[q];
     }
-    ptrs[5] = dev + off;
+    ptrs[7] = dev + off;
     if (weights && !weights->empty()) std::memcpy(h + off, weights->data(), sizeof(float) * weights->size());
     off += wbytes;
     MHC_CUDA(cudaMemcpyAsync(dev, h, off, cudaMemcpyHostToDevice, st));
@@ -303,7 +325,9 @@ int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, cha
     out.grids = reinterpret_cast<float *>(ptrs[2]);
     out.warp_obj = reinterpret_cast<int *>(ptrs[3]);
     out.warp_first = reinterpret_cast<int *>(ptrs[4]);
-    out.weights = weights ? reinterpret_cast<float *>(ptrs[5]) : nullptr;
+    out.gen_obj = reinterpret_cast<int *>(ptrs[5]);
+    out.gen_first = reinterpret_cast<int *>(ptrs[6]);
+    out.weights = weights ? reinterpret_cast<float *>(ptrs[7]) : nullptr;
     return MHC_OK;
 }
 
@@ -343,9 +367,9 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
                const mhc_poses *coll_in, int16_t *table, bool risk, const mhc_risk *rout, cudaStream_t st) {
     if (gen_out) {
         GenArgs g;
-        g.objs = D.objs; g.grids = D.grids; g.warp_obj = D.warp_obj; g.warp_first = D.warp_first;
-        g.n_warps = (int)L.warp_obj.size(); g.n_steps = L.N; g.substeps = L.K; g.model = L.model;
-        g.tau = L.tau; g.tau_d = (double)L.tau;
+        g.objs = D.objs; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
+        g.n_warps = (int)L.gen_obj.size(); g.lanes = L.gen_lanes; g.n_steps = L.N; g.substeps = L.K; g.model = L.model;
+        g.tau = L.tau; g.tau_i_d = (double)L.tau / (double)L.K;
         g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
         cudaError_t e = launch_generate(g, st);
@@ -354,13 +378,18 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     if (coll_in) {
         float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_tiles32 * L.N));
         if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
-        if (ctx->cull) {
-            BoundsArgs b;
-            b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
-            b.n_warps = (int)L.warp_obj.size(); b.n_steps = L.N; b.x = coll_in->x; b.y = coll_in->y; b.bounds = bounds;
-            TimedScope ts(ctx, st, MHC_K_BOUNDS, 1);
-            cudaError_t e = launch_bounds(b, st);
-            if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
+        {
+            TimedScope ts(ctx, st, MHC_K_BOUNDS, ctx->cull ? 2 : 1);
+            cudaError_t e = launch_fill_table(table, L.n_entries, st);
+            if (e != cudaSuccess) return cuda_fail(e, "table fill launch");
+            if (ctx->cull) {
+                BoundsArgs b;
+                b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
+                b.n_warps = (int)L.warp_obj.size(); b.n_steps = L.N; b.x = coll_in->x; b.y = coll_in->y;
+                b.bounds = bounds;
+                e = launch_bounds(b, st);
+                if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
+            }
         }
         CollideArgs c;
         c.objs = D.objs; c.pairs = D.pairs; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
@@ -378,22 +407,22 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         r.n_steps = L.N; r.ego = L.ego; r.h_e = L.h_e; r.n_tiles = L.n_tiles; r.table = table;
         r.weights = D.weights;
         r.prob = static_cast<double *>(bump.take(sizeof(double) * (size_t)L.n_traj));
+        r.probf = static_cast<float *>(bump.take(sizeof(float) * (size_t)L.n_traj));
         const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
-        const long long words = np + np * N + np + np * N + he + he + he * N * no + he * no + no + N + 4;
+        const long long words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4;
         unsigned long long *w = static_cast<unsigned long long *>(bump.take(8 * (size_t)words));
-        if (!r.prob || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
+        if (!r.prob || !r.probf || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
         RiskScratch &A = r.acc;
         A.base = w; A.n_words = words;
         A.count = w; w += np;
         A.count_k = w; w += np * N;
-        A.P = reinterpret_cast<double *>(w); w += np;
-        A.H = reinterpret_cast<double *>(w); w += np * N;
-        A.naive = reinterpret_cast<double *>(w); w += he;
+        A.P = w; w += np;
+        A.H = w; w += np * N;
         A.hits = w; w += he;
-        A.logq = reinterpret_cast<double *>(w); w += he * N * no;
-        A.mass = reinterpret_cast<double *>(w); w += he * no;
-        A.attr_obj = reinterpret_cast<double *>(w); w += no;
-        A.attr_step = reinterpret_cast<double *>(w); w += N;
+        A.lsum = w; w += he * N * no;
+        A.mass = w; w += he * no;
+        A.attr_obj = w; w += no;
+        A.attr_step = w; w += N;
         A.scalars = reinterpret_cast<double *>(w);
         r.count = reinterpret_cast<long long *>(rout->count);
         r.count_k = reinterpret_cast<long long *>(rout->count_k);
@@ -445,6 +474,7 @@ int mhc_create(mhc_ctx **out, int device, void *arena, size_t arena_bytes) {
     mhc_ctx *c = new mhc_ctx();
     c->device = device;
     c->arena_bytes = arena_bytes;
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) c->n_sm = 152;
     if (arena) {
         c->arena = static_cast<char *>(arena);
     } else {
@@ -558,6 +588,7 @@ int mhc_generate_trajectories(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_
     if (!out || !out->x || !out->y || !out->c || !out->s) return fail(MHC_E_INVALID, "pose planes must be non-NULL");
     Layout L;
     if (int r = build_layout(scen, L)) return r;
+    plan_generation(L, ctx->n_sm);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Scratch S = scratch_of(L, false);
     Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
@@ -627,6 +658,7 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     if (!out) return fail(MHC_E_INVALID, "out is NULL");
     Layout L;
     if (int r = build_layout(scen, L)) return r;
+    plan_generation(L, ctx->n_sm);
     std::vector<float> w;
     if (int r = gather_weights(L, traj_weights, w)) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -12,21 +12,12 @@
 namespace mhc {
 namespace {
 
-// Error-free sum (Knuth's two-sum): s + e == a + b exactly.
-__device__ __forceinline__ float two_sum(float a, float b, float &e) {
-    const float s = __fadd_rn(a, b);
-    const float bp = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
-    return s;
-}
-
-// (hi, lo) += d, renormalised so that |lo| <= ulp(hi) / 2; hi + lo carries the running sum.
-__device__ __forceinline__ void acc2(float &hi, float &lo, float d) {
-    float e;
-    const float s = two_sum(hi, d, e);
-    const float t = __fadd_rn(lo, e);
-    hi = __fadd_rn(s, t);
-    lo = __fsub_rn(t, __fsub_rn(hi, s));
+// Kahan summation: (hi, c) carries the running sum hi - c; c is the compensation of the lost low part.
+__device__ __forceinline__ void kahan_add(float &hi, float &c, float d) {
+    const float y = __fsub_rn(d, c);
+    const float t = __fadd_rn(hi, y);
+    c = __fsub_rn(__fsub_rn(t, hi), y);
+    hi = t;
 }
 
 // sin / cos of the angle (a_hi + a_lo) to first order in the small part a_lo.
@@ -37,110 +28,140 @@ __device__ __forceinline__ void sincos2(float a_hi, float a_lo, float &sn, float
     sn = fmaf(c0, a_lo, s0);
 }
 
-__device__ __forceinline__ double speed_at(double v0, double dv, long long n) {
+// sin / cos by the Taylor series to x^9 / x^10 (|x| <= 0.5: error < 2e-11), sincosf beyond.
+__device__ __forceinline__ void sincos_half(float x, float &sn, float &cs) {
+    if (fabsf(x) > 0.5f) {
+        sincosf(x, &sn, &cs);
+        return;
+    }
+    const float x2 = x * x;
+    float ps = fmaf(x2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    ps = fmaf(x2, ps, 1.0f / 120.0f);
+    ps = fmaf(x2, ps, -1.0f / 6.0f);
+    sn = fmaf(x * x2, ps, x);
+    float pc = fmaf(x2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    pc = fmaf(x2, pc, -1.0f / 720.0f);
+    pc = fmaf(x2, pc, 1.0f / 24.0f);
+    pc = fmaf(x2, pc, -0.5f);
+    cs = fmaf(x2, pc, 1.0f);
+}
+
+// sin / cos by the Taylor series to x^5 / x^6 (|x| <= 0.1: error < 3e-11), sincosf beyond.
+__device__ __forceinline__ void sincos_tenth(float x, float &sn, float &cs) {
+    if (fabsf(x) > 0.1f) {
+        sincosf(x, &sn, &cs);
+        return;
+    }
+    const float x2 = x * x;
+    sn = fmaf(x * x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), x);
+    cs = fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f), 1.0f);
+}
+
+__device__ __forceinline__ double speed_at(double v0, double dv, int n) {
     return __dadd_rn(v0, __dmul_rn((double)n, dv));
 }
 
-// Smallest n in [lo, hi] for which pred(n) holds, pred monotone false..true; hi if none below it.
+// Smallest n in [0, NK] with pred(n) (pred monotone false..true; NK if it never holds before NK), found
+// from an FP32 estimate and settled by evaluating the FP64 predicate next to it.
 template <class P>
-__device__ long long first_true(long long lo, long long hi, P pred) {
-    while (lo < hi) {
-        long long mid = lo + ((hi - lo) >> 1);
-        if (pred(mid)) hi = mid; else lo = mid + 1;
-    }
-    return lo;
+__device__ int first_true(int NK, float estimate, P pred) {
+    int n = estimate <= 0.0f ? 0 : (estimate >= (float)NK ? NK : (int)ceilf(estimate));
+    while (n > 0 && pred(n - 1)) --n;
+    while (n < NK && !pred(n)) ++n;
+    return n;
 }
 
-__device__ void vehicle(const ObjDesc &o, float acc, float delta, int model, int N, int K, float tau,
-                        double tau_d, long long base, int h, int i, float *X, float *Y, float *C, float *S) {
-    const double tau_i_d = __ddiv_rn(tau_d, (double)K);
+__device__ void vehicle(const ObjDesc &o, float acc, float delta, int model, int N, int K, double tau_i_d,
+                        long long base, int h, int i, float *X, float *Y, float *C, float *S) {
     const double dv_d = __dmul_rn((double)acc, tau_i_d);
     const double v0_d = (double)o.v0;
-    const long long NK = (long long)N * K;
-    // low-speed regime: sub-steps with v_n < kVMin (prefix if accelerating, suffix if braking)
-    long long low_lo = 0, low_hi = 0;   // low regime on [low_lo, low_hi)
+    const int NK = N * K;
+    const float dvf = (float)dv_d;
+    // low-speed regime: sub-steps with v_n < kVMin (a prefix when accelerating, a suffix when braking)
+    int low_lo = 0, low_hi = 0;   // low regime on [low_lo, low_hi)
     if (model == kModelKin) {
-        low_lo = 0; low_hi = NK;
+        low_hi = NK;
     } else if (acc > 0.0f) {
-        low_hi = first_true(0, NK, [&](long long n) { return speed_at(v0_d, dv_d, n) >= kVMinD; });
+        low_hi = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) >= kVMinD; });
     } else if (acc < 0.0f) {
-        low_lo = first_true(0, NK, [&](long long n) { return speed_at(v0_d, dv_d, n) < kVMinD; });
+        low_lo = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) < kVMinD; });
         low_hi = NK;
     } else if (v0_d < kVMinD) {
         low_hi = NK;
     }
-    long long n_stop = NK;   // sub-step at which v_{n+1} < 0 first holds
-    if (acc < 0.0f) n_stop = first_true(0, NK, [&](long long n) { return speed_at(v0_d, dv_d, n + 1) < 0.0; });
+    int n_stop = NK;   // sub-step at which v_{n+1} < 0 first holds
+    if (acc < 0.0f)
+        n_stop = first_true(NK, -o.v0 / dvf - 1.0f, [&](int n) { return speed_at(v0_d, dv_d, n + 1) < 0.0; });
 
     const float ti = (float)tau_i_d;
     const float hti2 = 0.5f * ti * ti;
-    const float dv = acc * ti;
+    const float dv = dvf;
     const float L = o.lf + o.lr;
     const float inv_m = 1.0f / o.m, inv_iz = 1.0f / o.Iz;
     const float k11 = -(o.caf + o.car) * inv_m;                 // a11 * v
     const float k12 = (o.car * o.lr - o.caf * o.lf) * inv_m;    // (a12 + 1) * v^2
     const float k21 = (o.car * o.lr - o.caf * o.lf) * inv_iz;   // a21
     const float k22 = -(o.caf * o.lf * o.lf + o.car * o.lr * o.lr) * inv_iz;  // a22 * v
-    const float kb1 = o.caf * inv_m;                            // b1 * v
-    const float kb2 = o.caf * o.lf * inv_iz;                    // b2
+    const float kb1 = o.caf * inv_m * delta;                    // b1 * v * delta
+    const float kb2 = o.caf * o.lf * inv_iz * delta;            // b2 * delta
     const float tdel = tanf(delta);
     const float beta_kin = atanf(o.lr * tdel / L);
     const float kappa = cosf(beta_kin) * tdel / L;              // r = v * kappa in the kinematic limit
+    const float stop_den = 0.5f / fabsf(acc == 0.0f ? 1.0f : acc);
 
-    float xh = o.x0, xl = 0.0f, yh = o.y0, yl = 0.0f, ph = o.psi0, pl = 0.0f;
+    float xh = o.x0, xc = 0.0f, yh = o.y0, yc = 0.0f, ph = o.psi0, pc = 0.0f;   // Kahan sums
+    float cps, sps;                      // cos / sin of the heading, carried between output steps
+    sincos2(ph, -pc, sps, cps);
     float beta = 0.0f, r = 0.0f, ax = acc, ay = 0.0f;
     bool stopped = false;
-    long long n = 0;
+    int n = 0;
     for (int k = 0; k < N; ++k) {
         for (int q = 0; q < K; ++q, ++n) {
-            if (stopped) continue;
+            // every lane runs the same straight-line sub-step; regime and stop act through selects
+            const bool low = n >= low_lo && n < low_hi;
+            const bool stop_now = n == n_stop;
             const float v = fmaf((float)n, dv, o.v0);
-            float bd, rd;
-            if (n >= low_lo && n < low_hi) {
-                beta = beta_kin;
-                r = v * kappa;
-                bd = 0.0f;
-                rd = 0.0f;
-            } else {
-                const float iv = 1.0f / v;
-                bd = k11 * iv * beta + (k12 * iv * iv - 1.0f) * r + kb1 * iv * delta;
-                rd = k21 * beta + k22 * iv * r + kb2 * delta;
-            }
-            float spb, cpb, e_pb;
-            const float pb = two_sum(ph, beta, e_pb);             // course angle psi + beta, split exactly
-            sincos2(pb, __fadd_rn(e_pb, pl), spb, cpb);
-            if (n == n_stop) {
-                const float d = v * v / (2.0f * fabsf(acc));
-                acc2(xh, xl, cpb * d);
-                acc2(yh, yl, spb * d);
-                stopped = true;
-                continue;
-            }
-            float spc, cpc;
-            sincos2(ph, pl, spc, cpc);
-            const float dx = cpb * v * ti + (cpc * ax - spc * ay) * hti2;
-            const float dy = spb * v * ti + (spc * ax + cpc * ay) * hti2;
+            const float iv = __fdividef(1.0f, fmaxf(v, 1e-3f));
+            const float bd_ot = fmaf(k11 * iv, beta, fmaf(fmaf(k12 * iv, iv, -1.0f), r, kb1 * iv));
+            const float rd_ot = fmaf(k21, beta, fmaf(k22 * iv, r, kb2));
+            const float b_use = low ? beta_kin : beta;
+            const float r_use = low ? v * kappa : r;
+            const float bd = low ? 0.0f : bd_ot;
+            const float rd = low ? 0.0f : rd_ot;
             float sb, cb;
-            sincosf(beta, &sb, &cb);
-            const float w = v * (bd + r);
-            const float ax_n = cb * acc - sb * w;
-            const float ay_n = sb * acc + cb * w;
-            const float dpsi = r * ti + rd * hti2;
-            beta = fmaf(bd, ti, beta);
-            r = fmaf(rd, ti, r);
-            ax = ax_n;
-            ay = ay_n;
-            acc2(xh, xl, dx);
-            acc2(yh, yl, dy);
-            acc2(ph, pl, dpsi);
+            sincos_half(b_use, sb, cb);
+            const float cpb = fmaf(cps, cb, -sps * sb);          // course angle psi + beta
+            const float spb = fmaf(sps, cb, cps * sb);
+            const float d_stop = v * v * stop_den;
+            const float dx = stop_now ? cpb * d_stop : fmaf(cpb * v, ti, fmaf(cps, ax, -sps * ay) * hti2);
+            const float dy = stop_now ? spb * d_stop : fmaf(spb * v, ti, fmaf(sps, ax, cps * ay) * hti2);
+            const float w = v * (bd + r_use);
+            const float ax_n = fmaf(cb, acc, -sb * w);
+            const float ay_n = fmaf(sb, acc, cb * w);
+            const float dpsi = fmaf(r_use, ti, rd * hti2);
+            const bool move = !stopped && !stop_now;             // a state update beyond the position
+            kahan_add(xh, xc, stopped ? 0.0f : dx);
+            kahan_add(yh, yc, stopped ? 0.0f : dy);
+            kahan_add(ph, pc, move ? dpsi : 0.0f);
+            if (move) {
+                beta = fmaf(bd, ti, b_use);
+                r = fmaf(rd, ti, r_use);
+                ax = ax_n;
+                ay = ay_n;
+                float sd, cd;                                   // rotate (cos, sin) of the heading by dpsi
+                sincos_tenth(dpsi, sd, cd);
+                const float c2 = fmaf(cps, cd, -sps * sd);
+                sps = fmaf(sps, cd, cps * sd);
+                cps = c2;
+            }
+            stopped = stopped || stop_now;
         }
-        float sp, cp;
-        sincos2(ph, pl, sp, cp);
+        sincos2(ph, -pc, sps, cps);                              // re-anchor on the exact heading
         const long long idx = base + (long long)k * h + i;
-        X[idx] = xh + xl;
-        Y[idx] = yh + yl;
-        C[idx] = cp;
-        S[idx] = sp;
+        X[idx] = xh - xc;
+        Y[idx] = yh - yc;
+        C[idx] = cps;
+        S[idx] = sps;
     }
 }
 
@@ -173,7 +194,7 @@ __device__ void pedestrian(const ObjDesc &o, float ga, float gb, int N, float ta
 
 __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= a.n_warps) return;
+    if (w >= a.n_warps || (threadIdx.x & 31) >= a.lanes) return;
     const ObjDesc &o = a.objs[a.warp_obj[w]];
     const int i = a.warp_first[w] + (threadIdx.x & 31);
     if (i >= o.h) return;
@@ -181,7 +202,7 @@ __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
     const float ga = a.grids[o.grid_off + ia];
     const float gb = a.grids[o.grid_off + o.n_a + ib];
     if (o.kind == kVehicle)
-        vehicle(o, ga, gb, a.model, a.n_steps, a.substeps, a.tau, a.tau_d, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
+        vehicle(o, ga, gb, a.model, a.n_steps, a.substeps, a.tau_i_d, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
     else
         pedestrian(o, ga, gb, a.n_steps, a.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
 }
@@ -216,7 +237,7 @@ __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
 
 cudaError_t launch_generate(const GenArgs &a, cudaStream_t st) {
     if (a.n_warps <= 0) return cudaSuccess;
-    // few hypotheses: one warp per block so that the latency-bound integration spreads over all SMs
+    // few warps: one warp per block so that the latency-bound integration spreads over all SMs
     const int warps_per_block = a.n_warps < 4 * 152 ? 1 : 4;
     const int blocks = (a.n_warps + warps_per_block - 1) / warps_per_block;
     gen_kernel<<<blocks, 32 * warps_per_block, 0, st>>>(a);

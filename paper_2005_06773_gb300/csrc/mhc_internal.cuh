@@ -54,12 +54,14 @@ struct PairDesc {
 struct GenArgs {
     const ObjDesc *objs;
     const float *grids;
-    const int *warp_obj;      // object of each 32-hypothesis warp task
+    const int *warp_obj;      // object of each warp task
     const int *warp_first;    // first hypothesis of each warp task
     int n_warps;
+    int lanes;                // hypotheses per warp task (1..32): fewer than 32 spreads small workloads
+                              // over more warp schedulers, since each hypothesis is a sequential chain
     int n_steps, substeps, model;
     float tau;
-    double tau_d;
+    double tau_i_d;           // (double)tau / substeps, the sub-step of the speed recurrence
     float *x, *y, *c, *s;
 };
 
@@ -84,16 +86,21 @@ struct CollideArgs {
     unsigned long long *counters;  // optional: [0] broad-phase tests executed, [1] narrow-phase tests
 };
 
-// Risk accumulators: one contiguous block of 8-byte words, zeroed before every assessment.
+// Risk accumulators: one contiguous block of 64-bit words, zeroed before every assessment.  Masses and
+// log-survival sums are unsigned fixed point (kFixProb / kFixLog fractional bits): every term is an FP32
+// value converted exactly, and integer atomics add them exactly and in any order.
+constexpr int kFixProb = 62;   // probability masses: every accumulated sum is at most 1
+constexpr int kFixLog = 40;    // sums of -log(1 - p): each term capped at 2^22
+
 struct RiskScratch {
     unsigned long long *count;     // [n_pairs]
     unsigned long long *count_k;   // [n_pairs * N]
-    double *P, *H;                 // [n_pairs], [n_pairs * N]
-    double *naive;                 // [h_e]
-    unsigned long long *hits;      // [h_e]
-    double *logq;                  // [h_e * N * n_obj]: sum of log(1 - p_b[j]) over entries (i, b, j) at step k
-    double *mass;                  // [h_e * n_obj]:     sum of p_b[j] over colliding entries (i, b, j)
-    double *attr_obj, *attr_step;  // [n_obj], [N]
+    unsigned long long *P, *H;     // [n_pairs], [n_pairs * N]        sum p_a[i] p_b[j]
+    unsigned long long *hits;      // [h_e]                            colliding (b, j) per EGO hypothesis
+    unsigned long long *lsum;      // [h_e * N * n_obj]                sum -log(1 - p_b[j]) per (i, k, b) cell
+    unsigned long long *mass;      // [h_e * n_obj]                    sum p_b[j] per (i, b)
+    unsigned long long *attr_obj;  // [n_obj]
+    unsigned long long *attr_step; // [N]
     double *scalars;               // [4]
     unsigned long long *base;      // first word of the block
     long long n_words;             // words to zero
@@ -107,6 +114,7 @@ struct RiskArgs {
     const int16_t *table;
     const float *weights;          // [n_traj] raw non-negative weights, or null for uniform
     double *prob;                  // [n_traj] normalised probabilities (scratch)
+    float *probf;                  // [n_traj] the same rounded to FP32 (the per-hit arithmetic)
     RiskScratch acc;
     // outputs (device); any may be null
     long long *count, *count_k;
@@ -119,7 +127,8 @@ struct RiskArgs {
 
 cudaError_t launch_generate(const GenArgs &a, cudaStream_t st);
 cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st);
-cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);
+cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st);   // table[0, n) = -1
+cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);               // stores first hits only
 cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st);
 
 }  // namespace mhc

@@ -3,20 +3,47 @@
 //   prepare  zero the accumulators; L1-normalise each object's weights into probabilities (Section IV-D.1)
 //   scan     one CTA per 64 x 64 table tile (the collision tiling): counts, first-step histograms and
 //            probability masses per object pair (Eq. totalCrashProb per pair); for pairs containing the
-//            EGO object also per-EGO-hypothesis naive mass, hit counts and, per (step, CO object), the sum
-//            of log(1 - p) that the chronological scaling needs
-//   ego      one thread per EGO hypothesis walks (step, object) cells in ascending order: a cell whose
-//            entries have survival product Q = exp(sum log(1 - p)) contributes S (1 - Q) and leaves
-//            S Q, which is exactly the entry-by-entry scaling of Eq. p21 summed over the cell
-//            (telescoping); plus the per-object independence measure and the scalar totals
-//   finish   escape routes ranked by probability (Section VI-A) and the copy of totals to the outputs
-// Probabilities and masses accumulate in FP64 (only colliding entries touch them).
+//            EGO object also per-EGO-hypothesis hit counts, per-(hypothesis, CO object) masses and, per
+//            (hypothesis, step, CO object) cell, the sum of -log(1 - p) over the cell's entries
+//   ego      one warp per EGO hypothesis walks the cells in ascending (step, object) order: a cell with
+//            survival factor 1 - q = exp(-sum) contributes S q and leaves S (1 - q), S being the survival
+//            product of the earlier cells -- exactly the entry-by-entry scaling of Eq. p21 summed over
+//            the cell (telescoping); plus the per-object independence measure and the scalar totals
+//   finish   escape routes ranked by probability (Section VI-A) and the conversion of the totals
+//
+// Collisions are rare and scattered inside a warp, so the per-hit work uses only FP32 and integer
+// instructions: each term (p_a p_b, p, -log(1 - p)) is formed in FP32 and added exactly as unsigned
+// 64-bit fixed point by integer atomics (exact, order-independent, bitwise reproducible).  FP64 -- a
+// narrow pipe on this GPU -- runs only in dense per-warp steps.
 #include "mhc_internal.cuh"
 
 namespace mhc {
 namespace {
 
 constexpr int kMaxSmemSteps = 1024;
+constexpr int kMaxSmemCells = 256;           // 64 x 256 cells x 8 B = 128 KiB of dynamic shared memory
+constexpr float kMaxLogTerm = 4194304.0f;    // 2^22: -log(1 - p) for p = 1 (a certain trajectory)
+
+// Exact unsigned fixed point of a finite w >= 0 with `frac` fractional bits (round to nearest).
+__device__ __forceinline__ unsigned long long to_fixed(float w, int frac) {
+    const unsigned b = __float_as_uint(w);
+    const int e = (int)(b >> 23);
+    if (e == 0) return 0ull;                 // zero (and denormals, below 2^-126)
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+    const int sh = e - 150 + frac;           // w = m 2^(e - 150)
+    if (sh >= 0) return m << sh;
+    if (sh <= -25) return 0ull;
+    return (m + (1ull << (-sh - 1))) >> -sh;
+}
+
+__device__ __forceinline__ double from_fixed(unsigned long long v, int frac) {
+    return __ull2double_rn(v) * exp2((double)-frac);
+}
+
+// -log(1 - p) in FP32, capped for p -> 1
+__device__ __forceinline__ float neg_log_survival(float p) {
+    return p >= 1.0f ? kMaxLogTerm : fminf(-log1pf(-p), kMaxLogTerm);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -49,13 +76,17 @@ __global__ void __launch_bounds__(256) prepare_kernel(const RiskArgs a) {
     } else {
         sum = (double)o.h;
     }
-    for (int i = threadIdx.x; i < o.h; i += blockDim.x)
-        a.prob[o.traj_off + i] = (a.weights ? (double)a.weights[o.traj_off + i] : 1.0) / sum;
+    for (int i = threadIdx.x; i < o.h; i += blockDim.x) {
+        const double p = (a.weights ? (double)a.weights[o.traj_off + i] : 1.0) / sum;
+        a.prob[o.traj_off + i] = p;
+        a.probf[o.traj_off + i] = (float)p;
+    }
 }
 
 __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
-    extern __shared__ unsigned char s_dyn[];
-    __shared__ double s_row_mass[kTile];
+    // dynamic: [N] u64 masses | [N] u32 counts | [64][N] u64 log-survival cells of the tile's EGO hypotheses
+    extern __shared__ unsigned long long s_dyn64[];
+    __shared__ unsigned long long s_row_mass[kTile];
     __shared__ unsigned s_row_hits[kTile];
     const long long g = blockIdx.x;
     if (g >= a.n_tiles) return;
@@ -75,50 +106,63 @@ __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
     const int tid = threadIdx.x;
     const int N = a.n_steps;
     const bool smem_hist = N <= kMaxSmemSteps;
-    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_dyn);
-    double *s_H = reinterpret_cast<double *>(s_dyn + sizeof(unsigned) * ((N + 1) & ~1));
+    unsigned long long *s_H = s_dyn64;
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_dyn64 + N);
+    unsigned long long *s_L = s_dyn64 + N + (N + 1) / 2;
+    const bool smem_cells = smem_hist && N <= kMaxSmemCells && P.ego_side >= 0;
     if (smem_hist)
-        for (int k = tid; k < N; k += 64) { s_cnt[k] = 0u; s_H[k] = 0.0; }
-    s_row_mass[tid] = 0.0;
+        for (int k = tid; k < N; k += 64) { s_cnt[k] = 0u; s_H[k] = 0ull; }
+    if (smem_cells)
+        for (int q = tid; q < kTile * N; q += 64) s_L[q] = 0ull;
+    s_row_mass[tid] = 0ull;
     s_row_hits[tid] = 0u;
     __syncthreads();
 
     const int j = tid;
     const bool col_ok = j < cols;
-    const double pb = col_ok ? a.prob[B.traj_off + j0 + j] : 0.0;
-    const double lq_b = col_ok ? log1p(-pb) : 0.0;
-    unsigned long long cnt = 0;
-    double pm = 0.0, col_mass = 0.0;
+    const float pb = col_ok ? a.probf[B.traj_off + j0 + j] : 0.0f;
+    unsigned long long cnt = 0, pm = 0, col_mass = 0;
     unsigned col_hits = 0;
     if (col_ok) {
         const int16_t *row = a.table + P.off + (long long)i0 * B.h + j0 + j;
-        for (int i = 0; i < rows; ++i) {
-            const int T = row[(long long)i * B.h];
-            if (T < 0 || T >= N) continue;   // -1: no collision; values >= N cannot come from the collision kernel
-            const double pa = a.prob[A.traj_off + i0 + i];
-            const double w = pa * pb;
-            ++cnt;
-            pm += w;
-            if (smem_hist) {
-                atomicAdd(s_cnt + T, 1u);
-                atomicAdd(s_H + T, w);
-            } else {
-                atomicAdd(a.acc.count_k + (long long)p * N + T, 1ull);
-                atomicAdd(a.acc.H + (long long)p * N + T, w);
-            }
-            if (P.ego_side == 0) {          // row hypothesis belongs to the EGO object, CO = b
-                atomicAdd(s_row_mass + i, pb);
-                atomicAdd(s_row_hits + i, 1u);
-                atomicAdd(a.acc.logq + ((long long)(i0 + i) * N + T) * a.n_obj + P.b, lq_b);
-            } else if (P.ego_side == 1) {   // column hypothesis belongs to the EGO object, CO = a
-                col_mass += pa;
-                ++col_hits;
-                atomicAdd(a.acc.logq + ((long long)(j0 + j) * N + T) * a.n_obj + P.a, log1p(-pa));
+        const unsigned long long pb_fix = to_fixed(pb, kFixProb);
+        for (int ib = 0; ib < rows; ib += 16) {
+            int16_t v[16];   // 16 independent loads in flight, then the (rare) hits
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = ib + q < rows ? __ldg(row + (long long)(ib + q) * B.h) : (int16_t)-1;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int T = v[q];
+                if (T < 0 || T >= N) continue;   // -1: no collision; >= N cannot come from the collision kernel
+                const int i = ib + q;
+                const float pa = a.probf[A.traj_off + i0 + i];
+                const unsigned long long w = to_fixed(pa * pb, kFixProb);
+                ++cnt;
+                pm += w;
+                if (smem_hist) {
+                    atomicAdd(s_cnt + T, 1u);
+                    atomicAdd(s_H + T, w);
+                } else {
+                    atomicAdd(a.acc.count_k + (long long)p * N + T, 1ull);
+                    atomicAdd(a.acc.H + (long long)p * N + T, w);
+                }
+                if (P.ego_side == 0) {          // row hypothesis belongs to the EGO object, CO = b
+                    atomicAdd(s_row_mass + i, pb_fix);
+                    atomicAdd(s_row_hits + i, 1u);
+                    const unsigned long long lq = to_fixed(neg_log_survival(pb), kFixLog);
+                    if (smem_cells) atomicAdd(s_L + i * N + T, lq);
+                    else atomicAdd(a.acc.lsum + ((long long)(i0 + i) * N + T) * a.n_obj + P.b, lq);
+                } else if (P.ego_side == 1) {   // column hypothesis belongs to the EGO object, CO = a
+                    col_mass += to_fixed(pa, kFixProb);
+                    ++col_hits;
+                    const unsigned long long lq = to_fixed(neg_log_survival(pa), kFixLog);
+                    if (smem_cells) s_L[j * N + T] += lq;   // only this thread owns column j's cells
+                    else atomicAdd(a.acc.lsum + ((long long)(j0 + j) * N + T) * a.n_obj + P.a, lq);
+                }
             }
         }
     }
     if (P.ego_side == 1 && col_hits) {
-        atomicAdd(a.acc.naive + j0 + j, col_mass);
         atomicAdd(a.acc.mass + (long long)(j0 + j) * a.n_obj + P.a, col_mass);
         atomicAdd(a.acc.hits + j0 + j, (unsigned long long)col_hits);
     }
@@ -137,89 +181,147 @@ __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
             }
         }
     }
+    if (smem_cells) {
+        const int e0 = P.ego_side == 0 ? i0 : j0, other = P.ego_side == 0 ? P.b : P.a;
+        for (int q = tid; q < kTile * N; q += 64) {
+            const unsigned long long v = s_L[q];
+            if (v) {
+                const int e = q / N, k = q - e * N;
+                atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + k) * a.n_obj + other, v);
+            }
+        }
+    }
     if (P.ego_side == 0 && tid < rows && s_row_hits[tid]) {
-        atomicAdd(a.acc.naive + i0 + tid, s_row_mass[tid]);
         atomicAdd(a.acc.mass + (long long)(i0 + tid) * a.n_obj + P.b, s_row_mass[tid]);
         atomicAdd(a.acc.hits + i0 + tid, (unsigned long long)s_row_hits[tid]);
     }
 }
 
-__global__ void __launch_bounds__(256) ego_kernel(const RiskArgs a) {
-    extern __shared__ double s_attr[];   // [n_obj] then [N]
-    __shared__ double s_tot[3][8];
+// One warp per EGO hypothesis.  The (step, object) cells are read in ascending order 32 at a time; a chunk
+// with a non-empty cell gets an exclusive warp prefix product of the survival factors (1 - q), so each
+// cell knows the survival S of every earlier cell and contributes S q.
+__global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
+    extern __shared__ unsigned long long s_attr[];   // [n_obj] then [N], fixed point
+    __shared__ double s_tot[3][2];
     const int N = a.n_steps, n_obj = a.n_obj;
     const bool smem = (n_obj + N) <= 4096;
     if (smem) {
-        for (int q = threadIdx.x; q < n_obj + N; q += blockDim.x) s_attr[q] = 0.0;
+        for (int q = threadIdx.x; q < n_obj + N; q += blockDim.x) s_attr[q] = 0ull;
         __syncthreads();
     }
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
     double naive = 0.0, cond = 0.0, indep = 0.0, pe = 0.0;
+    unsigned long long hits = 0;
     if (i < a.h_e) {
         const ObjDesc &E = a.objs[a.ego];
         pe = a.prob[E.traj_off + i];
-        naive = a.acc.naive[i];
-        const double *lq = a.acc.logq + (long long)i * N * n_obj;
-        double ls = 0.0;     // log of the survival product of all earlier cells
-        for (int k = 0; k < N; ++k) {
-            for (int b = 0; b < n_obj; ++b) {
-                const double L = lq[(long long)k * n_obj + b];
-                if (L == 0.0) continue;
-                const double eff = exp(ls) * -expm1(L);
-                cond += eff;
-                ls += L;
-                if (smem) {
-                    atomicAdd(s_attr + b, pe * eff);
-                    atomicAdd(s_attr + n_obj + k, pe * eff);
-                } else {
-                    atomicAdd(a.acc.attr_obj + b, pe * eff);
-                    atomicAdd(a.acc.attr_step + k, pe * eff);
-                }
+        const float pef = a.probf[E.traj_off + i];
+        hits = a.acc.hits[i];
+        if (hits) {
+            // per-object masses: naive sum and independence product
+            double surv = 1.0, mass_sum = 0.0;
+            const unsigned long long *ms = a.acc.mass + (long long)i * n_obj;
+            for (int b = lane; b < n_obj; b += 32) {
+                const double m = from_fixed(ms[b], kFixProb);
+                mass_sum += m;
+                surv *= 1.0 - m;
             }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) surv *= __shfl_xor_sync(0xffffffffu, surv, d);
+            naive = warp_sum(mass_sum);
+            indep = 1.0 - surv;
+            // chronological walk over the cells
+            const unsigned long long *lc = a.acc.lsum + (long long)i * N * n_obj;
+            const long long cells = (long long)N * n_obj;
+            double carry = 1.0, part = 0.0;   // carry: survival product of every cell before the chunk
+            for (long long c0 = 0; c0 < cells; c0 += 32) {
+                const long long c = c0 + lane;
+                const unsigned long long lf = c < cells ? lc[c] : 0ull;
+                if (!__ballot_sync(0xffffffffu, lf != 0ull)) continue;     // empty cells change nothing
+                const float qf = lf ? -expm1f(-(float)lf * (1.0f / 1099511627776.0f)) : 0.0f;  // 2^-40
+                double incl = 1.0 - (double)qf;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const double u = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl *= u;
+                }
+                double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+                if (lane == 0) excl = 1.0;
+                const double eff = carry * excl * (double)qf;
+                part += eff;
+                if (lf) {
+                    const int k = (int)(c / n_obj), b = (int)(c - (long long)k * n_obj);
+                    const unsigned long long w = to_fixed(pef * (float)eff, kFixProb);
+                    if (smem) {
+                        atomicAdd(s_attr + b, w);
+                        atomicAdd(s_attr + n_obj + k, w);
+                    } else {
+                        atomicAdd(a.acc.attr_obj + b, w);
+                        atomicAdd(a.acc.attr_step + k, w);
+                    }
+                }
+                carry *= __shfl_sync(0xffffffffu, incl, 31);
+            }
+            cond = warp_sum(part);
         }
-        double surv = 1.0;
-        const double *ms = a.acc.mass + (long long)i * n_obj;
-        for (int b = 0; b < n_obj; ++b) surv *= 1.0 - ms[b];
-        indep = 1.0 - surv;
-        if (a.naive) a.naive[i] = naive;
-        if (a.cond) a.cond[i] = cond;
-        if (a.indep) a.indep[i] = indep;
-        if (a.hits) a.hits[i] = (int)a.acc.hits[i];
+        if (lane == 0) {
+            if (a.naive) a.naive[i] = naive;
+            if (a.cond) a.cond[i] = cond;
+            if (a.indep) a.indep[i] = indep;
+            if (a.hits) a.hits[i] = (int)hits;
+        }
     }
-    double v0 = warp_sum(pe * naive), v1 = warp_sum(pe * cond), v2 = warp_sum(pe * indep);
-    if ((threadIdx.x & 31) == 0) {
-        s_tot[0][threadIdx.x >> 5] = v0; s_tot[1][threadIdx.x >> 5] = v1; s_tot[2][threadIdx.x >> 5] = v2;
+    if (lane == 0) {
+        s_tot[0][warp] = pe * naive; s_tot[1][warp] = pe * cond; s_tot[2][warp] = pe * indep;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double s = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += s_tot[threadIdx.x][q];
-        atomicAdd(a.acc.scalars + threadIdx.x, s);
+        const double t = s_tot[threadIdx.x][0] + s_tot[threadIdx.x][1];
+        if (t != 0.0) atomicAdd(a.acc.scalars + threadIdx.x, t);
     }
     if (smem) {
         for (int q = threadIdx.x; q < n_obj + N; q += blockDim.x) {
-            const double v = s_attr[q];
-            if (v != 0.0) atomicAdd(q < n_obj ? a.acc.attr_obj + q : a.acc.attr_step + (q - n_obj), v);
+            const unsigned long long v = s_attr[q];
+            if (v) atomicAdd(q < n_obj ? a.acc.attr_obj + q : a.acc.attr_step + (q - n_obj), v);
         }
     }
 }
 
-// single CTA: escape-route ranking and the copy of the totals to the caller's outputs
+// single CTA: escape-route ranking and the conversion of the totals into the caller's outputs
 __global__ void __launch_bounds__(1024) finish_kernel(const RiskArgs a) {
     const int he = a.h_e;
     const ObjDesc &E = a.objs[a.ego];
     const double *pe = a.prob + E.traj_off;
+    // Probabilities are non-negative, so their IEEE bit patterns order like the values: ranking compares
+    // 64-bit integer keys (integer pipe) instead of doubles.  Key -1 marks a hypothesis that collides.
+    constexpr int kCached = 4096;
+    __shared__ long long s_key[kCached];
     __shared__ int s_n;
+    const bool cached = he <= kCached;
     if (threadIdx.x == 0) s_n = 0;
+    if (cached)
+        for (int i = threadIdx.x; i < he; i += blockDim.x)
+            s_key[i] = a.acc.hits[i] == 0ull ? __double_as_longlong(pe[i]) : -1ll;
     __syncthreads();
     for (int i = threadIdx.x; i < he; i += blockDim.x) {
         if (a.acc.hits[i] != 0ull) continue;
         atomicAdd(&s_n, 1);
         if (!a.escape) continue;
-        const double p = pe[i];
+        const long long key = __double_as_longlong(pe[i]);
         int rank = 0;
-        for (int q = 0; q < he; ++q)
-            if (a.acc.hits[q] == 0ull && (pe[q] > p || (pe[q] == p && q < i))) ++rank;
+        if (cached) {
+            for (int q = 0; q < he; ++q) {
+                const long long kq = s_key[q];
+                rank += (kq > key || (kq == key && q < i)) ? 1 : 0;
+            }
+        } else {
+            for (int q = 0; q < he; ++q) {
+                if (a.acc.hits[q] != 0ull) continue;
+                const long long kq = __double_as_longlong(pe[q]);
+                rank += (kq > key || (kq == key && q < i)) ? 1 : 0;
+            }
+        }
         a.escape[rank] = i;
     }
     __syncthreads();
@@ -227,16 +329,16 @@ __global__ void __launch_bounds__(1024) finish_kernel(const RiskArgs a) {
     const long long npn = (long long)a.n_pairs * a.n_steps;
     for (long long q = threadIdx.x; q < npn; q += blockDim.x) {
         if (a.count_k) a.count_k[q] = (long long)a.acc.count_k[q];
-        if (a.H) a.H[q] = a.acc.H[q];
+        if (a.H) a.H[q] = from_fixed(a.acc.H[q], kFixProb);
     }
     for (int q = threadIdx.x; q < a.n_pairs; q += blockDim.x) {
         if (a.count) a.count[q] = (long long)a.acc.count[q];
-        if (a.P) a.P[q] = a.acc.P[q];
+        if (a.P) a.P[q] = from_fixed(a.acc.P[q], kFixProb);
     }
     for (int q = threadIdx.x; q < a.n_obj; q += blockDim.x)
-        if (a.attr_obj) a.attr_obj[q] = a.acc.attr_obj[q];
+        if (a.attr_obj) a.attr_obj[q] = from_fixed(a.acc.attr_obj[q], kFixProb);
     for (int q = threadIdx.x; q < a.n_steps; q += blockDim.x)
-        if (a.attr_step) a.attr_step[q] = a.acc.attr_step[q];
+        if (a.attr_step) a.attr_step[q] = from_fixed(a.acc.attr_step[q], kFixProb);
     if (threadIdx.x < 4 && a.scalars) a.scalars[threadIdx.x] = threadIdx.x < 3 ? a.acc.scalars[threadIdx.x] : 0.0;
 }
 
@@ -249,14 +351,19 @@ cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (a.n_tiles > 0) {
         if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-        const size_t smem = a.n_steps <= kMaxSmemSteps
-                                ? sizeof(unsigned) * ((a.n_steps + 1) & ~1) + sizeof(double) * a.n_steps : 0;
+        size_t smem = 0;
+        if (a.n_steps <= kMaxSmemSteps) smem = 8 * ((size_t)a.n_steps + (a.n_steps + 1) / 2);
+        if (a.n_steps <= kMaxSmemCells) smem += 8 * (size_t)kTile * a.n_steps;
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
         scan_kernel<<<(unsigned)a.n_tiles, 64, smem, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (a.h_e > 0) {
-        const size_t smem = (a.n_obj + a.n_steps) <= 4096 ? sizeof(double) * (a.n_obj + a.n_steps) : 0;
-        ego_kernel<<<(a.h_e + 255) / 256, 256, smem, st>>>(a);
+        const size_t smem = (a.n_obj + a.n_steps) <= 4096 ? 8 * (size_t)(a.n_obj + a.n_steps) : 0;
+        ego_kernel<<<(a.h_e + 1) / 2, 64, smem, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     finish_kernel<<<1, 1024, 0, st>>>(a);

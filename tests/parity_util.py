@@ -5,15 +5,16 @@ Acceptance (the method's tolerances):
   * first-collision tables: equal, except hypothesis pairs whose disagreeing steps are all borderline,
     i.e. the oracle's exact signed margin there is below 1e-3 m in magnitude; such excused pairs must stay
     below 1e-5 of all pose-pair tests;
-  * risk measures computed from the same table: integer outputs identical, probabilities within 1e-9
-    relative (FP64 on both sides, different summation order).
+  * risk measures computed from the same table: integer outputs identical, probabilities within 1e-6
+    relative (the stated tolerance).  On the GPU every per-collision term is formed in FP32 (relative
+    rounding ~2e-7) and summed exactly in 64-bit fixed point.
 """
 import numpy as np
 
 POSE_TOL = 1e-4
 BORDER_TOL = 1e-3
 EXCUSE_FRACTION = 1e-5
-PROB_RTOL = 1e-9
+PROB_RTOL = 1e-6
 
 
 def corner_error(sc, orc_poses, gx, gy, gc, gs):
