@@ -50,18 +50,36 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the stress32 / paper_s2 measurements")
+    ap.add_argument("--workload", default="intersection11", choices=sorted(WORKLOADS),
+                    help="the timed workload (the default is the benchmark's; the others serve profiling)")
     return ap.parse_args()
+
+
+WORKLOADS = {
+    "intersection11": "intersection11: 7 cars (4.5x1.8 m, 441 hypotheses = 21 accel x 21 steer) + 4 pedestrians "
+                      "(r 0.4 m, 121 = 11 speeds x 11 headings), 30 steps of 0.1 s (5 sub-steps), all 55 object pairs",
+    "stress32": "stress32: 32 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps of 0.1 s, 496 object pairs",
+    "stress12": "stress12: 12 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps of 0.1 s, 66 object pairs",
+    "paper_s2": "paper_s2: EGO 2058 (6 x 343) + 10 COs x 42 (6 x 7), 100 steps of 20 ms, EGO-only pairs",
+}
+WORKLOAD = "intersection11"
 
 
 def workload(rank: int = 0):
     from paper_2005_06773_gb300 import scenarios as S
+    if WORKLOAD == "stress32":
+        return S.stress32(4 + rank)
+    if WORKLOAD == "stress12":
+        return S.stress32(4 + rank, n_cars=12)
+    if WORKLOAD == "paper_s2":
+        return S.paper_s1s2(10, 6, seed=6 + rank)
     return S.intersection11(2 + rank)
 
 
 def config_of(sc, rank0_seed=2):
     return {
-        "workload": "intersection11: 7 cars (4.5x1.8 m, 441 hypotheses = 21 accel x 21 steer) + 4 pedestrians "
-                    "(r 0.4 m, 121 = 11 speeds x 11 headings), 30 steps of 0.1 s (5 sub-steps), all 55 object pairs",
+        "workload": WORKLOADS[WORKLOAD],
         "seed": rank0_seed,
         "tests_per_step": sc.n_tests(),
         "trajectory_pairs_per_step": sc.n_traj_pairs(),
@@ -213,6 +231,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_workload(mhc, torch, sc, dev, steps, flush, peak):
+    """Device time of the whole hot path (mhc_evaluate) on one more workload, L2 flushed per step."""
+    cs = mhc.as_c(sc)
+    lay = mhc.layout(cs)
+    ctx = mhc.Context(dev.index or 0, 512 << 20)
+    poses = mhc.alloc_poses(sc, dev)
+    table = torch.empty(lay["n_entries"], dtype=torch.int16, device=dev)
+    risk = mhc.alloc_risk(cs, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    mhc.generate(ctx, cs, poses, stream=stream)
+    tuned = mhc.autotune(ctx, cs, poses, table, stream=stream)
+    for _ in range(2):
+        mhc.evaluate(ctx, cs, poses, table, out=risk, stream=stream)
+    torch.cuda.synchronize()
+    ctx.counters(reset=True)
+    ctx.profile_read(reset=True)
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s_ in range(steps):
+        flush.zero_()
+        ev[s_][0].record(stream)
+        mhc.evaluate(ctx, cs, poses, table, out=risk, stream=stream)
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    prof = ctx.profile_read(reset=True)
+    executed, narrow = ctx.counters(reset=True)
+    coll_ms, coll_n = prof["collide"]
+    coll_s = coll_ms / 1e3 / max(coll_n, 1)
+    ops = (OPS_PER_BROAD_TEST * executed + OPS_PER_NARROW_TEST * narrow) / max(coll_n, 1)
+    out = {"tests_per_step": sc.n_tests(), "ms_per_step": ms, "tests_per_s": sc.n_tests() / (ms / 1e3),
+           "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+           "executed_tests_per_launch": executed / max(coll_n, 1),
+           "collide_roofline_frac": ops / coll_s / 1e12 / peak, "collide_achieved": ops / coll_s / 1e12,
+           "collide_layout": {"variant": tuned[0], "cull": tuned[1]}}
+    ctx.close()
+    del table
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_mhc(args):
     import torch
     import torch.distributed as dist
@@ -236,10 +296,11 @@ def run_mhc(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        mhc.generate(ctx, cs, poses, stream=stream)
-        mhc.detect(ctx, cs, poses, table, stream=stream)
-        mhc.assess(ctx, cs, table, out=risk, stream=stream)
+    def step():   # the whole hot path in one C-ABI call (fused collision + risk accumulation)
+        mhc.evaluate(ctx, cs, poses, table, out=risk, stream=stream)
+
+    mhc.generate(ctx, cs, poses, stream=stream)
+    tuned = mhc.autotune(ctx, cs, poses, table, stream=stream)   # untimed set-up: picks the collision layout
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -326,9 +387,18 @@ def run_mhc(args):
                      "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                                     "(sm_max_mhz of MEASURED_PEAKS.json)"},
         "clocks": clk,
+        "collide_layout": {"variant": tuned[0], "cull": tuned[1], "chosen_by": "mhc_autotune (untimed set-up)"},
         "wall_s_timed_region": wall,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if not args.no_extra:
+        from paper_2005_06773_gb300 import scenarios as S
+        line["extra_workloads"] = {
+            "stress32": dict(measure_workload(mhc, torch, S.stress32(4), dev, 5, flush, peak),
+                             workload="32 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps, 496 pairs"),
+            "paper_s2": dict(measure_workload(mhc, torch, S.paper_s1s2(10, 6), dev, 50, flush, peak),
+                             workload="paper Table I S2 shape: EGO 2058 x 10 CO 42, 100 steps of 20 ms, EGO-only"),
+        }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD == "intersection11":
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -338,7 +408,9 @@ def run_mhc(args):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = args.workload
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return

@@ -160,6 +160,13 @@ void mhc_destroy(mhc_ctx *ctx);
  *                 bounding boxes of the two tiles' pose centres, grown by both circumradii, do not meet.
  *                 The table is identical either way; 0 tests every step (used to check that). */
 #define MHC_OPT_CULL 1
+/*   MHC_OPT_COLLIDE_VARIANT  thread layout of the collision kernel (same table in every case):
+ *                 1: 256 threads per 64 x 64 tile, 4 x 4 micro-tiles, all warps on one step at a time;
+ *                 2: 64 threads per tile, 8 x 8 micro-tiles;
+ *                 3: 4 warps per tile, each warp testing whole steps (8 x 16 micro-tiles per lane);
+ *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 3 for at
+ *                 least 32 tiles per SM and 1 below. */
+#define MHC_OPT_COLLIDE_VARIANT 3
 int mhc_set_option(mhc_ctx *ctx, int option, long long value);
 
 /* Work counters of the collision kernel since the last reset, summed over calls on this context:
@@ -170,7 +177,8 @@ int mhc_collision_counters(mhc_ctx *ctx, uint64_t out[2], int reset, void *strea
 /* Kernel timing (mhc_set_option(ctx, MHC_OPT_PROFILE, 1)): the library records a CUDA event pair on the
    launching stream around every kernel it launches.  mhc_profile_read synchronises those events and
    returns, per kernel class (MHC_K_GENERATE; MHC_K_BOUNDS = the table fill and the tile-bounds kernel;
-   MHC_K_COLLIDE; MHC_K_RISK = the risk chain of four kernels), the summed milliseconds and the launch counts
+   MHC_K_COLLIDE; MHC_K_RISK = the risk kernels: prepare, table scan (not in the fused mhc_evaluate /
+   mhc_run path) and the EGO walk), the summed milliseconds and the launch counts
    since the last reset; reset != 0 clears them.  Disabled by default (no events recorded). */
 #define MHC_OPT_PROFILE 2
 enum { MHC_K_GENERATE = 0, MHC_K_BOUNDS = 1, MHC_K_COLLIDE = 2, MHC_K_RISK = 3, MHC_K_COUNT = 4 };
@@ -223,6 +231,26 @@ int mhc_detect_collisions(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_pose
  */
 int mhc_assess_risk(mhc_ctx *ctx, const mhc_scenario *scen, const int16_t *table,
                     const float *const *traj_weights, const mhc_risk *out, void *stream);
+
+/*
+ * The whole method on device buffers in one call: generation (Section IV-B) into `poses`, collision
+ * recognition (Section IV-C) into `table`, risk (Section IV-D) into the device outputs `out` -- the same
+ * results as the three calls above.  The collision kernel accumulates the risk terms at each first hit,
+ * so the table is not read a second time.  Asynchronous on `stream`.  Errors as above.
+ */
+int mhc_evaluate(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, const mhc_poses *poses,
+                 int16_t *table, const mhc_risk *out, void *stream);
+
+/*
+ * Autotuner of the collision stage: times the collision kernel (its own CUDA events) with every thread
+ * layout and with culling on and off, on `poses` / `table` (device buffers as for mhc_detect_collisions),
+ * either as mhc_detect_collisions runs it (fused = 0) or as mhc_evaluate / mhc_run run it with the risk
+ * terms accumulated inside (fused = 1; outputs go to the arena).  The fastest is kept for scenarios of
+ * this size class (floor(log2(tiles)), floor(log2(n_steps))) and that path, and reported; later calls
+ * with MHC_OPT_COLLIDE_VARIANT 0 use it.  Synchronises `stream`.
+ */
+int mhc_autotune(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses, int16_t *table, int fused,
+                 int32_t *best_variant, int32_t *best_cull, void *stream);
 
 /* Arena bytes mhc_run needs for this scenario (poses + table + scratch). */
 int mhc_run_bytes(const mhc_scenario *scen, size_t *bytes);

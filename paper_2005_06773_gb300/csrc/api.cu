@@ -175,7 +175,7 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
     s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj);
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
     const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
-    s.acc_words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4;
+    s.acc_words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4 + 2;
     s.acc = align_up(8 * (size_t)s.acc_words);
     s.total = s.desc + s.weights + s.bounds + s.prob + s.acc;
     return s;
@@ -196,7 +196,11 @@ struct mhc_ctx {
     cudaStream_t last_stream = nullptr;
     bool has_last = false;
     int cull = 1;
+    int variant = 0;
     int n_sm = 152;
+    // autotuned collision configuration per size class (log2 of the tile count, log2 of the steps)
+    struct Tuned { int tiles_log2, steps_log2, fused, variant, cull; };
+    std::vector<Tuned> tuned;
     unsigned long long *counters = nullptr;
     // kernel timing
     bool profile = false;
@@ -363,8 +367,98 @@ int gather_weights(const Layout &L, const float *const *w, std::vector<float> &o
     return MHC_OK;
 }
 
+// Risk scratch of one assessment (accumulators + probabilities) carved from the arena.
+int make_risk_args(const Layout &L, const DevDesc &D, Bump &bump, const int16_t *table, const mhc_risk *rout,
+                   RiskArgs &r) {
+    std::memset(&r, 0, sizeof r);
+    r.objs = D.objs; r.pairs = D.pairs; r.n_pairs = (int)L.pairs.size(); r.n_obj = L.n_obj;
+    r.n_steps = L.N; r.ego = L.ego; r.h_e = L.h_e; r.n_tiles = L.n_tiles; r.table = table;
+    r.weights = D.weights;
+    r.prob = static_cast<double *>(bump.take(sizeof(double) * (size_t)L.n_traj));
+    r.probf = static_cast<float *>(bump.take(sizeof(float) * (size_t)L.n_traj));
+    const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+    const long long words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4 + 2;
+    unsigned long long *w = static_cast<unsigned long long *>(bump.take(8 * (size_t)words));
+    if (!r.prob || !r.probf || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
+    RiskScratch &A = r.acc;
+    A.base = w; A.n_words = words;
+    A.count = w; w += np;
+    A.count_k = w; w += np * N;
+    A.P = w; w += np;
+    A.H = w; w += np * N;
+    A.hits = w; w += he;
+    A.lsum = w; w += he * N * no;
+    A.mass = w; w += he * no;
+    A.attr_obj = w; w += no;
+    A.attr_step = w; w += N;
+    A.scalars = reinterpret_cast<double *>(w); w += 4;
+    A.n_escape = w; w += 1;
+    A.done = w;
+    r.count = reinterpret_cast<long long *>(rout->count);
+    r.count_k = reinterpret_cast<long long *>(rout->count_k);
+    r.P = rout->P; r.H = rout->H; r.naive = rout->naive; r.cond = rout->cond; r.indep = rout->indep;
+    r.hits = rout->hits; r.attr_obj = rout->attr_obj; r.attr_step = rout->attr_step;
+    r.scalars = rout->scalars; r.escape = rout->escape; r.n_escape = rout->n_escape;
+    return MHC_OK;
+}
+
+int log2_floor(long long v) {
+    int r = 0;
+    while (v > 1) { v >>= 1; ++r; }
+    return r;
+}
+
+// Collision configuration for a scenario: the forced variant, else the tuned one of its size class, else
+// the default (warp-per-step layout for at least 32 tiles per SM, else 256 threads x 4 x 4).
+void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &variant, int &cull) {
+    cull = ctx->cull;
+    if (ctx->variant != 0) { variant = ctx->variant; return; }
+    const int tl = log2_floor(L.n_tiles), sl = log2_floor(L.N);
+    for (const auto &t : ctx->tuned)
+        if (t.tiles_log2 == tl && t.steps_log2 == sl && t.fused == (int)fused) {
+            variant = t.variant;
+            cull = t.cull;
+            return;
+        }
+    variant = L.n_tiles >= 32LL * ctx->n_sm ? 3 : 1;
+}
+
+// Device buffers for the risk outputs of one assessment, carved from the arena.
+bool take_risk_outputs(Bump &bump, const Layout &L, mhc_risk &R) {
+    const size_t np = L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+    std::memset(&R, 0, sizeof R);
+    R.count = static_cast<int64_t *>(bump.take(8 * np));
+    R.count_k = static_cast<int64_t *>(bump.take(8 * np * N));
+    R.P = static_cast<double *>(bump.take(8 * np));
+    R.H = static_cast<double *>(bump.take(8 * np * N));
+    R.naive = static_cast<double *>(bump.take(8 * he));
+    R.cond = static_cast<double *>(bump.take(8 * he));
+    R.indep = static_cast<double *>(bump.take(8 * he));
+    R.hits = static_cast<int32_t *>(bump.take(4 * he));
+    R.attr_obj = static_cast<double *>(bump.take(8 * no));
+    R.attr_step = static_cast<double *>(bump.take(8 * N));
+    R.scalars = static_cast<double *>(bump.take(8 * 4));
+    R.escape = static_cast<int32_t *>(bump.take(4 * he));
+    R.n_escape = static_cast<int32_t *>(bump.take(4));
+    return R.count && R.count_k && R.P && R.H && R.naive && R.cond && R.indep && R.hits && R.attr_obj &&
+           R.attr_step && R.scalars && R.escape && R.n_escape;
+}
+
+// Launch sequence.  fused: the collision kernel accumulates the risk terms at each first hit (no second
+// pass over the table): prepare -> generate -> fill + bounds -> collide -> ego walk + finish.
 int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, const mhc_poses *gen_out,
-               const mhc_poses *coll_in, int16_t *table, bool risk, const mhc_risk *rout, cudaStream_t st) {
+               const mhc_poses *coll_in, int16_t *table, bool risk, const mhc_risk *rout, cudaStream_t st,
+               bool fused = false) {
+    RiskArgs r;
+    fused = fused && risk && coll_in;
+    if (risk) {
+        if (int rc = make_risk_args(L, D, bump, table, rout, r)) return rc;
+    }
+    if (fused) {
+        TimedScope ts(ctx, st, MHC_K_RISK, 1);
+        cudaError_t e = launch_risk_prepare(r, st);
+        if (e != cudaSuccess) return cuda_fail(e, "risk prepare launch");
+    }
     if (gen_out) {
         GenArgs g;
         g.objs = D.objs; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
@@ -376,13 +470,15 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         if (e != cudaSuccess) return cuda_fail(e, "generation kernel launch");
     }
     if (coll_in) {
+        int variant = 1, cull = 1;
+        pick_collide_config(ctx, L, fused, variant, cull);
         float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_tiles32 * L.N));
         if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
         {
-            TimedScope ts(ctx, st, MHC_K_BOUNDS, ctx->cull ? 2 : 1);
+            TimedScope ts(ctx, st, MHC_K_BOUNDS, cull ? 2 : 1);
             cudaError_t e = launch_fill_table(table, L.n_entries, st);
             if (e != cudaSuccess) return cuda_fail(e, "table fill launch");
-            if (ctx->cull) {
+            if (cull) {
                 BoundsArgs b;
                 b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
                 b.n_warps = (int)L.warp_obj.size(); b.n_steps = L.N; b.x = coll_in->x; b.y = coll_in->y;
@@ -391,46 +487,23 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
                 if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
             }
         }
-        CollideArgs c;
+        CollideArgs c{};
         c.objs = D.objs; c.pairs = D.pairs; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
-        c.n_steps = L.N; c.cull = ctx->cull;
+        c.n_steps = L.N; c.cull = cull; c.variant = variant;
         c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
         c.bounds = bounds; c.table = table; c.counters = ctx->counters;
+        if (fused) {
+            c.probf = r.probf;
+            c.acc = r.acc;
+            c.n_obj = L.n_obj;
+        }
         TimedScope ts(ctx, st, MHC_K_COLLIDE, 1);
         cudaError_t e = launch_collide(c, st);
         if (e != cudaSuccess) return cuda_fail(e, "collision kernel launch");
     }
     if (risk) {
-        RiskArgs r;
-        std::memset(&r, 0, sizeof r);
-        r.objs = D.objs; r.pairs = D.pairs; r.n_pairs = (int)L.pairs.size(); r.n_obj = L.n_obj;
-        r.n_steps = L.N; r.ego = L.ego; r.h_e = L.h_e; r.n_tiles = L.n_tiles; r.table = table;
-        r.weights = D.weights;
-        r.prob = static_cast<double *>(bump.take(sizeof(double) * (size_t)L.n_traj));
-        r.probf = static_cast<float *>(bump.take(sizeof(float) * (size_t)L.n_traj));
-        const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
-        const long long words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4;
-        unsigned long long *w = static_cast<unsigned long long *>(bump.take(8 * (size_t)words));
-        if (!r.prob || !r.probf || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
-        RiskScratch &A = r.acc;
-        A.base = w; A.n_words = words;
-        A.count = w; w += np;
-        A.count_k = w; w += np * N;
-        A.P = w; w += np;
-        A.H = w; w += np * N;
-        A.hits = w; w += he;
-        A.lsum = w; w += he * N * no;
-        A.mass = w; w += he * no;
-        A.attr_obj = w; w += no;
-        A.attr_step = w; w += N;
-        A.scalars = reinterpret_cast<double *>(w);
-        r.count = reinterpret_cast<long long *>(rout->count);
-        r.count_k = reinterpret_cast<long long *>(rout->count_k);
-        r.P = rout->P; r.H = rout->H; r.naive = rout->naive; r.cond = rout->cond; r.indep = rout->indep;
-        r.hits = rout->hits; r.attr_obj = rout->attr_obj; r.attr_step = rout->attr_step;
-        r.scalars = rout->scalars; r.escape = rout->escape; r.n_escape = rout->n_escape;
-        TimedScope ts(ctx, st, MHC_K_RISK, 4);
-        cudaError_t e = launch_risk(r, st);
+        TimedScope ts(ctx, st, MHC_K_RISK, fused ? 1 : 3);
+        cudaError_t e = fused ? launch_risk_tail(r, st) : launch_risk(r, st);
         if (e != cudaSuccess) return cuda_fail(e, "risk kernel launch");
     }
     return MHC_OK;
@@ -514,6 +587,11 @@ int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
     if (int r = check_ctx(ctx)) return r;
     if (option == MHC_OPT_CULL) { ctx->cull = value != 0; return MHC_OK; }
     if (option == MHC_OPT_PROFILE) { ctx->profile = value != 0; return MHC_OK; }
+    if (option == MHC_OPT_COLLIDE_VARIANT) {
+        if (value < 0 || value > 3) return fail(MHC_E_INVALID, "collide variant must be 0 to 3");
+        ctx->variant = (int)value;
+        return MHC_OK;
+    }
     return fail(MHC_E_INVALID, "unknown option");
 }
 
@@ -640,6 +718,90 @@ int mhc_assess_risk(mhc_ctx *ctx, const mhc_scenario *scen, const int16_t *table
     return end_call(ctx, st);
 }
 
+int mhc_evaluate(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, const mhc_poses *poses,
+                 int16_t *table, const mhc_risk *out, void *stream) {
+    if (int r = check_ctx(ctx)) return r;
+    if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table || !out)
+        return fail(MHC_E_INVALID, "poses, table and out must be non-NULL");
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    plan_generation(L, ctx->n_sm);
+    std::vector<float> w;
+    if (int r = gather_weights(L, traj_weights, w)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch S = scratch_of(L, !w.empty());
+    Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
+    char *dev = static_cast<char *>(bump.take(S.desc + S.weights));
+    if (!dev) return fail(MHC_E_NOMEM, "arena too small for the descriptors");
+    if (int r = begin_call(ctx, st)) return r;
+    DevDesc D;
+    if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
+    if (int r = launch_all(ctx, L, D, bump, poses, poses, table, true, out, st, true)) return r;
+    return end_call(ctx, st);
+}
+
+int mhc_autotune(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses, int16_t *table, int fused,
+                 int32_t *best_variant, int32_t *best_cull, void *stream) {
+    if (int r = check_ctx(ctx)) return r;
+    if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table)
+        return fail(MHC_E_INVALID, "poses and table must be non-NULL");
+    Layout L;
+    if (int r = build_layout(scen, L)) return r;
+    plan_generation(L, ctx->n_sm);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int saved_variant = ctx->variant, saved_cull = ctx->cull;
+    const bool saved_profile = ctx->profile;
+    double saved_ms[MHC_K_COUNT];
+    int64_t saved_n[MHC_K_COUNT];
+    if (int r = mhc_profile_read(ctx, saved_ms, saved_n, 1)) return r;   // keep the caller's totals aside
+    float best = 1e30f;
+    int bv = 1, bc = 1, rc = MHC_OK;
+    ctx->profile = true;
+    for (int cull = 1; cull >= 0 && rc == MHC_OK; --cull) {
+        for (int v = 1; v <= 3 && rc == MHC_OK; ++v) {
+            ctx->variant = v;
+            ctx->cull = cull;
+            double ms[MHC_K_COUNT];
+            int64_t n[MHC_K_COUNT];
+            for (int rep = 0; rep < 5 && rc == MHC_OK; ++rep) {   // the first run warms up, four count
+                if (fused) {
+                    Scratch S = scratch_of(L, false);
+                    Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
+                    char *dev = static_cast<char *>(bump.take(S.desc));
+                    mhc_risk R;
+                    if (!dev || !take_risk_outputs(bump, L, R)) { rc = fail(MHC_E_NOMEM, "arena too small to autotune"); break; }
+                    if ((rc = begin_call(ctx, st))) break;
+                    DevDesc D;
+                    if ((rc = upload(ctx, L, nullptr, dev, st, D))) break;
+                    if ((rc = launch_all(ctx, L, D, bump, poses, poses, table, true, &R, st, true))) break;
+                    if ((rc = end_call(ctx, st))) break;
+                } else {
+                    rc = mhc_detect_collisions(ctx, scen, poses, table, stream);
+                    if (rc) break;
+                }
+                if ((rc = mhc_profile_read(ctx, ms, n, rep == 0))) break;
+            }
+            if (rc != MHC_OK) break;
+            const float t = (float)ms[MHC_K_COLLIDE];
+            mhc_profile_read(ctx, nullptr, nullptr, 1);
+            if (t < best) { best = t; bv = v; bc = cull; }
+        }
+    }
+    ctx->variant = saved_variant;
+    ctx->cull = saved_cull;
+    ctx->profile = saved_profile;
+    for (int k = 0; k < MHC_K_COUNT; ++k) { ctx->prof_ms[k] = saved_ms[k]; ctx->prof_n[k] = saved_n[k]; }
+    if (rc != MHC_OK) return rc;
+    const int tl = log2_floor(L.n_tiles), sl = log2_floor(L.N);
+    bool stored = false;
+    for (auto &t : ctx->tuned)
+        if (t.tiles_log2 == tl && t.steps_log2 == sl && t.fused == (fused != 0)) { t.variant = bv; t.cull = bc; stored = true; }
+    if (!stored) ctx->tuned.push_back({tl, sl, fused != 0, bv, bc});
+    if (best_variant) *best_variant = bv;
+    if (best_cull) *best_cull = bc;
+    return MHC_OK;
+}
+
 int mhc_run_bytes(const mhc_scenario *scen, size_t *bytes) {
     Layout L;
     if (int r = build_layout(scen, L)) return r;
@@ -674,27 +836,13 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     int16_t *table = static_cast<int16_t *>(bump.take(sizeof(int16_t) * (size_t)L.n_entries));
     const size_t np = L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
     mhc_risk R;
-    std::memset(&R, 0, sizeof R);
-    R.count = static_cast<int64_t *>(bump.take(8 * np));
-    R.count_k = static_cast<int64_t *>(bump.take(8 * np * N));
-    R.P = static_cast<double *>(bump.take(8 * np));
-    R.H = static_cast<double *>(bump.take(8 * np * N));
-    R.naive = static_cast<double *>(bump.take(8 * he));
-    R.cond = static_cast<double *>(bump.take(8 * he));
-    R.indep = static_cast<double *>(bump.take(8 * he));
-    R.hits = static_cast<int32_t *>(bump.take(4 * he));
-    R.attr_obj = static_cast<double *>(bump.take(8 * no));
-    R.attr_step = static_cast<double *>(bump.take(8 * N));
-    R.scalars = static_cast<double *>(bump.take(8 * 4));
-    R.escape = static_cast<int32_t *>(bump.take(4 * he));
-    R.n_escape = static_cast<int32_t *>(bump.take(4));
-    if (!dev || !P.x || !P.y || !P.c || !P.s || !table || !R.count || !R.count_k || !R.P || !R.H || !R.naive ||
-        !R.cond || !R.indep || !R.hits || !R.attr_obj || !R.attr_step || !R.scalars || !R.escape || !R.n_escape)
+    const bool outs = take_risk_outputs(bump, L, R);
+    if (!dev || !P.x || !P.y || !P.c || !P.s || !table || !outs)
         return fail(MHC_E_NOMEM, "arena too small for mhc_run (see mhc_run_bytes)");
     if (int r = begin_call(ctx, st)) return r;
     DevDesc D;
     if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
-    if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st)) return r;
+    if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st, true)) return r;
     struct Cp { void *dst; const void *src; size_t n; } cps[] = {
         {out->count, R.count, 8 * np}, {out->count_k, R.count_k, 8 * np * N}, {out->P, R.P, 8 * np},
         {out->H, R.H, 8 * np * N}, {out->naive, R.naive, 8 * he}, {out->cond, R.cond, 8 * he},

@@ -49,25 +49,8 @@ __device__ __forceinline__ bool rect_disc(float dx, float dy, float c, float s, 
 }
 
 constexpr int kMaxChunks = (32767 + 31) / 32;   // 32-step activity words for the longest horizon
-
-// One staged pose per (thread, slot): slot q < 64 is hypothesis i0 + q of object a, q >= 64 is
-// hypothesis j0 + q - 64 of object b; padding rows and columns sit far away.
-__device__ __forceinline__ float4 load_pose(const CollideArgs &a, const ObjDesc &A, const ObjDesc &B, int k, int i0,
-                                            int j0, int rows, int cols, int q) {
-    if (q < kTile) {
-        if (q < rows) {
-            const long long idx = A.pose_base + (long long)k * A.h + i0 + q;
-            return make_float4(__ldg(a.x + idx), __ldg(a.y + idx), __ldg(a.c + idx), __ldg(a.s + idx));
-        }
-        return make_float4(kFar, 0.0f, 1.0f, 0.0f);
-    }
-    q -= kTile;
-    if (q < cols) {
-        const long long idx = B.pose_base + (long long)k * B.h + j0 + q;
-        return make_float4(__ldg(a.x + idx), __ldg(a.y + idx), __ldg(a.c + idx), __ldg(a.s + idx));
-    }
-    return make_float4(-kFar, 0.0f, 1.0f, 0.0f);
-}
+constexpr int kFusedHistSteps = 1024;            // per-CTA step histograms in shared memory up to this N
+constexpr int kFusedCellSteps = 160;             // per-CTA EGO survival cells (64 x N x 8 B) up to this N
 
 // Next active step at or after k (-1 if none), from the per-32-step activity words.
 __device__ __forceinline__ int next_active(const unsigned *mask, int n_chunks, int k) {
@@ -81,18 +64,27 @@ __device__ __forceinline__ int next_active(const unsigned *mask, int n_chunks, i
     return (w << 5) + __ffs(m) - 1;
 }
 
-// THREADS threads per 64 x 64 tile, each testing an MI x MJ micro-tile: rows ti + TI m, columns tj + TJ n.
-template <int THREADS, int MI, int MJ>
+// THREADS threads per 64 x 64 tile, each testing an MI x MJ micro-tile (rows ti + TI m, columns tj + TJ n).
+// The tile's active steps are taken CH at a time: all their poses are staged into shared memory with
+// every load in flight at once, then each warp runs through the CH steps without further barriers.
+template <int THREADS, int MI, int MJ, int CH, bool FUSED>
 __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
     constexpr int TI = kTile / MI, TJ = kTile / MJ;
     static_assert(TI * TJ == THREADS, "micro-tiles must cover the tile");
     static_assert(MI * MJ <= 64, "first-hit mask is 64 bits");
-    constexpr int SLOTS = (2 * kTile + THREADS - 1) / THREADS;   // staged poses per thread
-    __shared__ float4 s_pa[2][kTile];    // x, y, h_a
-    __shared__ float4 s_pb[2][kTile];    // x, y, h_b
-    __shared__ float2 s_ra[2][kTile];    // c, s
-    __shared__ float2 s_rb[2][kTile];
+    // dynamic shared memory: CH staged steps, then (FUSED) the tile's risk accumulators
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    float4 *s_pa = reinterpret_cast<float4 *>(s_dyn);               // [CH][64] x, y, h_a
+    float4 *s_pb = s_pa + CH * kTile;                                  // [CH][64] x, y, h_b
+    float2 *s_ra = reinterpret_cast<float2 *>(s_pb + CH * kTile);     // [CH][64] c, s
+    float2 *s_rb = s_ra + CH * kTile;
+    unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(s_rb + CH * kTile);
     __shared__ unsigned s_mask[kMaxChunks];
+    __shared__ int s_klist[CH];
+    __shared__ int s_nk, s_cursor;
+    constexpr int WARPS = THREADS / 32;
+    __shared__ unsigned long long s_found[THREADS];          // bit MJ m + n: the thread's pair has hit
+    __shared__ unsigned short s_queue[WARPS][32 * MI * MJ];  // per-warp candidates: owner lane << 6 | bit
 
     const long long g = blockIdx.x;
     if (g >= a.n_tiles) return;
@@ -136,72 +128,144 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
         const unsigned m = __ballot_sync(0xffffffffu, act);
         if ((tid & 31) == 0) s_mask[w] = m;
     }
+    if (tid == 0) s_cursor = 0;
     __syncthreads();
+    if (next_active(s_mask, n_chunks, 0) < 0) return;   // the tiles never come close: nothing to test
+
+    // fused risk accumulation: [N] u64 masses | [N] u32 counts | [64][N] u64 log-survival cells of the
+    // tile's EGO hypotheses (when N <= kFusedCellSteps)
+    __shared__ float s_prob[2][kTile];
+    __shared__ unsigned long long s_emass[kTile];
+    __shared__ unsigned s_ehits[kTile];
+    unsigned long long *s_H = s_acc;
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_acc + N);
+    unsigned long long *s_L = s_acc + N + (N + 1) / 2;
+    const bool smem_hist = FUSED && N <= kFusedHistSteps;
+    const bool smem_cells = smem_hist && N <= kFusedCellSteps && P.ego_side >= 0;
+    if (FUSED) {
+        if (smem_hist)
+            for (int q = tid; q < N; q += THREADS) { s_H[q] = 0ull; s_cnt[q] = 0u; }
+        if (smem_cells)
+            for (int q = tid; q < kTile * N; q += THREADS) s_L[q] = 0ull;
+        for (int q = tid; q < 2 * kTile; q += THREADS) {
+            const int r = q & (kTile - 1);
+            if (q < kTile) {
+                s_prob[0][r] = r < rows ? a.probf[A.traj_off + i0 + r] : 0.0f;
+                s_emass[r] = 0ull;
+                s_ehits[r] = 0u;
+            } else {
+                s_prob[1][r] = r < cols ? a.probf[B.traj_off + j0 + r] : 0.0f;
+            }
+        }
+    }
+    unsigned long long hit_cnt = 0, hit_mass = 0;
 
     const float la = A.hl, wa = A.hw, ra = A.rad, lb = B.hl, wb = B.hw, rb = B.rad;
     const float rc2 = P.rc2 + kEps0;     // (R_a + R_b)^2 plus the absolute slack
     const float ka = 0.5f * (1.0f - kEps);
-    unsigned long long found = 0ull;     // bit MJ m + n: pair (ti + TI m, tj + TJ n) has had its first hit
+    s_found[tid] = 0ull;                 // bit MJ m + n: pair (ti + TI m, tj + TJ n) has had its first hit
     unsigned long long narrow = 0;
-    int buf = 0, active_steps = 0;
-    int k = next_active(s_mask, n_chunks, 0);
-    float4 nxt[SLOTS];
-    if (k >= 0) {
-#pragma unroll
-        for (int q = 0; q < SLOTS; ++q)
-            if (tid + q * THREADS < 2 * kTile) nxt[q] = load_pose(a, A, B, k, i0, j0, rows, cols, tid + q * THREADS);
-    }
-    while (k >= 0) {
-#pragma unroll
-        for (int q = 0; q < SLOTS; ++q) {
-            const int slot = tid + q * THREADS;
-            if (slot < kTile) {
-                s_pa[buf][slot] = make_float4(nxt[q].x, nxt[q].y, ka * fmaf(nxt[q].x, nxt[q].x, nxt[q].y * nxt[q].y), 0.0f);
-                s_ra[buf][slot] = make_float2(nxt[q].z, nxt[q].w);
-            } else if (slot < 2 * kTile) {
-                const float hb = 0.5f * fmaf(1.0f - kEps, fmaf(nxt[q].x, nxt[q].x, nxt[q].y * nxt[q].y), -rc2);
-                s_pb[buf][slot - kTile] = make_float4(nxt[q].x, nxt[q].y, hb, 0.0f);
-                s_rb[buf][slot - kTile] = make_float2(nxt[q].z, nxt[q].w);
+    const int lane = tid & 31, warp = tid >> 5;
+    unsigned short *queue = s_queue[warp];
+    int active_steps = 0;
+    for (;;) {
+        if (tid == 0) {   // the next CH active steps
+            int c = 0, k = next_active(s_mask, n_chunks, s_cursor);
+            while (c < CH && k >= 0) {
+                s_klist[c++] = k;
+                k = next_active(s_mask, n_chunks, k + 1);
             }
-        }
-        const int k_next = next_active(s_mask, n_chunks, k + 1);
-        if (k_next >= 0) {   // the next step's poses load while this step is tested
-#pragma unroll
-            for (int q = 0; q < SLOTS; ++q)
-                if (tid + q * THREADS < 2 * kTile)
-                    nxt[q] = load_pose(a, A, B, k_next, i0, j0, rows, cols, tid + q * THREADS);
+            s_nk = c;
+            s_cursor = k < 0 ? N : k;
         }
         __syncthreads();
-        ++active_steps;
-        float4 pa[MI], pb[MJ];
-#pragma unroll
-        for (int m = 0; m < MI; ++m) pa[m] = s_pa[buf][ti + TI * m];
-#pragma unroll
-        for (int n = 0; n < MJ; ++n) pb[n] = s_pb[buf][tj + TJ * n];
-        unsigned rowhit = 0;                 // bit m: row m of the micro-tile has a broad-phase candidate
-#pragma unroll
-        for (int m = 0; m < MI; ++m) {
-            bool any = false;
-#pragma unroll
-            for (int n = 0; n < MJ; ++n)
-                any |= fmaf(pa[m].x, pb[n].x, fmaf(pa[m].y, pb[n].y, -pb[n].z)) >= pa[m].z;
-            rowhit |= any ? (1u << m) : 0u;
+        const int nk = s_nk;
+        if (nk == 0) break;
+        // stage: every pose of the chunk's steps, all loads issued before any is needed
+#pragma unroll 4
+        for (int e = tid; e < nk * 2 * kTile; e += THREADS) {
+            const int c = e >> 7, q = e & (2 * kTile - 1);
+            const int k = s_klist[c];
+            if (q < kTile) {
+                float x = kFar, y = 0.0f, cc = 1.0f, ss = 0.0f;
+                if (q < rows) {
+                    const long long idx = A.pose_base + (long long)k * A.h + i0 + q;
+                    x = __ldg(a.x + idx); y = __ldg(a.y + idx); cc = __ldg(a.c + idx); ss = __ldg(a.s + idx);
+                }
+                s_pa[c * kTile + q] = make_float4(x, y, ka * fmaf(x, x, y * y), 0.0f);
+                s_ra[c * kTile + q] = make_float2(cc, ss);
+            } else {
+                const int r = q - kTile;
+                float x = -kFar, y = 0.0f, cc = 1.0f, ss = 0.0f;
+                if (r < cols) {
+                    const long long idx = B.pose_base + (long long)k * B.h + j0 + r;
+                    x = __ldg(a.x + idx); y = __ldg(a.y + idx); cc = __ldg(a.c + idx); ss = __ldg(a.s + idx);
+                }
+                s_pb[c * kTile + r] = make_float4(x, y, 0.5f * fmaf(1.0f - kEps, fmaf(x, x, y * y), -rc2), 0.0f);
+                s_rb[c * kTile + r] = make_float2(cc, ss);
+            }
         }
-        while (rowhit) {   // rare: only the flagged rows are re-derived (from shared memory)
-            const int m = __ffs(rowhit) - 1;
-            rowhit &= rowhit - 1;
-            const int i = ti + TI * m;
-            const float4 qa4 = s_pa[buf][i];
-#pragma unroll 1
-            for (int n = 0; n < MJ; ++n) {
-                const unsigned long long bit = 1ull << (MJ * m + n);
-                if (found & bit) continue;
-                const float4 qb4 = s_pb[buf][tj + TJ * n];
-                if (!(fmaf(qa4.x, qb4.x, fmaf(qa4.y, qb4.y, -qb4.z)) >= qa4.z)) continue;
-                const int j = tj + TJ * n;
-                ++narrow;
+        __syncthreads();
+        active_steps += nk;
+        for (int c = 0; c < nk; ++c) {
+            const int k = s_klist[c];
+            const float4 *pa_s = s_pa + c * kTile, *pb_s = s_pb + c * kTile;
+            float4 pa[MI], pb[MJ];
+#pragma unroll
+            for (int m = 0; m < MI; ++m) pa[m] = pa_s[ti + TI * m];
+#pragma unroll
+            for (int n = 0; n < MJ; ++n) pb[n] = pb_s[tj + TJ * n];
+            unsigned rowhit = 0;             // bit m: row m of the micro-tile has a broad-phase candidate
+#pragma unroll
+            for (int m = 0; m < MI; ++m) {
+                bool any = false;
+#pragma unroll
+                for (int n = 0; n < MJ; ++n)
+                    any |= fmaf(pa[m].x, pb[n].x, fmaf(pa[m].y, pb[n].y, -pb[n].z)) >= pa[m].z;
+                rowhit |= any ? (1u << m) : 0u;
+            }
+            // candidates of this thread not yet decided: re-derived from shared memory for flagged rows
+            unsigned long long cand = 0ull;
+            if (rowhit) {
+                const unsigned long long found = s_found[tid];
+                while (rowhit) {
+                    const int m = __ffs(rowhit) - 1;
+                    rowhit &= rowhit - 1;
+                    const float4 qa4 = pa_s[ti + TI * m];
+#pragma unroll
+                    for (int n = 0; n < MJ; ++n) {
+                        const float4 qb4 = pb_s[tj + TJ * n];
+                        if (fmaf(qa4.x, qb4.x, fmaf(qa4.y, qb4.y, -qb4.z)) >= qa4.z) cand |= 1ull << (MJ * m + n);
+                    }
+                }
+                cand &= ~found;
+            }
+            // compact the warp's candidates and test them one per lane (the exact test is long: dense lanes)
+            const int cnt = __popcll(cand);
+            if (!__ballot_sync(0xffffffffu, cnt != 0)) continue;
+            int off = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, off, d);
+                if (lane >= d) off += u;
+            }
+            const int total = __shfl_sync(0xffffffffu, off, 31);
+            off -= cnt;
+            while (cand) {
+                const int bit = __ffsll((long long)cand) - 1;
+                cand &= cand - 1;
+                queue[off++] = (unsigned short)((lane << 6) | bit);
+            }
+            __syncwarp();
+            narrow += total;   // counted once per warp below (lane 0)
+            for (int e = lane; e < total; e += 32) {
+                const int ent = queue[e];
+                const int owner = (warp << 5) | (ent >> 6), bit = ent & 63;
+                const int m = bit / MJ, n = bit - m * MJ;
+                const int i = owner / TJ + TI * m, j = owner % TJ + TJ * n;
+                const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
-                const float2 qa = s_ra[buf][i], qb = s_rb[buf][j];
+                const float2 qa = s_ra[c * kTile + i], qb = s_rb[c * kTile + j];
                 bool hit;
                 switch (P.combo) {
                     case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
@@ -209,20 +273,398 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
                     case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
                     default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
                 }
-                if (hit) {
-                    found |= bit;
-                    a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
+                if (!hit) continue;
+                atomicOr(s_found + owner, 1ull << bit);
+                a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
+                if (FUSED) {   // the risk terms of this first hit (FP32 terms, exact fixed-point sums)
+                    const float pa_ = s_prob[0][i], pb_ = s_prob[1][j];
+                    const unsigned long long w = to_fixed(pa_ * pb_, kFixProb);
+                    ++hit_cnt;
+                    hit_mass += w;
+                    if (smem_hist) {
+                        atomicAdd(s_cnt + k, 1u);
+                        atomicAdd(s_H + k, w);
+                    } else {
+                        atomicAdd(a.acc.count_k + (long long)lo * N + k, 1ull);
+                        atomicAdd(a.acc.H + (long long)lo * N + k, w);
+                    }
+                    if (P.ego_side >= 0) {
+                        const int eg = P.ego_side == 0 ? i : j;             // the EGO hypothesis
+                        const float pco = P.ego_side == 0 ? pb_ : pa_;      // the CO hypothesis
+                        atomicAdd(s_emass + eg, to_fixed(pco, kFixProb));
+                        atomicAdd(s_ehits + eg, 1u);
+                        const unsigned long long lq = to_fixed(neg_log_survival(pco), kFixLog);
+                        if (smem_cells) {
+                            atomicAdd(s_L + eg * N + k, lq);
+                        } else {
+                            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
+                            atomicAdd(a.acc.lsum + ((long long)(e0 + eg) * N + k) * a.n_obj + co, lq);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();   // the chunk's staged poses are no longer read
+    }
+    if (a.counters) {   // every lane of a warp counted the warp's exact tests: lane 0 reports them
+        if ((tid & 31) == 0 && narrow) atomicAdd(a.counters + 1, narrow);
+        if (tid == 0 && active_steps) atomicAdd(a.counters, (unsigned long long)active_steps * kTile * kTile);
+    }
+    if (FUSED) {   // merge the tile's risk accumulators into the global ones
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            hit_cnt += __shfl_xor_sync(0xffffffffu, hit_cnt, d);
+            hit_mass += __shfl_xor_sync(0xffffffffu, hit_mass, d);
+        }
+        if ((tid & 31) == 0 && hit_cnt) {
+            atomicAdd(a.acc.count + lo, hit_cnt);
+            atomicAdd(a.acc.P + lo, hit_mass);
+        }
+        if (smem_hist) {
+            for (int q = tid; q < N; q += THREADS) {
+                if (s_cnt[q]) {
+                    atomicAdd(a.acc.count_k + (long long)lo * N + q, (unsigned long long)s_cnt[q]);
+                    atomicAdd(a.acc.H + (long long)lo * N + q, s_H[q]);
                 }
             }
         }
-        buf ^= 1;
-        k = k_next;
+        if (P.ego_side >= 0) {
+            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
+            for (int q = tid; q < kTile; q += THREADS) {
+                if (s_ehits[q]) {
+                    atomicAdd(a.acc.mass + (long long)(e0 + q) * a.n_obj + co, s_emass[q]);
+                    atomicAdd(a.acc.hits + e0 + q, (unsigned long long)s_ehits[q]);
+                }
+            }
+            if (smem_cells) {
+                for (int q = tid; q < kTile * N; q += THREADS) {
+                    const unsigned long long v = s_L[q];
+                    if (v) {
+                        const int e = q / N, kk = q - e * N;
+                        atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + kk) * a.n_obj + co, v);
+                    }
+                }
+            }
+        }
     }
-    if (a.counters) {
+}
+
+// Fused risk terms of one first hit (i, j) at step k of pair `pair` (FP32 terms, exact fixed-point sums)
+// into the CTA's shared accumulators (or the global ones when they do not fit).
+struct TileRisk {
+    unsigned long long *s_H;
+    unsigned *s_cnt;
+    unsigned long long *s_L;
+    float *pa, *pb;                     // [64] probabilities of the tile's rows / columns
+    unsigned long long *emass;          // [64] per EGO hypothesis of the tile
+    unsigned *ehits;
+    bool hist, cells;
+};
+
+__device__ __forceinline__ void add_hit(const CollideArgs &a, const PairDesc &P, int pair, int N, const TileRisk &R,
+                                        int i0, int j0, int i, int j, int k, unsigned long long &cnt,
+                                        unsigned long long &mass) {
+    const float pa_ = R.pa[i], pb_ = R.pb[j];
+    const unsigned long long w = to_fixed(pa_ * pb_, kFixProb);
+    ++cnt;
+    mass += w;
+    if (R.hist) {
+        atomicAdd(R.s_cnt + k, 1u);
+        atomicAdd(R.s_H + k, w);
+    } else {
+        atomicAdd(a.acc.count_k + (long long)pair * N + k, 1ull);
+        atomicAdd(a.acc.H + (long long)pair * N + k, w);
+    }
+    if (P.ego_side >= 0) {
+        const int e = P.ego_side == 0 ? i : j;                // the EGO hypothesis
+        const float pco = P.ego_side == 0 ? pb_ : pa_;        // the CO hypothesis
+        atomicAdd(R.emass + e, to_fixed(pco, kFixProb));
+        atomicAdd(R.ehits + e, 1u);
+        const unsigned long long lq = to_fixed(neg_log_survival(pco), kFixLog);
+        if (R.cells) {
+            atomicAdd(R.s_L + e * N + k, lq);
+        } else {
+            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
+            atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + k) * a.n_obj + co, lq);
+        }
+    }
+}
+
+// Warp-per-step layout: a CTA of WARPS warps takes a 64 x 64 tile; its active steps are staged CH at a
+// time, and warp w tests steps w, w + WARPS, ... of the chunk on its own (no barrier between steps).  A
+// lane holds an 8 x 16 micro-tile (rows lr + 8 m, columns lc + 4 n with lr = lane / 4, lc = lane % 4), so
+// a warp covers the 4096 pairs of a step and the per-step overhead (candidate compaction) is paid once
+// per 4096 tests.  Candidates are tested one per lane; the earliest overlapping step of each pair is
+// kept with a shared-memory atomicMin, and the first hits are stored (and their risk terms added) once,
+// when the tile is done.
+template <int WARPS, int CH, bool FUSED>
+__global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideArgs a) {
+    constexpr int THREADS = WARPS * 32;
+    constexpr int QCAP = 256;            // candidates compacted per warp per round
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    float4 *s_pa = reinterpret_cast<float4 *>(s_dyn);               // [CH][64] x, y, h_a
+    float4 *s_pb = s_pa + CH * kTile;                                  // [CH][64] x, y, h_b
+    float2 *s_ra = reinterpret_cast<float2 *>(s_pb + CH * kTile);     // [CH][64] c, s
+    float2 *s_rb = s_ra + CH * kTile;
+    int *s_first = reinterpret_cast<int *>(s_rb + CH * kTile);        // [64 * 64] earliest hit step
+    unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(s_first + kTile * kTile);
+    __shared__ unsigned s_mask[kMaxChunks];
+    __shared__ int s_klist[CH];
+    __shared__ int s_nk, s_cursor;
+    __shared__ unsigned short s_queue[WARPS][QCAP];
+
+    const long long g = blockIdx.x;
+    if (g >= a.n_tiles) return;
+    int lo = 0, hi = a.n_pairs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
+    }
+    const PairDesc P = a.pairs[lo];
+    const ObjDesc &A = a.objs[P.a];
+    const ObjDesc &B = a.objs[P.b];
+    const long long t = g - P.tile_start;
+    const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
+    const int i0 = ta * kTile, j0 = tb * kTile;
+    const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lr = lane >> 2, lc = lane & 3;
+    const int N = a.n_steps;
+    const int n_chunks = (N + 31) >> 5;
+
+    const int na = (rows + kBoundTile - 1) / kBoundTile, nb = (cols + kBoundTile - 1) / kBoundTile;
+    const float4 *bA0 = a.bounds + (long long)(A.tile_base + ta * 2) * N;
+    const float4 *bB0 = a.bounds + (long long)(B.tile_base + tb * 2) * N;
+    for (int w = warp; w < n_chunks; w += WARPS) {
+        const int k = (w << 5) + lane;
+        bool act = k < N;
+        if (act && a.cull) {
+            float4 ba = bA0[k];
+            if (na > 1) {
+                const float4 q = bA0[N + k];
+                ba = make_float4(fminf(ba.x, q.x), fminf(ba.y, q.y), fmaxf(ba.z, q.z), fmaxf(ba.w, q.w));
+            }
+            float4 bb = bB0[k];
+            if (nb > 1) {
+                const float4 q = bB0[N + k];
+                bb = make_float4(fminf(bb.x, q.x), fminf(bb.y, q.y), fmaxf(bb.z, q.z), fmaxf(bb.w, q.w));
+            }
+            const float r = P.r_cull;
+            act = (ba.x - r <= bb.z) && (bb.x - r <= ba.z) && (ba.y - r <= bb.w) && (bb.y - r <= ba.w);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) s_mask[w] = m;
+    }
+    if (tid == 0) s_cursor = 0;
+    __syncthreads();
+    if (next_active(s_mask, n_chunks, 0) < 0) return;   // the tiles never come close: nothing to test
+    for (int q = tid; q < kTile * kTile; q += THREADS) s_first[q] = kNoHit;
+
+    const float la = A.hl, wa = A.hw, ra = A.rad, lb = B.hl, wb = B.hw, rb = B.rad;
+    const float rc2 = P.rc2 + kEps0;
+    const float ka = 0.5f * (1.0f - kEps);
+    unsigned long long narrow = 0;
+    int active_steps = 0;
+    unsigned short *queue = s_queue[warp];
+    for (;;) {
+        if (tid == 0) {   // the next CH active steps
+            int c = 0, k = next_active(s_mask, n_chunks, s_cursor);
+            while (c < CH && k >= 0) {
+                s_klist[c++] = k;
+                k = next_active(s_mask, n_chunks, k + 1);
+            }
+            s_nk = c;
+            s_cursor = k < 0 ? N : k;
+        }
+        __syncthreads();
+        const int nk = s_nk;
+        if (nk == 0) break;
+#pragma unroll 4
+        for (int e = tid; e < nk * 2 * kTile; e += THREADS) {
+            const int c = e >> 7, q = e & (2 * kTile - 1);
+            const int k = s_klist[c];
+            if (q < kTile) {
+                float x = kFar, y = 0.0f, cc = 1.0f, ss = 0.0f;
+                if (q < rows) {
+                    const long long idx = A.pose_base + (long long)k * A.h + i0 + q;
+                    x = __ldg(a.x + idx); y = __ldg(a.y + idx); cc = __ldg(a.c + idx); ss = __ldg(a.s + idx);
+                }
+                s_pa[c * kTile + q] = make_float4(x, y, ka * fmaf(x, x, y * y), 0.0f);
+                s_ra[c * kTile + q] = make_float2(cc, ss);
+            } else {
+                const int r = q - kTile;
+                float x = -kFar, y = 0.0f, cc = 1.0f, ss = 0.0f;
+                if (r < cols) {
+                    const long long idx = B.pose_base + (long long)k * B.h + j0 + r;
+                    x = __ldg(a.x + idx); y = __ldg(a.y + idx); cc = __ldg(a.c + idx); ss = __ldg(a.s + idx);
+                }
+                s_pb[c * kTile + r] = make_float4(x, y, 0.5f * fmaf(1.0f - kEps, fmaf(x, x, y * y), -rc2), 0.0f);
+                s_rb[c * kTile + r] = make_float2(cc, ss);
+            }
+        }
+        __syncthreads();
+        active_steps += nk;
+        for (int c = warp; c < nk; c += WARPS) {
+            const int k = s_klist[c];
+            const float4 *pa_s = s_pa + c * kTile, *pb_s = s_pb + c * kTile;
+            float4 pa[8], pb[16];
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) narrow += __shfl_xor_sync(0xffffffffu, narrow, d);
-        if ((tid & 31) == 0 && narrow) atomicAdd(a.counters + 1, narrow);
+            for (int m = 0; m < 8; ++m) pa[m] = pa_s[lr + 8 * m];
+#pragma unroll
+            for (int n = 0; n < 16; ++n) pb[n] = pb_s[lc + 4 * n];
+            unsigned rowhit = 0;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                bool any = false;
+#pragma unroll
+                for (int n = 0; n < 16; ++n)
+                    any |= fmaf(pa[m].x, pb[n].x, fmaf(pa[m].y, pb[n].y, -pb[n].z)) >= pa[m].z;
+                rowhit |= any ? (1u << m) : 0u;
+            }
+            if (!__ballot_sync(0xffffffffu, rowhit != 0)) continue;
+            // this lane's candidates, 16 bits per flagged row (bit 16 m + n)
+            unsigned long long cand_lo = 0ull, cand_hi = 0ull;
+            while (rowhit) {
+                const int m = __ffs(rowhit) - 1;
+                rowhit &= rowhit - 1;
+                const float4 qa4 = pa_s[lr + 8 * m];
+                unsigned bits = 0;
+#pragma unroll
+                for (int n = 0; n < 16; ++n) {
+                    const float4 qb4 = pb_s[lc + 4 * n];
+                    bits |= (fmaf(qa4.x, qb4.x, fmaf(qa4.y, qb4.y, -qb4.z)) >= qa4.z) ? (1u << n) : 0u;
+                }
+                if (m < 4) cand_lo |= (unsigned long long)bits << (16 * m);
+                else cand_hi |= (unsigned long long)bits << (16 * (m - 4));
+            }
+            // compact and test one candidate per lane, in rounds of at most QCAP
+            for (;;) {
+                int cnt = 0;
+                unsigned short mine[8];
+                while (cnt < 8 && (cand_lo | cand_hi)) {
+                    int bit;
+                    if (cand_lo) { bit = __ffsll((long long)cand_lo) - 1; cand_lo &= cand_lo - 1; }
+                    else { bit = 64 + __ffsll((long long)cand_hi) - 1; cand_hi &= cand_hi - 1; }
+                    mine[cnt++] = (unsigned short)((lane << 7) | bit);
+                }
+                if (!__ballot_sync(0xffffffffu, cnt != 0)) break;
+                int off = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, off, d);
+                    if (lane >= d) off += u;
+                }
+                const int total = __shfl_sync(0xffffffffu, off, 31);
+                off -= cnt;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < cnt) queue[off + q] = mine[q];
+                __syncwarp();
+                narrow += total;
+                for (int e = lane; e < total; e += 32) {
+                    const int ent = queue[e];
+                    const int owner = ent >> 7, bit = ent & 127;
+                    const int m = bit >> 4, n = bit & 15;
+                    const int i = (owner >> 2) + 8 * m, j = (owner & 3) + 4 * n;
+                    if (s_first[i * kTile + j] <= k) continue;    // an earlier step already overlaps
+                    const float4 qa4 = pa_s[i], qb4 = pb_s[j];
+                    const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
+                    const float2 qa = s_ra[c * kTile + i], qb = s_rb[c * kTile + j];
+                    bool hit;
+                    switch (P.combo) {
+                        case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
+                        case 1: hit = rect_disc(dx, dy, qa.x, qa.y, la, wa, rb); break;
+                        case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
+                        default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
+                    }
+                    if (hit) atomicMin(s_first + i * kTile + j, k);
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();   // the chunk's staged poses are no longer read
+    }
+    if (a.counters) {   // every lane counted its warp's exact tests: lane 0 reports them
+        if (lane == 0 && narrow) atomicAdd(a.counters + 1, narrow);
         if (tid == 0 && active_steps) atomicAdd(a.counters, (unsigned long long)active_steps * kTile * kTile);
+    }
+    // first hits: store them (and add their risk terms)
+    __shared__ float s_prob[2][kTile];
+    __shared__ unsigned long long s_emass[kTile];
+    __shared__ unsigned s_ehits[kTile];
+    TileRisk R;
+    R.s_H = s_acc;
+    R.s_cnt = reinterpret_cast<unsigned *>(s_acc + N);
+    R.s_L = s_acc + N + (N + 1) / 2;
+    R.pa = s_prob[0];
+    R.pb = s_prob[1];
+    R.emass = s_emass;
+    R.ehits = s_ehits;
+    R.hist = FUSED && N <= kFusedHistSteps;
+    R.cells = R.hist && N <= kFusedCellSteps && P.ego_side >= 0;
+    if (FUSED) {
+        if (R.hist)
+            for (int q = tid; q < N; q += THREADS) { R.s_H[q] = 0ull; R.s_cnt[q] = 0u; }
+        if (R.cells)
+            for (int q = tid; q < kTile * N; q += THREADS) R.s_L[q] = 0ull;
+        for (int q = tid; q < 2 * kTile; q += THREADS) {
+            const int r = q & (kTile - 1);
+            if (q < kTile) {
+                s_prob[0][r] = r < rows ? a.probf[A.traj_off + i0 + r] : 0.0f;
+                s_emass[r] = 0ull;
+                s_ehits[r] = 0u;
+            } else {
+                s_prob[1][r] = r < cols ? a.probf[B.traj_off + j0 + r] : 0.0f;
+            }
+        }
+        __syncthreads();
+    }
+    unsigned long long hit_cnt = 0, hit_mass = 0;
+    for (int q = tid; q < kTile * kTile; q += THREADS) {
+        const int k = s_first[q];
+        if (k == kNoHit) continue;
+        const int i = q >> 6, j = q & (kTile - 1);
+        a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
+        if (FUSED) add_hit(a, P, lo, N, R, i0, j0, i, j, k, hit_cnt, hit_mass);
+    }
+    if (FUSED) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            hit_cnt += __shfl_xor_sync(0xffffffffu, hit_cnt, d);
+            hit_mass += __shfl_xor_sync(0xffffffffu, hit_mass, d);
+        }
+        if (lane == 0 && hit_cnt) {
+            atomicAdd(a.acc.count + lo, hit_cnt);
+            atomicAdd(a.acc.P + lo, hit_mass);
+        }
+        __syncthreads();
+        if (R.hist) {
+            for (int q = tid; q < N; q += THREADS) {
+                if (R.s_cnt[q]) {
+                    atomicAdd(a.acc.count_k + (long long)lo * N + q, (unsigned long long)R.s_cnt[q]);
+                    atomicAdd(a.acc.H + (long long)lo * N + q, R.s_H[q]);
+                }
+            }
+        }
+        if (P.ego_side >= 0) {
+            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
+            for (int q = tid; q < kTile; q += THREADS) {
+                if (s_ehits[q]) {
+                    atomicAdd(a.acc.mass + (long long)(e0 + q) * a.n_obj + co, s_emass[q]);
+                    atomicAdd(a.acc.hits + e0 + q, (unsigned long long)s_ehits[q]);
+                }
+            }
+            if (R.cells) {
+                for (int q = tid; q < kTile * N; q += THREADS) {
+                    const unsigned long long v = R.s_L[q];
+                    if (v) {
+                        const int e = q / N, kk = q - e * N;
+                        atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + kk) * a.n_obj + co, v);
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -249,16 +691,51 @@ cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int THREADS, int MI, int MJ, int CH, bool FUSED>
+cudaError_t launch_variant(const CollideArgs &a, cudaStream_t st) {
+    size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2));
+    if (FUSED) {
+        if (a.n_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.n_steps + (a.n_steps + 1) / 2);
+        if (a.n_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.n_steps;
+    }
+    if (smem > 32 * 1024) {   // dynamic + static (about 5 KiB) above the default 48 KiB needs the opt-in
+        cudaError_t e = cudaFuncSetAttribute(collide_kernel<THREADS, MI, MJ, CH, FUSED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    collide_kernel<THREADS, MI, MJ, CH, FUSED><<<(unsigned)a.n_tiles, THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int WARPS, int CH, bool FUSED>
+cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
+    size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2)) + sizeof(int) * kTile * kTile;
+    if (FUSED) {
+        if (a.n_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.n_steps + (a.n_steps + 1) / 2);
+        if (a.n_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.n_steps;
+    }
+    if (smem > 32 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(collide_warp_kernel<WARPS, CH, FUSED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    collide_warp_kernel<WARPS, CH, FUSED><<<(unsigned)a.n_tiles, WARPS * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     int n_sm = 152, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (a.n_tiles >= 32LL * n_sm)   // many tiles: throughput, fewest loads per test
-        collide_kernel<64, 8, 8><<<(unsigned)a.n_tiles, 64, 0, st>>>(a);
-    else                            // few tiles: latency, 8 warps share each tile's tests
-        collide_kernel<256, 4, 4><<<(unsigned)a.n_tiles, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    // 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests) measured faster than 8 x 8 with
+    // 64 threads on every workload tried, from 1,445 to 507,904 tiles; variant 2 keeps the latter selectable.
+    (void)n_sm;
+    const bool many = a.variant == 2;
+    if (a.variant == 3)
+        return a.probf ? launch_warp_variant<4, 8, true>(a, st) : launch_warp_variant<4, 8, false>(a, st);
+    if (a.probf) return many ? launch_variant<64, 8, 8, 8, true>(a, st) : launch_variant<256, 4, 4, 16, true>(a, st);
+    return many ? launch_variant<64, 8, 8, 8, false>(a, st) : launch_variant<256, 4, 4, 16, false>(a, st);
 }
 
 }  // namespace mhc

@@ -73,19 +73,6 @@ struct BoundsArgs {
     float4 *bounds;
 };
 
-struct CollideArgs {
-    const ObjDesc *objs;
-    const PairDesc *pairs;
-    int n_pairs;
-    long long n_tiles;        // total collision tiles over all pairs
-    int n_steps;
-    int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
-    const float *x, *y, *c, *s;
-    const float4 *bounds;
-    int16_t *table;
-    unsigned long long *counters;  // optional: [0] broad-phase tests executed, [1] narrow-phase tests
-};
-
 // Risk accumulators: one contiguous block of 64-bit words, zeroed before every assessment.  Masses and
 // log-survival sums are unsigned fixed point (kFixProb / kFixLog fractional bits): every term is an FP32
 // value converted exactly, and integer atomics add them exactly and in any order.
@@ -102,8 +89,28 @@ struct RiskScratch {
     unsigned long long *attr_obj;  // [n_obj]
     unsigned long long *attr_step; // [N]
     double *scalars;               // [4]
+    unsigned long long *n_escape;  // [1] collision-free EGO hypotheses
+    unsigned long long *done;      // [1] EGO-walk CTAs finished (the last one converts the totals)
     unsigned long long *base;      // first word of the block
     long long n_words;             // words to zero
+};
+
+struct CollideArgs {
+    const ObjDesc *objs;
+    const PairDesc *pairs;
+    int n_pairs;
+    long long n_tiles;        // total collision tiles over all pairs
+    int n_steps;
+    int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
+    int variant;              // 0: chosen by tile count, 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8
+    const float *x, *y, *c, *s;
+    const float4 *bounds;
+    int16_t *table;
+    unsigned long long *counters;  // optional: [0] broad-phase tests executed, [1] narrow-phase tests
+    // fused risk accumulation at first-hit time (probf null: table only)
+    const float *probf;            // [n_traj] FP32 probabilities
+    RiskScratch acc;               // accumulators, zeroed beforehand
+    int n_obj;
 };
 
 struct RiskArgs {
@@ -125,10 +132,32 @@ struct RiskArgs {
     int *escape, *n_escape;
 };
 
+// ---- per-hit risk accumulation helpers (shared by the risk scan and the fused collision kernel) ----
+constexpr float kMaxLogTerm = 4194304.0f;    // 2^22: -log(1 - p) for p = 1 (a certain trajectory)
+
+// Exact unsigned fixed point of a finite w >= 0 with `frac` fractional bits (round to nearest).
+__device__ __forceinline__ unsigned long long to_fixed(float w, int frac) {
+    const unsigned b = __float_as_uint(w);
+    const int e = (int)(b >> 23);
+    if (e == 0) return 0ull;                 // zero (and denormals, below 2^-126)
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+    const int sh = e - 150 + frac;           // w = m 2^(e - 150)
+    if (sh >= 0) return m << sh;
+    if (sh <= -25) return 0ull;
+    return (m + (1ull << (-sh - 1))) >> -sh;
+}
+
+// -log(1 - p) in FP32, capped for p -> 1
+__device__ __forceinline__ float neg_log_survival(float p) {
+    return p >= 1.0f ? kMaxLogTerm : fminf(-log1pf(-p), kMaxLogTerm);
+}
+
 cudaError_t launch_generate(const GenArgs &a, cudaStream_t st);
 cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st);
 cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st);   // table[0, n) = -1
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);               // stores first hits only
+cudaError_t launch_risk_prepare(const RiskArgs &a, cudaStream_t st);             // zero + normalise
+cudaError_t launch_risk_tail(const RiskArgs &a, cudaStream_t st);                // ego walk + finish
 cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st);
 
 }  // namespace mhc

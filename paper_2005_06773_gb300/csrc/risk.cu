@@ -9,7 +9,7 @@
 //            survival factor 1 - q = exp(-sum) contributes S q and leaves S (1 - q), S being the survival
 //            product of the earlier cells -- exactly the entry-by-entry scaling of Eq. p21 summed over
 //            the cell (telescoping); plus the per-object independence measure and the scalar totals
-//   finish   escape routes ranked by probability (Section VI-A) and the conversion of the totals
+//            and the escape-route ranks (Section VI-A); its last CTA converts the totals
 //
 // Collisions are rare and scattered inside a warp, so the per-hit work uses only FP32 and integer
 // instructions: each term (p_a p_b, p, -log(1 - p)) is formed in FP32 and added exactly as unsigned
@@ -22,27 +22,9 @@ namespace {
 
 constexpr int kMaxSmemSteps = 1024;
 constexpr int kMaxSmemCells = 256;           // 64 x 256 cells x 8 B = 128 KiB of dynamic shared memory
-constexpr float kMaxLogTerm = 4194304.0f;    // 2^22: -log(1 - p) for p = 1 (a certain trajectory)
-
-// Exact unsigned fixed point of a finite w >= 0 with `frac` fractional bits (round to nearest).
-__device__ __forceinline__ unsigned long long to_fixed(float w, int frac) {
-    const unsigned b = __float_as_uint(w);
-    const int e = (int)(b >> 23);
-    if (e == 0) return 0ull;                 // zero (and denormals, below 2^-126)
-    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
-    const int sh = e - 150 + frac;           // w = m 2^(e - 150)
-    if (sh >= 0) return m << sh;
-    if (sh <= -25) return 0ull;
-    return (m + (1ull << (-sh - 1))) >> -sh;
-}
-
+// value of a fixed-point sum with `frac` fractional bits (the scale is an exact power of two)
 __device__ __forceinline__ double from_fixed(unsigned long long v, int frac) {
-    return __ull2double_rn(v) * exp2((double)-frac);
-}
-
-// -log(1 - p) in FP32, capped for p -> 1
-__device__ __forceinline__ float neg_log_survival(float p) {
-    return p >= 1.0f ? kMaxLogTerm : fminf(-log1pf(-p), kMaxLogTerm);
+    return __ull2double_rn(v) * (1.0 / (double)(1ull << frac));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -197,12 +179,38 @@ __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
     }
 }
 
-// One warp per EGO hypothesis.  The (step, object) cells are read in ascending order 32 at a time; a chunk
-// with a non-empty cell gets an exclusive warp prefix product of the survival factors (1 - q), so each
-// cell knows the survival S of every earlier cell and contributes S q.
+// Writes the totals of the assessment into the caller's outputs (fixed point -> double).
+__device__ void convert_totals(const RiskArgs &a, int t, int nt) {
+    const long long npn = (long long)a.n_pairs * a.n_steps;
+    for (long long q = t; q < npn; q += nt) {
+        if (a.count_k) a.count_k[q] = (long long)a.acc.count_k[q];
+        if (a.H) a.H[q] = from_fixed(a.acc.H[q], kFixProb);
+    }
+    for (int q = t; q < a.n_pairs; q += nt) {
+        if (a.count) a.count[q] = (long long)a.acc.count[q];
+        if (a.P) a.P[q] = from_fixed(a.acc.P[q], kFixProb);
+    }
+    for (int q = t; q < a.n_obj; q += nt)
+        if (a.attr_obj) a.attr_obj[q] = from_fixed(a.acc.attr_obj[q], kFixProb);
+    for (int q = t; q < a.n_steps; q += nt)
+        if (a.attr_step) a.attr_step[q] = from_fixed(a.acc.attr_step[q], kFixProb);
+    if (t < 4 && a.scalars) a.scalars[t] = t < 3 ? a.acc.scalars[t] : 0.0;
+    if (t == 0 && a.n_escape) *a.n_escape = (int)*a.acc.n_escape;
+}
+
+// One warp per EGO hypothesis.
+//  * collision-free hypothesis: its escape-route rank (Section VI-A) = the number of collision-free
+//    hypotheses more probable than it, ties by index, counted 32 at a time with ballots on integer keys
+//    (probabilities are non-negative, so their bit patterns order like the values);
+//  * otherwise the chronological walk: the (step, object) cells are read in ascending order 32 at a time,
+//    128 per group with the four loads in flight together; a chunk with a non-empty cell gets an exclusive
+//    warp prefix product of the survival factors (1 - q), so each cell knows the survival S of every
+//    earlier cell and contributes S q.
+// The last CTA to finish converts the totals.
 __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
     extern __shared__ unsigned long long s_attr[];   // [n_obj] then [N], fixed point
     __shared__ double s_tot[3][2];
+    __shared__ bool s_last;
     const int N = a.n_steps, n_obj = a.n_obj;
     const bool smem = (n_obj + N) <= 4096;
     if (smem) {
@@ -218,7 +226,23 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
         pe = a.prob[E.traj_off + i];
         const float pef = a.probf[E.traj_off + i];
         hits = a.acc.hits[i];
-        if (hits) {
+        if (!hits) {
+            if (a.escape) {
+                const long long key = __double_as_longlong(pe);
+                int rank = 0;
+                for (int q0 = 0; q0 < a.h_e; q0 += 32) {
+                    const int q = q0 + lane;
+                    bool above = false;
+                    if (q < a.h_e && a.acc.hits[q] == 0ull) {
+                        const long long kq = __double_as_longlong(a.prob[E.traj_off + q]);
+                        above = kq > key || (kq == key && q < i);
+                    }
+                    rank += __popc(__ballot_sync(0xffffffffu, above));
+                }
+                if (lane == 0) a.escape[rank] = i;
+            }
+            if (lane == 0) atomicAdd(a.acc.n_escape, 1ull);
+        } else {
             // per-object masses: naive sum and independence product
             double surv = 1.0, mass_sum = 0.0;
             const unsigned long long *ms = a.acc.mass + (long long)i * n_obj;
@@ -235,33 +259,42 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
             const unsigned long long *lc = a.acc.lsum + (long long)i * N * n_obj;
             const long long cells = (long long)N * n_obj;
             double carry = 1.0, part = 0.0;   // carry: survival product of every cell before the chunk
-            for (long long c0 = 0; c0 < cells; c0 += 32) {
-                const long long c = c0 + lane;
-                const unsigned long long lf = c < cells ? lc[c] : 0ull;
-                if (!__ballot_sync(0xffffffffu, lf != 0ull)) continue;     // empty cells change nothing
-                const float qf = lf ? -expm1f(-(float)lf * (1.0f / 1099511627776.0f)) : 0.0f;  // 2^-40
-                double incl = 1.0 - (double)qf;
+            for (long long g0 = 0; g0 < cells; g0 += 128) {
+                unsigned long long lv[4];
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const double u = __shfl_up_sync(0xffffffffu, incl, d);
-                    if (lane >= d) incl *= u;
+                for (int u = 0; u < 4; ++u) {
+                    const long long c = g0 + 32 * u + lane;
+                    lv[u] = c < cells ? lc[c] : 0ull;
                 }
-                double excl = __shfl_up_sync(0xffffffffu, incl, 1);
-                if (lane == 0) excl = 1.0;
-                const double eff = carry * excl * (double)qf;
-                part += eff;
-                if (lf) {
-                    const int k = (int)(c / n_obj), b = (int)(c - (long long)k * n_obj);
-                    const unsigned long long w = to_fixed(pef * (float)eff, kFixProb);
-                    if (smem) {
-                        atomicAdd(s_attr + b, w);
-                        atomicAdd(s_attr + n_obj + k, w);
-                    } else {
-                        atomicAdd(a.acc.attr_obj + b, w);
-                        atomicAdd(a.acc.attr_step + k, w);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long lf = lv[u];
+                    if (!__ballot_sync(0xffffffffu, lf != 0ull)) continue;     // empty cells change nothing
+                    const long long c = g0 + 32 * u + lane;
+                    const float qf = lf ? -expm1f(-(float)lf * (1.0f / 1099511627776.0f)) : 0.0f;  // 2^-40
+                    double incl = 1.0 - (double)qf;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const double v = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (lane >= d) incl *= v;
                     }
+                    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+                    if (lane == 0) excl = 1.0;
+                    const double eff = carry * excl * (double)qf;
+                    part += eff;
+                    if (lf) {
+                        const int k = (int)(c / n_obj), b = (int)(c - (long long)k * n_obj);
+                        const unsigned long long w = to_fixed(pef * (float)eff, kFixProb);
+                        if (smem) {
+                            atomicAdd(s_attr + b, w);
+                            atomicAdd(s_attr + n_obj + k, w);
+                        } else {
+                            atomicAdd(a.acc.attr_obj + b, w);
+                            atomicAdd(a.acc.attr_step + k, w);
+                        }
+                    }
+                    carry *= __shfl_sync(0xffffffffu, incl, 31);
                 }
-                carry *= __shfl_sync(0xffffffffu, incl, 31);
             }
             cond = warp_sum(part);
         }
@@ -286,68 +319,40 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
             if (v) atomicAdd(q < n_obj ? a.acc.attr_obj + q : a.acc.attr_step + (q - n_obj), v);
         }
     }
+    // the last CTA converts the totals once every CTA's atomics are visible
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.acc.done, 1ull) == (unsigned long long)gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        convert_totals(a, threadIdx.x, blockDim.x);
+    }
 }
 
-// single CTA: escape-route ranking and the conversion of the totals into the caller's outputs
-__global__ void __launch_bounds__(1024) finish_kernel(const RiskArgs a) {
-    const int he = a.h_e;
-    const ObjDesc &E = a.objs[a.ego];
-    const double *pe = a.prob + E.traj_off;
-    // Probabilities are non-negative, so their IEEE bit patterns order like the values: ranking compares
-    // 64-bit integer keys (integer pipe) instead of doubles.  Key -1 marks a hypothesis that collides.
-    constexpr int kCached = 4096;
-    __shared__ long long s_key[kCached];
-    __shared__ int s_n;
-    const bool cached = he <= kCached;
-    if (threadIdx.x == 0) s_n = 0;
-    if (cached)
-        for (int i = threadIdx.x; i < he; i += blockDim.x)
-            s_key[i] = a.acc.hits[i] == 0ull ? __double_as_longlong(pe[i]) : -1ll;
-    __syncthreads();
-    for (int i = threadIdx.x; i < he; i += blockDim.x) {
-        if (a.acc.hits[i] != 0ull) continue;
-        atomicAdd(&s_n, 1);
-        if (!a.escape) continue;
-        const long long key = __double_as_longlong(pe[i]);
-        int rank = 0;
-        if (cached) {
-            for (int q = 0; q < he; ++q) {
-                const long long kq = s_key[q];
-                rank += (kq > key || (kq == key && q < i)) ? 1 : 0;
-            }
-        } else {
-            for (int q = 0; q < he; ++q) {
-                if (a.acc.hits[q] != 0ull) continue;
-                const long long kq = __double_as_longlong(pe[q]);
-                rank += (kq > key || (kq == key && q < i)) ? 1 : 0;
-            }
-        }
-        a.escape[rank] = i;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && a.n_escape) *a.n_escape = s_n;
-    const long long npn = (long long)a.n_pairs * a.n_steps;
-    for (long long q = threadIdx.x; q < npn; q += blockDim.x) {
-        if (a.count_k) a.count_k[q] = (long long)a.acc.count_k[q];
-        if (a.H) a.H[q] = from_fixed(a.acc.H[q], kFixProb);
-    }
-    for (int q = threadIdx.x; q < a.n_pairs; q += blockDim.x) {
-        if (a.count) a.count[q] = (long long)a.acc.count[q];
-        if (a.P) a.P[q] = from_fixed(a.acc.P[q], kFixProb);
-    }
-    for (int q = threadIdx.x; q < a.n_obj; q += blockDim.x)
-        if (a.attr_obj) a.attr_obj[q] = from_fixed(a.acc.attr_obj[q], kFixProb);
-    for (int q = threadIdx.x; q < a.n_steps; q += blockDim.x)
-        if (a.attr_step) a.attr_step[q] = from_fixed(a.acc.attr_step[q], kFixProb);
-    if (threadIdx.x < 4 && a.scalars) a.scalars[threadIdx.x] = threadIdx.x < 3 ? a.acc.scalars[threadIdx.x] : 0.0;
-}
+// Without EGO hypotheses to walk (h_e == 0 cannot happen for a valid scenario) the totals still convert.
+__global__ void __launch_bounds__(256) totals_kernel(const RiskArgs a) { convert_totals(a, threadIdx.x, 256); }
 
 }  // namespace
 
-cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st) {
+cudaError_t launch_risk_prepare(const RiskArgs &a, cudaStream_t st) {
     const int prep_blocks = a.n_obj > 304 ? a.n_obj : 304;
     prepare_kernel<<<prep_blocks, 256, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_risk_tail(const RiskArgs &a, cudaStream_t st) {
+    if (a.h_e > 0) {
+        const size_t smem = (a.n_obj + a.n_steps) <= 4096 ? 8 * (size_t)(a.n_obj + a.n_steps) : 0;
+        ego_kernel<<<(a.h_e + 1) / 2, 64, smem, st>>>(a);
+    } else {
+        totals_kernel<<<1, 256, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st) {
+    cudaError_t e = launch_risk_prepare(a, st);
     if (e != cudaSuccess) return e;
     if (a.n_tiles > 0) {
         if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -361,13 +366,7 @@ cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st) {
         scan_kernel<<<(unsigned)a.n_tiles, 64, smem, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (a.h_e > 0) {
-        const size_t smem = (a.n_obj + a.n_steps) <= 4096 ? 8 * (size_t)(a.n_obj + a.n_steps) : 0;
-        ego_kernel<<<(a.h_e + 1) / 2, 64, smem, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    finish_kernel<<<1, 1024, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_risk_tail(a, st);
 }
 
 }  // namespace mhc

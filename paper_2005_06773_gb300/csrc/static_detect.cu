@@ -199,7 +199,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
     b.bounds = d_bounds;
     if ((e = launch_fill_table(table, entries, st)) != cudaSuccess) return cuda_fail(e, "table fill launch");
     if ((e = launch_bounds(b, st)) != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
-    CollideArgs c;
+    CollideArgs c{};
     c.objs = d_objs;
     c.pairs = d_pairs;
     c.n_pairs = n_pairs;

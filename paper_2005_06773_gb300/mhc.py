@@ -19,6 +19,7 @@ from . import build as _build
 MHC_OK, MHC_PENDING = 0, 1
 MHC_OPT_CULL = 1
 MHC_OPT_PROFILE = 2
+MHC_OPT_COLLIDE_VARIANT = 3
 KERNEL_CLASSES = ("generate", "bounds", "collide", "risk")
 
 
@@ -78,6 +79,10 @@ def _load():
     L.mhc_generate_trajectories.argtypes = [c_void_p, POINTER(MhcScenario), POINTER(MhcPoses), c_void_p]
     L.mhc_detect_collisions.argtypes = [c_void_p, POINTER(MhcScenario), POINTER(MhcPoses), c_void_p, c_void_p]
     L.mhc_assess_risk.argtypes = [c_void_p, POINTER(MhcScenario), c_void_p, c_void_p, POINTER(MhcRisk), c_void_p]
+    L.mhc_evaluate.argtypes = [c_void_p, POINTER(MhcScenario), c_void_p, POINTER(MhcPoses), c_void_p,
+                               POINTER(MhcRisk), c_void_p]
+    L.mhc_autotune.argtypes = [c_void_p, POINTER(MhcScenario), POINTER(MhcPoses), c_void_p, c_int,
+                               POINTER(c_int32), POINTER(c_int32), c_void_p]
     L.mhc_run_bytes.argtypes = [POINTER(MhcScenario), POINTER(c_size_t)]
     L.mhc_run.argtypes = [c_void_p, POINTER(MhcScenario), c_void_p, POINTER(MhcRisk), c_void_p]
     return L
@@ -284,6 +289,36 @@ def assess(ctx: Context, sc, table: torch.Tensor, weights=None, out=None, stream
     _check(lib.mhc_assess_risk(ctx.h, cs.ref, table.data_ptr(), w.ptr, ctypes.byref(rs), _stream(stream)),
            "mhc_assess_risk")
     return out
+
+
+def autotune(ctx: Context, sc, poses, table=None, fused: bool = True, stream=None):
+    """Times the collision kernel's layouts (and culling on / off) on this scenario, in the fused path of
+    evaluate / run (fused=True) or of detect; later calls on `ctx` use the fastest for its size class.
+    Returns (variant, cull)."""
+    cs = as_c(sc)
+    if table is None:
+        table = torch.empty(layout(cs)["n_entries"], dtype=torch.int16, device=poses["x"].device)
+    ps = _poses_struct(poses)
+    v, c = c_int32(), c_int32()
+    _check(lib.mhc_autotune(ctx.h, cs.ref, ctypes.byref(ps), table.data_ptr(), int(fused), ctypes.byref(v),
+                            ctypes.byref(c), _stream(stream)), "mhc_autotune")
+    return v.value, c.value
+
+
+def evaluate(ctx: Context, sc, poses=None, table=None, weights=None, out=None, stream=None):
+    """The whole method on device buffers in one call (fused collision + risk accumulation).
+    Returns (poses, table, risk outputs)."""
+    cs = as_c(sc)
+    poses = alloc_poses(cs.sc) if poses is None else poses
+    if table is None:
+        table = torch.empty(layout(cs)["n_entries"], dtype=torch.int16, device=poses["x"].device)
+    out = alloc_risk(cs, device=table.device) if out is None else out
+    ps = _poses_struct(poses)
+    rs = _risk_struct(out)
+    w = weights if isinstance(weights, CWeights) else CWeights(weights)
+    _check(lib.mhc_evaluate(ctx.h, cs.ref, w.ptr, ctypes.byref(ps), table.data_ptr(), ctypes.byref(rs),
+                            _stream(stream)), "mhc_evaluate")
+    return poses, table, out
 
 
 def run(ctx: Context, sc, weights=None, out=None, stream=None) -> Dict[str, torch.Tensor]:

@@ -162,6 +162,72 @@ def test_run_equals_separate_calls(mhc, ctx, orc):
             np.testing.assert_array_equal(a, b, err_msg=k)
 
 
+@pytest.mark.parametrize("name", ["mixed_small", "ragged", "ego_only_ego2_n70", "paper_s1", "ped_accel"])
+def test_fused_evaluate_equals_separate_calls(mhc, ctx, name):
+    """mhc_evaluate accumulates the risk terms inside the collision kernel; the result must equal generate +
+    detect + assess: tables and every fixed-point sum bit for bit, the FP64 scalar totals to 1e-12."""
+    sc = scene(name)
+    w = S.random_weights(sc, 11)
+    p = mhc.generate(ctx, sc)
+    t = mhc.detect(ctx, sc, p)
+    r1 = mhc.assess(ctx, sc, t, weights=w)
+    p2, t2, r2 = mhc.evaluate(ctx, sc, weights=w)
+    torch.cuda.synchronize()
+    for k in p:
+        assert torch.equal(p[k], p2[k])
+    assert torch.equal(t, t2)
+    for k in r1:
+        a, b = r1[k].cpu().numpy(), r2[k].cpu().numpy()
+        if k == "scalars":
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-18)
+        else:
+            np.testing.assert_array_equal(a, b, err_msg=k)
+
+
+@pytest.mark.parametrize("name", ["mixed_small", "ragged", "ego_only_ego2_n70", "paper_s1", "kinematic"])
+def test_collision_variants_agree(mhc, ctx, name):
+    """Every thread layout of the collision kernel (and culling on / off) gives the same table and, fused,
+    the same risk outputs."""
+    sc = scene(name)
+    p = mhc.generate(ctx, sc)
+    ref_t, ref_r = None, None
+    try:
+        for variant in (1, 2, 3):
+            for cull in (1, 0):
+                ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, variant)
+                ctx.set_option(mhc.MHC_OPT_CULL, cull)
+                t = mhc.detect(ctx, sc, p).cpu().numpy()
+                _, _, r = mhc.evaluate(ctx, sc, poses=p)
+                r = {k: v.cpu().numpy() for k, v in r.items()}
+                if ref_t is None:
+                    ref_t, ref_r = t, r
+                    continue
+                assert np.array_equal(t, ref_t), (variant, cull)
+                for k in r:
+                    if k == "scalars":
+                        np.testing.assert_allclose(r[k], ref_r[k], rtol=1e-12, atol=1e-18)
+                    else:
+                        np.testing.assert_array_equal(r[k], ref_r[k], err_msg=f"{k} variant {variant} cull {cull}")
+    finally:
+        ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, 0)
+        ctx.set_option(mhc.MHC_OPT_CULL, 1)
+
+
+def test_autotune_picks_a_layout_and_keeps_results(mhc):
+    sc = scene("mixed_small")
+    c = mhc.Context(0, 256 << 20)
+    try:
+        p = mhc.generate(c, sc)
+        before = mhc.detect(c, sc, p).clone()
+        v, cull = mhc.autotune(c, sc, p)
+        assert v in (1, 2, 3) and cull in (0, 1)
+        after = mhc.detect(c, sc, p)
+        torch.cuda.synchronize()
+        assert torch.equal(before, after)
+    finally:
+        c.close()
+
+
 def test_deterministic_and_stream_independent(mhc, ctx):
     sc = scene("mixed_small")
     s2 = torch.cuda.Stream()
