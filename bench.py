@@ -275,6 +275,79 @@ def measure_workload(mhc, torch, sc, dev, steps, flush, peak):
     return out
 
 
+def measure_batch(mhc, torch, dev, steps, flush, count=256):
+    """The uneven batch (256 scenarios, 2-24 objects, 64-1024 hypotheses, 20-50 steps) three ways, device
+    time per batch with CUDA events (L2 flushed before each): a plan replayed as one CUDA graph, one
+    mhc_evaluate_batch call, and the plain path of one mhc_evaluate call per scenario."""
+    from paper_2005_06773_gb300 import scenarios as S
+    batch = S.batch_scenarios(seed=3, count=count)
+    cb = mhc.as_batch(batch)
+    info, sls = mhc.batch_slices(cb)
+    tests = sum(sc.n_tests() for sc in batch)
+    stream = torch.cuda.current_stream(dev)
+    ctx = mhc.Context(dev.index or 0, int(info["scratch"]) + (64 << 20))
+    poses, table, out = mhc.alloc_batch(info, dev)
+    mhc.evaluate_batch(ctx, cb, poses, table, out=out, stream=stream)     # poses for the autotuner
+    tuned = mhc.autotune_batch(ctx, cb, poses, table, stream=stream)
+    plan = mhc.Plan(ctx, cb, graph=True, buffers=(poses, table, out))
+
+    def timed(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        walls = []
+        for q in range(n):
+            flush.zero_()
+            t0 = time.perf_counter()
+            ev[q][0].record(stream)
+            fn()
+            ev[q][1].record(stream)
+            walls.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return statistics.median(ms), 1e3 * statistics.median(walls)
+
+    g_ms, g_host = timed(lambda: plan.launch(stream), steps)
+    ctx.counters(reset=True)
+    ctx.profile_read(reset=True)
+    ctx.profile(True)
+    b_ms, b_host = timed(lambda: mhc.evaluate_batch(ctx, cb, poses, table, out=out, stream=stream), steps)
+    ctx.profile(False)
+    prof = ctx.profile_read(reset=True)
+    executed, narrow = ctx.counters(reset=True)
+    n_calls = steps + 2
+    # plain path: one mhc_evaluate per scenario into its own slice of the same buffers
+    singles = []
+    for sc, sl in zip(cb.items, sls):
+        n_pose = int(sum(o.n_hyp for o in sc.sc.objects)) * sc.sc.n_steps
+        singles.append((sc, {k: v[sl["pose0"]: sl["pose0"] + n_pose] for k, v in poses.items()},
+                        table[sl["entry0"]:], mhc.alloc_risk(sc, device=dev)))
+
+    def plain():
+        for sc, p, t, r in singles:
+            mhc.evaluate(ctx, sc, p, t, out=r, stream=stream)
+    p_ms, p_host = timed(plain, max(3, steps // 2))
+    plan.close()
+    ctx.close()
+    del poses, table, out, singles
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"{count} uneven scenarios (seed 3): 2-24 objects (70 % cars), 64-1024 hypotheses "
+                    "(log-uniform), 20-50 steps of 0.1 s, all object pairs",
+        "tests_per_batch": tests, "entries": info["n_entries"], "hypotheses": info["n_traj"],
+        "collide_layout": {"variant": tuned[0], "cull": tuned[1], "chosen_by": "mhc_autotune_batch"},
+        "graph": {"ms_per_batch": g_ms, "scenarios_per_s": count / (g_ms / 1e3), "tests_per_s": tests / (g_ms / 1e3),
+                  "host_ms_per_launch": g_host},
+        "batch_call": {"ms_per_batch": b_ms, "scenarios_per_s": count / (b_ms / 1e3),
+                       "tests_per_s": tests / (b_ms / 1e3), "host_ms_per_call": b_host,
+                       "kernels_ms_per_batch": {k: v[0] / n_calls for k, v in prof.items()},
+                       "executed_tests_per_batch": executed / n_calls, "narrow_tests_per_batch": narrow / n_calls},
+        "plain_per_scenario": {"ms_per_batch": p_ms, "scenarios_per_s": count / (p_ms / 1e3),
+                               "tests_per_s": tests / (p_ms / 1e3), "host_ms_per_batch": p_host},
+    }
+
+
 def run_mhc(args):
     import torch
     import torch.distributed as dist
@@ -407,6 +480,7 @@ def run_mhc(args):
             "paper_s2": dict(measure_workload(mhc, torch, S.paper_s1s2(10, 6), dev, 50, flush, peak),
                              workload="paper Table I S2 shape: EGO 2058 x 10 CO 42, 100 steps of 20 ms, EGO-only"),
         }
+        line["batch"] = measure_batch(mhc, torch, dev, 10, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD == "intersection11":
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:

@@ -44,7 +44,8 @@ enum { MHC_ALL_PAIRS = 0, MHC_EGO_ONLY = 1 };     /* which object pairs are test
 enum { MHC_MODEL_OT = 0, MHC_MODEL_KIN = 1 };     /* vehicle motion model */
 #define MHC_PED_ACCEL_GRID 1                       /* object flag: pedestrian grid_a holds accelerations */
 #define MHC_MAX_STEPS 32767                        /* first-collision steps are stored as int16 */
-#define MHC_MAX_OBJECTS 4096
+#define MHC_MAX_OBJECTS 4096                       /* per scenario */
+#define MHC_MAX_SCENARIOS 65536                    /* per batch */
 
 /*
  * One traffic object and the control grid of its hypotheses (Section IV-B; a hypothesis is one
@@ -117,7 +118,8 @@ typedef struct {
  *   attr_step    double [N] the same per step
  *   scalars      double [4]: p_cra (Eq. totalCrashProb), p_cra_cond = sum_i p_e[i] cond[i],
  *                            p_cra_indep = sum_i p_e[i] indep[i], 0
- *   escape       int32 [h_e] collision-free EGO hypotheses, most probable first, ties by index (Section VI-A)
+ *   escape       int32 [h_e] collision-free EGO hypotheses, most probable first, ties by index (Section VI-A);
+ *                the entries after the n_escape routes are -1
  *   n_escape     int32 [1] their number
  */
 typedef struct {
@@ -263,6 +265,74 @@ int mhc_run_bytes(const mhc_scenario *scen, size_t *bytes);
  */
 int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, const mhc_risk *out,
             void *stream);
+
+/*
+ * Batches: many scenarios of different sizes in one launch sequence (one generation launch over every
+ * hypothesis, one collision launch over every tile of every object pair, one risk walk over every EGO
+ * hypothesis).  The scenarios of a batch are concatenated in batch order: objects, hypotheses (weights),
+ * pose-plane elements, object pairs, table entries, per-pair step entries (count_k, H), EGO hypotheses
+ * (naive, cond, indep, hits, escape) and per-scenario steps (attr_step) of scenario s follow those of
+ * scenario s - 1, each scenario laid out exactly as it is alone; scalars hold 4 doubles and n_escape one
+ * int32 per scenario, and escape lists each scenario's routes from its ego0.  A single scenario is the
+ * batch of one (its sizes are those of mhc_layout).  Pair lists hold batch-wide object indices.
+ */
+typedef struct {
+    int64_t n_traj;          /* hypotheses of all objects (weights, probabilities) */
+    int64_t n_poses;         /* elements of each pose plane: sum over objects of h_a x its scenario's n_steps */
+    int64_t n_entries;       /* first-collision table entries */
+    int64_t n_step_entries;  /* per-pair step entries: length of count_k and H */
+    int64_t n_scen_steps;    /* sum of the scenarios' n_steps: length of attr_step */
+    int64_t h_ego;           /* EGO hypotheses of all scenarios */
+    int32_t n_pairs, n_objects, n_scenarios, max_steps;
+    size_t scratch;          /* arena bytes mhc_evaluate_batch needs */
+    size_t plan_bytes;       /* device scratch bytes mhc_plan_create needs */
+} mhc_batch_info;
+
+typedef struct {             /* where scenario s sits in the concatenated arrays */
+    int32_t obj0, n_objects, pair0, n_pairs, n_steps, ego;   /* ego: index within the scenario */
+    int64_t traj0, pose0, entry0, step_entry0, ego0, step0;
+} mhc_batch_slice;
+
+/* Sizes of a batch (host only, no GPU work); `slices` (n_scen entries) may be NULL.  Errors: MHC_E_INVALID
+   (reason names the scenario), also for n_scen outside [1, MHC_MAX_SCENARIOS]. */
+int mhc_batch_layout(const mhc_scenario *scens, int32_t n_scen, mhc_batch_info *info, mhc_batch_slice *slices);
+
+/* Pair list of a batch in table order (as mhc_pair_table, object indices batch-wide). */
+int mhc_batch_pair_table(const mhc_scenario *scens, int32_t n_scen, int32_t *pair_a, int32_t *pair_b,
+                         int64_t *pair_off);
+
+/* mhc_evaluate over a batch: traj_weights holds n_objects (batch-wide) host pointers or is NULL; poses,
+   table and out are device buffers of the batch sizes.  Results per scenario equal those of mhc_evaluate
+   on that scenario alone (integers and fixed-point sums exactly; the scalars to rounding of the order of
+   their double additions). */
+int mhc_evaluate_batch(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, const float *const *traj_weights,
+                       const mhc_poses *poses, int16_t *table, const mhc_risk *out, void *stream);
+
+/* mhc_autotune over a batch (size class of the whole batch: its tiles and max_steps). */
+int mhc_autotune_batch(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, const mhc_poses *poses,
+                       int16_t *table, int fused, int32_t *best_variant, int32_t *best_cull, void *stream);
+
+/*
+ * Plans: a batch evaluated repeatedly.  mhc_plan_create lays the batch out once into `scratch` (device,
+ * caller-owned, at least mhc_batch_info.plan_bytes, 256-byte aligned; used by the plan only) and keeps a
+ * pinned host copy of the descriptors.  With flags MHC_PLAN_GRAPH it runs the launch sequence once and
+ * captures it (descriptor upload from the pinned copy + the mhc_evaluate_batch kernels) as a CUDA graph;
+ * each mhc_plan_launch is then one cudaGraphLaunch on `stream`.  The collision configuration (autotuned
+ * or forced) is the one in force at creation.  mhc_plan_update replaces the scenarios by ones of the same
+ * structure (objects, grid sizes, steps, pairs; initial states, grid values and shapes may change): it
+ * waits for the plan's previous launch to finish, then rewrites the pinned copy, which the next launch
+ * uploads.  Launches of one plan are ordered after each other on the device.  poses / table / out stay
+ * the caller's and are rewritten by every launch.  The plan uses ctx (destroy it first) but not the
+ * context's arena.  Errors: MHC_E_INVALID, MHC_E_NOMEM (scratch too small), MHC_E_CUDA.
+ */
+typedef struct mhc_plan mhc_plan;
+#define MHC_PLAN_GRAPH 1
+int mhc_plan_create(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, const float *const *traj_weights,
+                    const mhc_poses *poses, int16_t *table, const mhc_risk *out, void *scratch,
+                    size_t scratch_bytes, int32_t flags, mhc_plan **plan);
+int mhc_plan_update(mhc_plan *plan, const mhc_scenario *scens, int32_t n_scen);
+int mhc_plan_launch(mhc_plan *plan, void *stream);
+void mhc_plan_destroy(mhc_plan *plan);
 
 /*
  * Collision recognition without any allocation (no counterpart in the paper: it serves deployment).

@@ -6,14 +6,17 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mhc.h"
-#include "mhc_internal.cuh"
+#include "runtime.h"
 
 using namespace mhc;
+using namespace mhc::host;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace mhc {
+namespace host {
 
 int fail(int code, const std::string &why) {
     g_err = why;
@@ -24,64 +27,39 @@ int cuda_fail(cudaError_t e, const char *what) {
     return fail(MHC_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define MHC_CUDA(call)                                      \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
-
-constexpr size_t kAlign = 256;
-constexpr size_t kReserved = 4096;    // persistent words at the start of the arena (counters)
-constexpr int kSlots = 4;
-
-size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
-
-bool finite(float v) { return std::isfinite(v); }
-
-// Host-side layout of a scenario: every descriptor the kernels read.
-struct Layout {
-    int n_obj = 0, N = 0, K = 0, model = 0, pair_mode = 0, ego = 0;
-    float tau = 0.f;
-    std::vector<ObjDesc> objs;
-    std::vector<PairDesc> pairs;
-    std::vector<float> grids;
-    std::vector<int> warp_obj, warp_first;          // 32-hypothesis bound tiles
-    std::vector<int> gen_obj, gen_first;            // generation warp tasks of gen_lanes hypotheses
-    int gen_lanes = 32;
-    long long n_traj = 0, n_entries = 0, n_tiles = 0;
-    int n_tiles32 = 0, h_e = 0;
-};
-
-int build_layout(const mhc_scenario *sc, Layout &L) {
-    if (!sc) return fail(MHC_E_INVALID, "scenario is NULL");
+// Validates scenario `si` and appends it to the layout.
+int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
+    char sw[48] = "";
+    if (batch) std::snprintf(sw, sizeof sw, "scenario %d: ", si);
+    const std::string pre(sw);
     if (sc->n_objects < 1 || sc->n_objects > MHC_MAX_OBJECTS || !sc->objects)
-        return fail(MHC_E_INVALID, "n_objects must be in [1, 4096] with a non-NULL objects array");
-    if (sc->n_steps < 1 || sc->n_steps > MHC_MAX_STEPS) return fail(MHC_E_INVALID, "n_steps must be in [1, 32767]");
+        return fail(MHC_E_INVALID, pre + "n_objects must be in [1, 4096] with a non-NULL objects array");
+    if (sc->n_steps < 1 || sc->n_steps > MHC_MAX_STEPS) return fail(MHC_E_INVALID, pre + "n_steps must be in [1, 32767]");
     if (sc->substeps < 1 || (long long)sc->n_steps * sc->substeps >= (1LL << 31))
-        return fail(MHC_E_INVALID, "substeps must be >= 1 with n_steps * substeps < 2^31");
-    if (!(sc->tau > 0.f) || !finite(sc->tau)) return fail(MHC_E_INVALID, "tau must be positive and finite");
-    if (sc->pair_mode != MHC_ALL_PAIRS && sc->pair_mode != MHC_EGO_ONLY) return fail(MHC_E_INVALID, "bad pair_mode");
-    if (sc->ego < 0 || sc->ego >= sc->n_objects) return fail(MHC_E_INVALID, "ego out of range");
-    if (sc->model != MHC_MODEL_OT && sc->model != MHC_MODEL_KIN) return fail(MHC_E_INVALID, "bad model");
-    if (sc->pair_mode == MHC_EGO_ONLY && sc->n_objects < 2) return fail(MHC_E_INVALID, "EGO_ONLY needs 2 objects");
-    L.n_obj = sc->n_objects; L.N = sc->n_steps; L.K = sc->substeps; L.model = sc->model;
-    L.pair_mode = sc->pair_mode; L.ego = sc->ego; L.tau = sc->tau;
-    L.objs.resize(L.n_obj);
+        return fail(MHC_E_INVALID, pre + "substeps must be >= 1 with n_steps * substeps < 2^31");
+    if (!(sc->tau > 0.f) || !finite(sc->tau)) return fail(MHC_E_INVALID, pre + "tau must be positive and finite");
+    if (sc->pair_mode != MHC_ALL_PAIRS && sc->pair_mode != MHC_EGO_ONLY) return fail(MHC_E_INVALID, pre + "bad pair_mode");
+    if (sc->ego < 0 || sc->ego >= sc->n_objects) return fail(MHC_E_INVALID, pre + "ego out of range");
+    if (sc->model != MHC_MODEL_OT && sc->model != MHC_MODEL_KIN) return fail(MHC_E_INVALID, pre + "bad model");
+    if (sc->pair_mode == MHC_EGO_ONLY && sc->n_objects < 2) return fail(MHC_E_INVALID, pre + "EGO_ONLY needs 2 objects");
+    const int N = sc->n_steps, obj0 = L.n_obj, n_obj_s = sc->n_objects;
+    if (L.n_obj + n_obj_s > (1 << 24)) return fail(MHC_E_INVALID, "too many objects in the batch");
+    if (N > L.max_steps) L.max_steps = N;
     static const float kDefault[6] = {1500.f, 2500.f, 1.2f, 1.5f, 80000.f, 80000.f};
-    long long traj = 0;
-    int tiles32 = 0;
-    for (int o = 0; o < L.n_obj; ++o) {
+    for (int o = 0; o < n_obj_s; ++o) {
         const mhc_object &src = sc->objects[o];
-        ObjDesc &d = L.objs[o];
+        ObjDesc d;
         std::memset(&d, 0, sizeof d);
-        char where[64];
-        std::snprintf(where, sizeof where, "object %d: ", o);
+        char where[80];
+        std::snprintf(where, sizeof where, "%sobject %d: ", pre.c_str(), o);
         if (src.kind != MHC_VEHICLE && src.kind != MHC_PEDESTRIAN) return fail(MHC_E_INVALID, std::string(where) + "bad kind");
         if (src.n_a < 1 || src.n_b < 1 || !src.grid_a || !src.grid_b)
             return fail(MHC_E_INVALID, std::string(where) + "grids must be non-empty and non-NULL");
         if ((long long)src.n_a * src.n_b > (1LL << 30)) return fail(MHC_E_INVALID, std::string(where) + "too many hypotheses");
         if (!finite(src.x0) || !finite(src.y0) || !finite(src.psi0) || !finite(src.v0) || !(src.v0 >= 0.f))
             return fail(MHC_E_INVALID, std::string(where) + "initial state must be finite with v0 >= 0");
+        if (L.grids.size() + (size_t)src.n_a + src.n_b > (size_t)0x7fffffff)
+            return fail(MHC_E_INVALID, std::string(where) + "grids too large");
         d.kind = src.kind; d.flags = src.flags; d.n_a = src.n_a; d.n_b = src.n_b; d.h = src.n_a * src.n_b;
         d.grid_off = (int)L.grids.size();
         for (int q = 0; q < src.n_a; ++q) {
@@ -94,12 +72,16 @@ int build_layout(const mhc_scenario *sc, Layout &L) {
             if (!finite(src.grid_b[q])) return fail(MHC_E_INVALID, std::string(where) + "grid_b not finite");
             L.grids.push_back(src.grid_b[q]);
         }
-        d.traj_off = traj;
-        d.pose_base = traj * (long long)L.N;
-        traj += d.h;
-        d.tile_base = tiles32;
+        d.traj_off = L.n_traj;
+        d.pose_base = L.n_pose;
+        L.n_traj += d.h;
+        L.n_pose += (long long)d.h * N;
+        d.tile_base = L.n_tiles32;
         d.n_tiles32 = (d.h + kBoundTile - 1) / kBoundTile;
-        tiles32 += d.n_tiles32;
+        if ((long long)L.n_tiles32 + d.n_tiles32 > 0x7fffffffLL) return fail(MHC_E_INVALID, "too many hypotheses in the batch");
+        L.n_tiles32 += d.n_tiles32;
+        d.bounds_base = L.n_bounds;
+        L.n_bounds += (long long)d.n_tiles32 * N;
         d.x0 = src.x0; d.y0 = src.y0; d.psi0 = src.psi0; d.v0 = src.v0; d.v_max = src.v_max;
         if (src.kind == MHC_VEHICLE) {
             if (!(src.length > 0.f) || !(src.width > 0.f) || !finite(src.length) || !finite(src.width))
@@ -114,14 +96,32 @@ int build_layout(const mhc_scenario *sc, Layout &L) {
             if (!(src.radius > 0.f) || !finite(src.radius)) return fail(MHC_E_INVALID, std::string(where) + "pedestrian needs a positive radius");
             d.rad = src.radius; d.circ = src.radius;
         }
-        for (int q = 0; q < d.n_tiles32; ++q) { L.warp_obj.push_back(o); L.warp_first.push_back(q * kBoundTile); }
+        d.scen = si; d.n_steps = N; d.substeps = sc->substeps; d.model = sc->model; d.tau = sc->tau;
+        d.tau_i_d = (double)sc->tau / (double)sc->substeps;
+        for (int q = 0; q < d.n_tiles32; ++q) { L.warp_obj.push_back(L.n_obj); L.warp_first.push_back(q * kBoundTile); }
+        L.objs.push_back(d);
+        ++L.n_obj;
     }
-    L.n_traj = traj;
-    L.n_tiles32 = tiles32;
-    L.h_e = L.objs[L.ego].h;
-    auto add_pair = [&](int a, int b) {
+    ScenDesc S;
+    std::memset(&S, 0, sizeof S);
+    S.ego = obj0 + sc->ego;
+    S.n_obj = n_obj_s;
+    S.n_steps = N;
+    S.h_e = L.objs[S.ego].h;
+    S.obj0 = obj0;
+    S.e_base = L.h_e;
+    S.lsum_base = L.n_lsum;
+    S.mass_base = L.n_mass;
+    S.step_base = L.n_steps_total;
+    L.h_e += S.h_e;
+    L.n_lsum += (long long)S.h_e * N * n_obj_s;
+    L.n_mass += (long long)S.h_e * n_obj_s;
+    L.n_steps_total += N;
+    L.entry0.push_back(L.n_entries);
+    auto add_pair = [&](int la, int lb) {
         PairDesc p;
         std::memset(&p, 0, sizeof p);
+        const int a = obj0 + la, b = obj0 + lb;
         const ObjDesc &A = L.objs[a], &B = L.objs[b];
         p.a = a; p.b = b;
         p.tiles_a = (A.h + kTile - 1) / kTile;
@@ -132,19 +132,46 @@ int build_layout(const mhc_scenario *sc, Layout &L) {
         p.rc2 = (float)(R * R * (1.0 + 1e-6));
         p.r_cull = (float)(R * (1.0 + 1e-6) + 1e-3);
         p.combo = (A.kind == MHC_VEHICLE ? 0 : 2) + (B.kind == MHC_VEHICLE ? 0 : 1);
-        p.ego_side = a == L.ego ? 0 : (b == L.ego ? 1 : -1);
+        p.ego_side = la == sc->ego ? 0 : (lb == sc->ego ? 1 : -1);
+        p.n_steps = N;
+        p.scen = si;
+        p.kofs = L.n_kofs;
+        p.lsum_base = S.lsum_base;
+        p.mass_base = S.mass_base;
+        p.hits_base = S.e_base;
+        p.n_obj_s = n_obj_s;
+        p.co_local = p.ego_side == 0 ? lb : (p.ego_side == 1 ? la : 0);
         L.n_entries += (long long)A.h * B.h;
         L.n_tiles += (long long)p.tiles_a * p.tiles_b;
+        L.n_kofs += N;
         L.pairs.push_back(p);
     };
-    if (L.pair_mode == MHC_EGO_ONLY) {
-        for (int b = 0; b < L.n_obj; ++b) if (b != L.ego) add_pair(L.ego, b);
+    if ((long long)L.pairs.size() + (long long)n_obj_s * (n_obj_s - 1) / 2 > 0x7fffffffLL)
+        return fail(MHC_E_INVALID, "too many object pairs in the batch");
+    if (sc->pair_mode == MHC_EGO_ONLY) {
+        for (int b = 0; b < n_obj_s; ++b) if (b != sc->ego) add_pair(sc->ego, b);
     } else {
-        for (int a = 0; a < L.n_obj; ++a) for (int b = a + 1; b < L.n_obj; ++b) add_pair(a, b);
+        for (int a = 0; a < n_obj_s; ++a) for (int b = a + 1; b < n_obj_s; ++b) add_pair(a, b);
     }
+    L.scens.push_back(S);
+    L.pair0.push_back((int)L.pairs.size());
+    ++L.n_scen;
     if (L.n_tiles > 0x7fffffffLL) return fail(MHC_E_INVALID, "too many collision tiles for one launch");
     return MHC_OK;
 }
+
+int build_layout(const mhc_scenario *sc, int n_scen, Layout &L) {
+    if (!sc) return fail(MHC_E_INVALID, "scenario is NULL");
+    if (n_scen < 1 || n_scen > MHC_MAX_SCENARIOS) return fail(MHC_E_INVALID, "n_scenarios must be in [1, 65536]");
+    L = Layout();
+    L.pair0.push_back(0);
+    for (int s = 0; s < n_scen; ++s)
+        if (int r = append_scenario(sc + s, s, n_scen > 1, L)) return r;
+    L.entry0.push_back(L.n_entries);
+    return MHC_OK;
+}
+
+int build_layout(const mhc_scenario *sc, Layout &L) { return build_layout(sc, 1, L); }
 
 // Generation warp tasks: a hypothesis is a sequential chain of sub-steps, so with fewer hypotheses than
 // warp schedulers (4 per SM) each warp takes fewer of them (down to 4) to occupy every scheduler.
@@ -160,59 +187,27 @@ void plan_generation(Layout &L, int n_sm) {
 }
 
 // Device scratch each call needs (besides caller buffers).
-struct Scratch {
-    size_t desc = 0, bounds = 0, prob = 0, acc = 0, weights = 0, total = 0;
-    long long acc_words = 0;
-};
+// 64-bit accumulator words of one assessment
+long long acc_words(const Layout &L) {
+    const long long np = (long long)L.pairs.size();
+    return np + L.n_kofs + np + L.n_kofs + L.h_e + L.n_lsum + L.n_mass + L.n_obj + L.n_steps_total +
+           5LL * L.n_scen + 1;
+}
 
 Scratch scratch_of(const Layout &L, bool with_weights) {
     Scratch s;
     const size_t gen_tasks = (size_t)L.n_traj / 4 + L.objs.size();   // the most generation tasks (4 lanes)
     s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
-             align_up(sizeof(float) * L.grids.size()) + 2 * align_up(sizeof(int) * L.warp_obj.size()) +
-             2 * align_up(sizeof(int) * gen_tasks);
-    s.bounds = align_up(sizeof(float4) * (size_t)L.n_tiles32 * L.N);
+             align_up(sizeof(ScenDesc) * L.scens.size()) + align_up(sizeof(float) * L.grids.size()) +
+             2 * align_up(sizeof(int) * L.warp_obj.size()) + 2 * align_up(sizeof(int) * gen_tasks);
+    s.bounds = align_up(sizeof(float4) * (size_t)L.n_bounds);
     s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj);
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
-    const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
-    s.acc_words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4 + 2;
+    s.acc_words = acc_words(L);
     s.acc = align_up(8 * (size_t)s.acc_words);
     s.total = s.desc + s.weights + s.bounds + s.prob + s.acc;
     return s;
 }
-
-}  // namespace
-
-struct mhc_ctx {
-    int device = 0;
-    char *arena = nullptr;
-    size_t arena_bytes = 0;
-    bool owns = false;
-    void *stage[kSlots] = {};
-    size_t stage_cap[kSlots] = {};
-    cudaEvent_t stage_ev[kSlots] = {};
-    int slot = 0;
-    cudaEvent_t done_ev = nullptr;
-    cudaStream_t last_stream = nullptr;
-    bool has_last = false;
-    int cull = 1;
-    int variant = 0;
-    int n_sm = 152;
-    // autotuned collision configuration per size class (log2 of the tile count, log2 of the steps)
-    struct Tuned { int tiles_log2, steps_log2, fused, variant, cull; };
-    std::vector<Tuned> tuned;
-    unsigned long long *counters = nullptr;
-    // kernel timing
-    bool profile = false;
-    struct Timed { cudaEvent_t a, b; int kind; int launches; };
-    std::vector<Timed> timed;
-    std::vector<cudaEvent_t> ev_pool;
-    double prof_ms[MHC_K_COUNT] = {};
-    long long prof_n[MHC_K_COUNT] = {};
-    long long h2d = 0, d2h = 0;
-};
-
-namespace {
 
 cudaEvent_t pooled_event(mhc_ctx *ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -224,37 +219,6 @@ cudaEvent_t pooled_event(mhc_ctx *ctx) {
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     return e;
 }
-
-// Records an event pair around the launches made in its scope when profiling is on.
-struct TimedScope {
-    mhc_ctx *ctx;
-    cudaStream_t st;
-    int kind, launches;
-    cudaEvent_t a = nullptr;
-    TimedScope(mhc_ctx *c, cudaStream_t s, int k, int n) : ctx(c), st(s), kind(k), launches(n) {
-        if (ctx->profile && (a = pooled_event(ctx))) cudaEventRecord(a, st);
-    }
-    ~TimedScope() {
-        if (!a) return;
-        cudaEvent_t b = pooled_event(ctx);
-        if (!b) { ctx->ev_pool.push_back(a); return; }
-        cudaEventRecord(b, st);
-        ctx->timed.push_back({a, b, kind, launches});
-    }
-};
-
-// Bump allocator over the arena for one call.
-struct Bump {
-    char *base;
-    size_t cap, off;
-    void *take(size_t n) {
-        n = align_up(n);
-        if (off + n > cap) return nullptr;
-        void *p = base + off;
-        off += n;
-        return p;
-    }
-};
 
 // Order this call after the context's previous call when it used another stream.
 int begin_call(mhc_ctx *ctx, cudaStream_t st) {
@@ -270,34 +234,48 @@ int end_call(mhc_ctx *ctx, cudaStream_t st) {
     return MHC_OK;
 }
 
-// Pack the descriptors into a pinned staging slot and copy them to `dev` on `st`.
-struct DevDesc {
-    ObjDesc *objs;
-    PairDesc *pairs;
-    float *grids;
-    int *warp_obj, *warp_first;
-    int *gen_obj, *gen_first;
-    float *weights;
-};
-
-int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, char *dev, cudaStream_t st,
-           DevDesc &out) {
-    std::vector<std::pair<const void *, size_t>> parts = {
+size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char *host, char *dev, DevDesc &out) {
+    constexpr int kParts = 8;
+    const std::pair<const void *, size_t> parts[kParts] = {
         {L.objs.data(), sizeof(ObjDesc) * L.objs.size()},
         {L.pairs.data(), sizeof(PairDesc) * L.pairs.size()},
+        {L.scens.data(), sizeof(ScenDesc) * L.scens.size()},
         {L.grids.data(), sizeof(float) * L.grids.size()},
         {L.warp_obj.data(), sizeof(int) * L.warp_obj.size()},
         {L.warp_first.data(), sizeof(int) * L.warp_first.size()},
         {L.gen_obj.data(), sizeof(int) * L.gen_obj.size()},
         {L.gen_first.data(), sizeof(int) * L.gen_first.size()},
     };
-    size_t caps[7] = {align_up(parts[0].second), align_up(sizeof(PairDesc) * (L.pairs.size() + 1)),
-                      align_up(parts[2].second), align_up(parts[3].second), align_up(parts[4].second),
-                      align_up(parts[5].second), align_up(parts[6].second)};
-    size_t total = 0;
-    for (size_t c : caps) total += c;
-    const size_t wbytes = weights ? align_up(sizeof(float) * weights->size()) : 0;
-    total += wbytes;
+    size_t caps[kParts];
+    for (int q = 0; q < kParts; ++q) caps[q] = align_up(parts[q].second);
+    caps[1] = align_up(sizeof(PairDesc) * (L.pairs.size() + 1));
+    size_t off = 0;
+    char *ptrs[kParts + 1];
+    for (int q = 0; q < kParts; ++q) {
+        if (host && parts[q].second) std::memcpy(host + off, parts[q].first, parts[q].second);
+        ptrs[q] = dev + off;
+        off += caps[q];
+    }
+    ptrs[kParts] = dev + off;
+    if (weights) {
+        if (host && !weights->empty()) std::memcpy(host + off, weights->data(), sizeof(float) * weights->size());
+        off += align_up(sizeof(float) * weights->size());
+    }
+    out.objs = reinterpret_cast<ObjDesc *>(ptrs[0]);
+    out.pairs = reinterpret_cast<PairDesc *>(ptrs[1]);
+    out.scens = reinterpret_cast<ScenDesc *>(ptrs[2]);
+    out.grids = reinterpret_cast<float *>(ptrs[3]);
+    out.warp_obj = reinterpret_cast<int *>(ptrs[4]);
+    out.warp_first = reinterpret_cast<int *>(ptrs[5]);
+    out.gen_obj = reinterpret_cast<int *>(ptrs[6]);
+    out.gen_first = reinterpret_cast<int *>(ptrs[7]);
+    out.weights = weights ? reinterpret_cast<float *>(ptrs[kParts]) : nullptr;
+    return off;
+}
+
+int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, char *dev, cudaStream_t st,
+           DevDesc &out) {
+    const size_t total = pack_descriptors(L, weights, nullptr, dev, out);
     const int s = ctx->slot;
     ctx->slot = (ctx->slot + 1) % kSlots;
     MHC_CUDA(cudaEventSynchronize(ctx->stage_ev[s]));
@@ -309,29 +287,11 @@ int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, cha
         MHC_CUDA(cudaHostAlloc(&ctx->stage[s], cap, cudaHostAllocDefault));
         ctx->stage_cap[s] = cap;
     }
-    char *h = static_cast<char *>(ctx->stage[s]);
-    size_t off = 0;
-    char *ptrs[8];
-    for (int q = 0; q < 7; ++q) {
-        if (parts[q].second) std::memcpy(h + off, parts[q].first, parts[q].second);
-        ptrs[q] = dev + off;
-        off += caps[q];
-    }
-    ptrs[7] = dev + off;
-    if (weights && !weights->empty()) std::memcpy(h + off, weights->data(), sizeof(float) * weights->size());
-    off += wbytes;
-    MHC_CUDA(cudaMemcpyAsync(dev, h, off, cudaMemcpyHostToDevice, st));
+    pack_descriptors(L, weights, static_cast<char *>(ctx->stage[s]), dev, out);
+    MHC_CUDA(cudaMemcpyAsync(dev, ctx->stage[s], total, cudaMemcpyHostToDevice, st));
     MHC_CUDA(cudaEventRecord(ctx->stage_ev[s], st));
-    ctx->h2d = (long long)off;
+    ctx->h2d = (long long)total;
     ctx->d2h = 0;
-    out.objs = reinterpret_cast<ObjDesc *>(ptrs[0]);
-    out.pairs = reinterpret_cast<PairDesc *>(ptrs[1]);
-    out.grids = reinterpret_cast<float *>(ptrs[2]);
-    out.warp_obj = reinterpret_cast<int *>(ptrs[3]);
-    out.warp_first = reinterpret_cast<int *>(ptrs[4]);
-    out.gen_obj = reinterpret_cast<int *>(ptrs[5]);
-    out.gen_first = reinterpret_cast<int *>(ptrs[6]);
-    out.weights = weights ? reinterpret_cast<float *>(ptrs[7]) : nullptr;
     return MHC_OK;
 }
 
@@ -371,28 +331,30 @@ int gather_weights(const Layout &L, const float *const *w, std::vector<float> &o
 int make_risk_args(const Layout &L, const DevDesc &D, Bump &bump, const int16_t *table, const mhc_risk *rout,
                    RiskArgs &r) {
     std::memset(&r, 0, sizeof r);
-    r.objs = D.objs; r.pairs = D.pairs; r.n_pairs = (int)L.pairs.size(); r.n_obj = L.n_obj;
-    r.n_steps = L.N; r.ego = L.ego; r.h_e = L.h_e; r.n_tiles = L.n_tiles; r.table = table;
+    r.objs = D.objs; r.pairs = D.pairs; r.scens = D.scens;
+    r.n_pairs = (int)L.pairs.size(); r.n_obj = L.n_obj; r.n_scen = L.n_scen;
+    r.h_e = L.h_e; r.n_kofs = L.n_kofs; r.n_steps_total = L.n_steps_total; r.max_steps = L.max_steps;
+    r.n_tiles = L.n_tiles; r.table = table;
     r.weights = D.weights;
     r.prob = static_cast<double *>(bump.take(sizeof(double) * (size_t)L.n_traj));
     r.probf = static_cast<float *>(bump.take(sizeof(float) * (size_t)L.n_traj));
-    const long long np = (long long)L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
-    const long long words = np + np * N + np + np * N + he + he * N * no + he * no + no + N + 4 + 2;
+    const long long np = (long long)L.pairs.size();
+    const long long words = acc_words(L);
     unsigned long long *w = static_cast<unsigned long long *>(bump.take(8 * (size_t)words));
     if (!r.prob || !r.probf || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
     RiskScratch &A = r.acc;
     A.base = w; A.n_words = words;
     A.count = w; w += np;
-    A.count_k = w; w += np * N;
+    A.count_k = w; w += L.n_kofs;
     A.P = w; w += np;
-    A.H = w; w += np * N;
-    A.hits = w; w += he;
-    A.lsum = w; w += he * N * no;
-    A.mass = w; w += he * no;
-    A.attr_obj = w; w += no;
-    A.attr_step = w; w += N;
-    A.scalars = reinterpret_cast<double *>(w); w += 4;
-    A.n_escape = w; w += 1;
+    A.H = w; w += L.n_kofs;
+    A.hits = w; w += L.h_e;
+    A.lsum = w; w += L.n_lsum;
+    A.mass = w; w += L.n_mass;
+    A.attr_obj = w; w += L.n_obj;
+    A.attr_step = w; w += L.n_steps_total;
+    A.scalars = reinterpret_cast<double *>(w); w += 4LL * L.n_scen;
+    A.n_escape = w; w += L.n_scen;
     A.done = w;
     r.count = reinterpret_cast<long long *>(rout->count);
     r.count_k = reinterpret_cast<long long *>(rout->count_k);
@@ -413,7 +375,7 @@ int log2_floor(long long v) {
 void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &variant, int &cull) {
     cull = ctx->cull;
     if (ctx->variant != 0) { variant = ctx->variant; return; }
-    const int tl = log2_floor(L.n_tiles), sl = log2_floor(L.N);
+    const int tl = log2_floor(L.n_tiles), sl = log2_floor(L.max_steps);
     for (const auto &t : ctx->tuned)
         if (t.tiles_log2 == tl && t.steps_log2 == sl && t.fused == (int)fused) {
             variant = t.variant;
@@ -425,30 +387,37 @@ void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &v
 
 // Device buffers for the risk outputs of one assessment, carved from the arena.
 bool take_risk_outputs(Bump &bump, const Layout &L, mhc_risk &R) {
-    const size_t np = L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+    const size_t np = L.pairs.size(), nk = L.n_kofs, he = L.h_e, no = L.n_obj, ns = L.n_scen;
     std::memset(&R, 0, sizeof R);
     R.count = static_cast<int64_t *>(bump.take(8 * np));
-    R.count_k = static_cast<int64_t *>(bump.take(8 * np * N));
+    R.count_k = static_cast<int64_t *>(bump.take(8 * nk));
     R.P = static_cast<double *>(bump.take(8 * np));
-    R.H = static_cast<double *>(bump.take(8 * np * N));
+    R.H = static_cast<double *>(bump.take(8 * nk));
     R.naive = static_cast<double *>(bump.take(8 * he));
     R.cond = static_cast<double *>(bump.take(8 * he));
     R.indep = static_cast<double *>(bump.take(8 * he));
     R.hits = static_cast<int32_t *>(bump.take(4 * he));
     R.attr_obj = static_cast<double *>(bump.take(8 * no));
-    R.attr_step = static_cast<double *>(bump.take(8 * N));
-    R.scalars = static_cast<double *>(bump.take(8 * 4));
+    R.attr_step = static_cast<double *>(bump.take(8 * (size_t)L.n_steps_total));
+    R.scalars = static_cast<double *>(bump.take(8 * 4 * ns));
     R.escape = static_cast<int32_t *>(bump.take(4 * he));
-    R.n_escape = static_cast<int32_t *>(bump.take(4));
+    R.n_escape = static_cast<int32_t *>(bump.take(4 * ns));
     return R.count && R.count_k && R.P && R.H && R.naive && R.cond && R.indep && R.hits && R.attr_obj &&
            R.attr_step && R.scalars && R.escape && R.n_escape;
+}
+
+// Device bytes of the risk outputs take_risk_outputs carves.
+size_t risk_output_bytes(const Layout &L) {
+    const size_t np = L.pairs.size(), nk = L.n_kofs, he = L.h_e, no = L.n_obj, ns = L.n_scen;
+    return align_up(8 * np) * 2 + align_up(8 * nk) * 2 + align_up(8 * he) * 3 + align_up(4 * he) * 2 +
+           align_up(8 * no) + align_up(8 * (size_t)L.n_steps_total) + align_up(32 * ns) + align_up(4 * ns);
 }
 
 // Launch sequence.  fused: the collision kernel accumulates the risk terms at each first hit (no second
 // pass over the table): prepare -> generate -> fill + bounds -> collide -> ego walk + finish.
 int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, const mhc_poses *gen_out,
                const mhc_poses *coll_in, int16_t *table, bool risk, const mhc_risk *rout, cudaStream_t st,
-               bool fused = false) {
+               bool fused) {
     RiskArgs r;
     fused = fused && risk && coll_in;
     if (risk) {
@@ -462,8 +431,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     if (gen_out) {
         GenArgs g;
         g.objs = D.objs; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
-        g.n_warps = (int)L.gen_obj.size(); g.lanes = L.gen_lanes; g.n_steps = L.N; g.substeps = L.K; g.model = L.model;
-        g.tau = L.tau; g.tau_i_d = (double)L.tau / (double)L.K;
+        g.n_warps = (int)L.gen_obj.size(); g.lanes = L.gen_lanes;
         g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
         cudaError_t e = launch_generate(g, st);
@@ -472,7 +440,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     if (coll_in) {
         int variant = 1, cull = 1;
         pick_collide_config(ctx, L, fused, variant, cull);
-        float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_tiles32 * L.N));
+        float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_bounds));
         if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
         {
             TimedScope ts(ctx, st, MHC_K_BOUNDS, cull ? 2 : 1);
@@ -481,7 +449,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
             if (cull) {
                 BoundsArgs b;
                 b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
-                b.n_warps = (int)L.warp_obj.size(); b.n_steps = L.N; b.x = coll_in->x; b.y = coll_in->y;
+                b.n_warps = (int)L.warp_obj.size(); b.max_steps = L.max_steps; b.x = coll_in->x; b.y = coll_in->y;
                 b.bounds = bounds;
                 e = launch_bounds(b, st);
                 if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
@@ -489,29 +457,27 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         }
         CollideArgs c{};
         c.objs = D.objs; c.pairs = D.pairs; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
-        c.n_steps = L.N; c.cull = cull; c.variant = variant;
+        c.max_steps = L.max_steps; c.cull = cull; c.variant = variant;
         c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
         c.bounds = bounds; c.table = table; c.counters = ctx->counters;
         if (fused) {
             c.probf = r.probf;
             c.acc = r.acc;
-            c.n_obj = L.n_obj;
         }
         TimedScope ts(ctx, st, MHC_K_COLLIDE, 1);
         cudaError_t e = launch_collide(c, st);
         if (e != cudaSuccess) return cuda_fail(e, "collision kernel launch");
     }
     if (risk) {
-        TimedScope ts(ctx, st, MHC_K_RISK, fused ? 1 : 3);
+        TimedScope ts(ctx, st, MHC_K_RISK, (fused ? 0 : 2) + risk_tail_launches(r));
         cudaError_t e = fused ? launch_risk_tail(r, st) : launch_risk(r, st);
         if (e != cudaSuccess) return cuda_fail(e, "risk kernel launch");
     }
     return MHC_OK;
 }
 
-}  // namespace
+}  // namespace host
 
-namespace mhc {
 // Records the reason of a failure for mhc_last_error() (used by entry points in other files).
 void set_last_error(const char *why) { g_err = why ? why : ""; }
 }  // namespace mhc
@@ -720,11 +686,26 @@ int mhc_assess_risk(mhc_ctx *ctx, const mhc_scenario *scen, const int16_t *table
 
 int mhc_evaluate(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, const mhc_poses *poses,
                  int16_t *table, const mhc_risk *out, void *stream) {
+    return evaluate_impl(ctx, scen, 1, traj_weights, poses, table, out, stream);
+}
+
+int mhc_autotune(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses, int16_t *table, int fused,
+                 int32_t *best_variant, int32_t *best_cull, void *stream) {
+    return autotune_impl(ctx, scen, 1, poses, table, fused, best_variant, best_cull, stream);
+}
+
+}  // extern "C"
+
+namespace mhc {
+namespace host {
+
+int evaluate_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const float *const *traj_weights,
+                  const mhc_poses *poses, int16_t *table, const mhc_risk *out, void *stream) {
     if (int r = check_ctx(ctx)) return r;
     if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table || !out)
         return fail(MHC_E_INVALID, "poses, table and out must be non-NULL");
     Layout L;
-    if (int r = build_layout(scen, L)) return r;
+    if (int r = build_layout(scen, n_scen, L)) return r;
     plan_generation(L, ctx->n_sm);
     std::vector<float> w;
     if (int r = gather_weights(L, traj_weights, w)) return r;
@@ -740,13 +721,13 @@ int mhc_evaluate(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *tra
     return end_call(ctx, st);
 }
 
-int mhc_autotune(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses, int16_t *table, int fused,
-                 int32_t *best_variant, int32_t *best_cull, void *stream) {
+int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_poses *poses, int16_t *table,
+                  int fused, int32_t *best_variant, int32_t *best_cull, void *stream) {
     if (int r = check_ctx(ctx)) return r;
     if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table)
         return fail(MHC_E_INVALID, "poses and table must be non-NULL");
     Layout L;
-    if (int r = build_layout(scen, L)) return r;
+    if (int r = build_layout(scen, n_scen, L)) return r;
     plan_generation(L, ctx->n_sm);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int saved_variant = ctx->variant, saved_cull = ctx->cull;
@@ -776,8 +757,15 @@ int mhc_autotune(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses,
                     if ((rc = launch_all(ctx, L, D, bump, poses, poses, table, true, &R, st, true))) break;
                     if ((rc = end_call(ctx, st))) break;
                 } else {
-                    rc = mhc_detect_collisions(ctx, scen, poses, table, stream);
-                    if (rc) break;
+                    Scratch S = scratch_of(L, false);
+                    Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
+                    char *dev = static_cast<char *>(bump.take(S.desc));
+                    if (!dev) { rc = fail(MHC_E_NOMEM, "arena too small to autotune"); break; }
+                    if ((rc = begin_call(ctx, st))) break;
+                    DevDesc D;
+                    if ((rc = upload(ctx, L, nullptr, dev, st, D))) break;
+                    if ((rc = launch_all(ctx, L, D, bump, nullptr, poses, table, false, nullptr, st))) break;
+                    if ((rc = end_call(ctx, st))) break;
                 }
                 if ((rc = mhc_profile_read(ctx, ms, n, rep == 0))) break;
             }
@@ -792,7 +780,7 @@ int mhc_autotune(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses,
     ctx->profile = saved_profile;
     for (int k = 0; k < MHC_K_COUNT; ++k) { ctx->prof_ms[k] = saved_ms[k]; ctx->prof_n[k] = saved_n[k]; }
     if (rc != MHC_OK) return rc;
-    const int tl = log2_floor(L.n_tiles), sl = log2_floor(L.N);
+    const int tl = log2_floor(L.n_tiles), sl = log2_floor(L.max_steps);
     bool stored = false;
     for (auto &t : ctx->tuned)
         if (t.tiles_log2 == tl && t.steps_log2 == sl && t.fused == (fused != 0)) { t.variant = bv; t.cull = bc; stored = true; }
@@ -802,15 +790,18 @@ int mhc_autotune(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *poses,
     return MHC_OK;
 }
 
+}  // namespace host
+}  // namespace mhc
+
+extern "C" {
+
 int mhc_run_bytes(const mhc_scenario *scen, size_t *bytes) {
     Layout L;
     if (int r = build_layout(scen, L)) return r;
     if (!bytes) return fail(MHC_E_INVALID, "bytes is NULL");
-    const size_t poses = 4 * align_up(sizeof(float) * (size_t)L.n_traj * L.N);
+    const size_t poses = 4 * align_up(sizeof(float) * (size_t)L.n_pose);
     const size_t table = align_up(sizeof(int16_t) * (size_t)L.n_entries);
-    const size_t np = L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
-    const size_t outs = align_up(8 * (np + np * N + np + np * N + 3 * he + no + N + 4)) + 2 * align_up(4 * he) + kAlign;
-    *bytes = kReserved + scratch_of(L, true).total + poses + table + outs;
+    *bytes = kReserved + scratch_of(L, true).total + poses + table + risk_output_bytes(L);
     return MHC_OK;
 }
 
@@ -827,14 +818,14 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     Scratch S = scratch_of(L, !w.empty());
     Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
     char *dev = static_cast<char *>(bump.take(S.desc + S.weights));
-    const size_t plane = sizeof(float) * (size_t)L.n_traj * L.N;
+    const size_t plane = sizeof(float) * (size_t)L.n_pose;
     mhc_poses P;
     P.x = static_cast<float *>(bump.take(plane));
     P.y = static_cast<float *>(bump.take(plane));
     P.c = static_cast<float *>(bump.take(plane));
     P.s = static_cast<float *>(bump.take(plane));
     int16_t *table = static_cast<int16_t *>(bump.take(sizeof(int16_t) * (size_t)L.n_entries));
-    const size_t np = L.pairs.size(), N = L.N, he = L.h_e, no = L.n_obj;
+    const size_t np = L.pairs.size(), nk = L.n_kofs, he = L.h_e, no = L.n_obj, ns = L.n_scen;
     mhc_risk R;
     const bool outs = take_risk_outputs(bump, L, R);
     if (!dev || !P.x || !P.y || !P.c || !P.s || !table || !outs)
@@ -844,11 +835,11 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
     if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st, true)) return r;
     struct Cp { void *dst; const void *src; size_t n; } cps[] = {
-        {out->count, R.count, 8 * np}, {out->count_k, R.count_k, 8 * np * N}, {out->P, R.P, 8 * np},
-        {out->H, R.H, 8 * np * N}, {out->naive, R.naive, 8 * he}, {out->cond, R.cond, 8 * he},
+        {out->count, R.count, 8 * np}, {out->count_k, R.count_k, 8 * nk}, {out->P, R.P, 8 * np},
+        {out->H, R.H, 8 * nk}, {out->naive, R.naive, 8 * he}, {out->cond, R.cond, 8 * he},
         {out->indep, R.indep, 8 * he}, {out->hits, R.hits, 4 * he}, {out->attr_obj, R.attr_obj, 8 * no},
-        {out->attr_step, R.attr_step, 8 * N}, {out->scalars, R.scalars, 8 * 4}, {out->escape, R.escape, 4 * he},
-        {out->n_escape, R.n_escape, 4}};
+        {out->attr_step, R.attr_step, 8 * (size_t)L.n_steps_total}, {out->scalars, R.scalars, 8 * 4 * ns},
+        {out->escape, R.escape, 4 * he}, {out->n_escape, R.n_escape, 4 * ns}};
     for (const Cp &c : cps) {
         if (!c.dst) continue;
         MHC_CUDA(cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, st));

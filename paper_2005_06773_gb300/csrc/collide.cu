@@ -101,13 +101,13 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
     const int i0 = ta * kTile, j0 = tb * kTile;
     const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
     const int tid = threadIdx.x, ti = tid / TJ, tj = tid % TJ;
-    const int N = a.n_steps;
+    const int N = P.n_steps;
     const int n_chunks = (N + 31) >> 5;
 
     // activity of every step: the two tiles' centre boxes, grown by both circumradii, must meet
     const int na = (rows + kBoundTile - 1) / kBoundTile, nb = (cols + kBoundTile - 1) / kBoundTile;
-    const float4 *bA0 = a.bounds + (long long)(A.tile_base + ta * 2) * N;
-    const float4 *bB0 = a.bounds + (long long)(B.tile_base + tb * 2) * N;
+    const float4 *bA0 = a.bounds + A.bounds_base + (long long)(ta * 2) * N;
+    const float4 *bB0 = a.bounds + B.bounds_base + (long long)(tb * 2) * N;
     for (int w = tid >> 5; w < n_chunks; w += THREADS / 32) {
         const int k = (w << 5) + (tid & 31);
         bool act = k < N;
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
     unsigned long long *s_H = s_acc;
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_acc + N);
     unsigned long long *s_L = s_acc + N + (N + 1) / 2;
-    const bool smem_hist = FUSED && N <= kFusedHistSteps;
-    const bool smem_cells = smem_hist && N <= kFusedCellSteps && P.ego_side >= 0;
+    const bool smem_hist = FUSED && a.max_steps <= kFusedHistSteps;
+    const bool smem_cells = smem_hist && a.max_steps <= kFusedCellSteps && P.ego_side >= 0;
     if (FUSED) {
         if (smem_hist)
             for (int q = tid; q < N; q += THREADS) { s_H[q] = 0ull; s_cnt[q] = 0u; }
@@ -285,8 +285,8 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
                         atomicAdd(s_cnt + k, 1u);
                         atomicAdd(s_H + k, w);
                     } else {
-                        atomicAdd(a.acc.count_k + (long long)lo * N + k, 1ull);
-                        atomicAdd(a.acc.H + (long long)lo * N + k, w);
+                        atomicAdd(a.acc.count_k + P.kofs + k, 1ull);
+                        atomicAdd(a.acc.H + P.kofs + k, w);
                     }
                     if (P.ego_side >= 0) {
                         const int eg = P.ego_side == 0 ? i : j;             // the EGO hypothesis
@@ -297,8 +297,8 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
                         if (smem_cells) {
                             atomicAdd(s_L + eg * N + k, lq);
                         } else {
-                            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
-                            atomicAdd(a.acc.lsum + ((long long)(e0 + eg) * N + k) * a.n_obj + co, lq);
+                            const int e0 = P.ego_side == 0 ? i0 : j0;
+                            atomicAdd(a.acc.lsum + P.lsum_base + ((long long)(e0 + eg) * N + k) * P.n_obj_s + P.co_local, lq);
                         }
                     }
                 }
@@ -324,17 +324,17 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
         if (smem_hist) {
             for (int q = tid; q < N; q += THREADS) {
                 if (s_cnt[q]) {
-                    atomicAdd(a.acc.count_k + (long long)lo * N + q, (unsigned long long)s_cnt[q]);
-                    atomicAdd(a.acc.H + (long long)lo * N + q, s_H[q]);
+                    atomicAdd(a.acc.count_k + P.kofs + q, (unsigned long long)s_cnt[q]);
+                    atomicAdd(a.acc.H + P.kofs + q, s_H[q]);
                 }
             }
         }
         if (P.ego_side >= 0) {
-            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
+            const int e0 = P.ego_side == 0 ? i0 : j0;
             for (int q = tid; q < kTile; q += THREADS) {
                 if (s_ehits[q]) {
-                    atomicAdd(a.acc.mass + (long long)(e0 + q) * a.n_obj + co, s_emass[q]);
-                    atomicAdd(a.acc.hits + e0 + q, (unsigned long long)s_ehits[q]);
+                    atomicAdd(a.acc.mass + P.mass_base + (long long)(e0 + q) * P.n_obj_s + P.co_local, s_emass[q]);
+                    atomicAdd(a.acc.hits + P.hits_base + e0 + q, (unsigned long long)s_ehits[q]);
                 }
             }
             if (smem_cells) {
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
                     const unsigned long long v = s_L[q];
                     if (v) {
                         const int e = q / N, kk = q - e * N;
-                        atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + kk) * a.n_obj + co, v);
+                        atomicAdd(a.acc.lsum + P.lsum_base + ((long long)(e0 + e) * N + kk) * P.n_obj_s + P.co_local, v);
                     }
                 }
             }
@@ -373,8 +373,8 @@ __device__ __forceinline__ void add_hit(const CollideArgs &a, const PairDesc &P,
         atomicAdd(R.s_cnt + k, 1u);
         atomicAdd(R.s_H + k, w);
     } else {
-        atomicAdd(a.acc.count_k + (long long)pair * N + k, 1ull);
-        atomicAdd(a.acc.H + (long long)pair * N + k, w);
+        atomicAdd(a.acc.count_k + P.kofs + k, 1ull);
+        atomicAdd(a.acc.H + P.kofs + k, w);
     }
     if (P.ego_side >= 0) {
         const int e = P.ego_side == 0 ? i : j;                // the EGO hypothesis
@@ -385,8 +385,8 @@ __device__ __forceinline__ void add_hit(const CollideArgs &a, const PairDesc &P,
         if (R.cells) {
             atomicAdd(R.s_L + e * N + k, lq);
         } else {
-            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
-            atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + k) * a.n_obj + co, lq);
+            const int e0 = P.ego_side == 0 ? i0 : j0;
+            atomicAdd(a.acc.lsum + P.lsum_base + ((long long)(e0 + e) * N + k) * P.n_obj_s + P.co_local, lq);
         }
     }
 }
@@ -430,12 +430,12 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
     const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lr = lane >> 2, lc = lane & 3;
-    const int N = a.n_steps;
+    const int N = P.n_steps;
     const int n_chunks = (N + 31) >> 5;
 
     const int na = (rows + kBoundTile - 1) / kBoundTile, nb = (cols + kBoundTile - 1) / kBoundTile;
-    const float4 *bA0 = a.bounds + (long long)(A.tile_base + ta * 2) * N;
-    const float4 *bB0 = a.bounds + (long long)(B.tile_base + tb * 2) * N;
+    const float4 *bA0 = a.bounds + A.bounds_base + (long long)(ta * 2) * N;
+    const float4 *bB0 = a.bounds + B.bounds_base + (long long)(tb * 2) * N;
     for (int w = warp; w < n_chunks; w += WARPS) {
         const int k = (w << 5) + lane;
         bool act = k < N;
@@ -601,8 +601,8 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
     R.pb = s_prob[1];
     R.emass = s_emass;
     R.ehits = s_ehits;
-    R.hist = FUSED && N <= kFusedHistSteps;
-    R.cells = R.hist && N <= kFusedCellSteps && P.ego_side >= 0;
+    R.hist = FUSED && a.max_steps <= kFusedHistSteps;
+    R.cells = R.hist && a.max_steps <= kFusedCellSteps && P.ego_side >= 0;
     if (FUSED) {
         if (R.hist)
             for (int q = tid; q < N; q += THREADS) { R.s_H[q] = 0ull; R.s_cnt[q] = 0u; }
@@ -642,17 +642,17 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
         if (R.hist) {
             for (int q = tid; q < N; q += THREADS) {
                 if (R.s_cnt[q]) {
-                    atomicAdd(a.acc.count_k + (long long)lo * N + q, (unsigned long long)R.s_cnt[q]);
-                    atomicAdd(a.acc.H + (long long)lo * N + q, R.s_H[q]);
+                    atomicAdd(a.acc.count_k + P.kofs + q, (unsigned long long)R.s_cnt[q]);
+                    atomicAdd(a.acc.H + P.kofs + q, R.s_H[q]);
                 }
             }
         }
         if (P.ego_side >= 0) {
-            const int e0 = P.ego_side == 0 ? i0 : j0, co = P.ego_side == 0 ? P.b : P.a;
+            const int e0 = P.ego_side == 0 ? i0 : j0;
             for (int q = tid; q < kTile; q += THREADS) {
                 if (s_ehits[q]) {
-                    atomicAdd(a.acc.mass + (long long)(e0 + q) * a.n_obj + co, s_emass[q]);
-                    atomicAdd(a.acc.hits + e0 + q, (unsigned long long)s_ehits[q]);
+                    atomicAdd(a.acc.mass + P.mass_base + (long long)(e0 + q) * P.n_obj_s + P.co_local, s_emass[q]);
+                    atomicAdd(a.acc.hits + P.hits_base + e0 + q, (unsigned long long)s_ehits[q]);
                 }
             }
             if (R.cells) {
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
                     const unsigned long long v = R.s_L[q];
                     if (v) {
                         const int e = q / N, kk = q - e * N;
-                        atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + kk) * a.n_obj + co, v);
+                        atomicAdd(a.acc.lsum + P.lsum_base + ((long long)(e0 + e) * N + kk) * P.n_obj_s + P.co_local, v);
                     }
                 }
             }
@@ -695,8 +695,8 @@ template <int THREADS, int MI, int MJ, int CH, bool FUSED>
 cudaError_t launch_variant(const CollideArgs &a, cudaStream_t st) {
     size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2));
     if (FUSED) {
-        if (a.n_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.n_steps + (a.n_steps + 1) / 2);
-        if (a.n_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.n_steps;
+        if (a.max_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.max_steps + (a.max_steps + 1) / 2);
+        if (a.max_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.max_steps;
     }
     if (smem > 32 * 1024) {   // dynamic + static (about 5 KiB) above the default 48 KiB needs the opt-in
         cudaError_t e = cudaFuncSetAttribute(collide_kernel<THREADS, MI, MJ, CH, FUSED>,
@@ -711,8 +711,8 @@ template <int WARPS, int CH, bool FUSED>
 cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
     size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2)) + sizeof(int) * kTile * kTile;
     if (FUSED) {
-        if (a.n_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.n_steps + (a.n_steps + 1) / 2);
-        if (a.n_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.n_steps;
+        if (a.max_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.max_steps + (a.max_steps + 1) / 2);
+        if (a.max_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.max_steps;
     }
     if (smem > 32 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(collide_warp_kernel<WARPS, CH, FUSED>,
@@ -726,11 +726,8 @@ cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    int n_sm = 152, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    // 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests) measured faster than 8 x 8 with
-    // 64 threads on every workload tried, from 1,445 to 507,904 tiles; variant 2 keeps the latter selectable.
-    (void)n_sm;
+    // variant 1: 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests); variant 2: 8 x 8 with
+    // 64 threads; variant 3: one warp per step (8 x 16 lanes).  The caller picks one (autotuned per size).
     const bool many = a.variant == 2;
     if (a.variant == 3)
         return a.probf ? launch_warp_variant<4, 8, true>(a, st) : launch_warp_variant<4, 8, false>(a, st);

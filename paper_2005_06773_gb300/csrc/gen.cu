@@ -202,18 +202,19 @@ __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
     const float ga = a.grids[o.grid_off + ia];
     const float gb = a.grids[o.grid_off + o.n_a + ib];
     if (o.kind == kVehicle)
-        vehicle(o, ga, gb, a.model, a.n_steps, a.substeps, a.tau_i_d, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
+        vehicle(o, ga, gb, o.model, o.n_steps, o.substeps, o.tau_i_d, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
     else
-        pedestrian(o, ga, gb, a.n_steps, a.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
+        pedestrian(o, ga, gb, o.n_steps, o.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
 }
 
 // Bounding box of the 32 pose centres of each bound tile at each step (warp min/max reduction).
 __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long total = (long long)a.n_warps * a.n_steps;
+    const long long total = (long long)a.n_warps * a.max_steps;
     if (g >= total) return;
-    const int w = (int)(g / a.n_steps), k = (int)(g - (long long)w * a.n_steps);
+    const int w = (int)(g / a.max_steps), k = (int)(g - (long long)w * a.max_steps);
     const ObjDesc &o = a.objs[a.warp_obj[w]];
+    if (k >= o.n_steps) return;
     const int lane = threadIdx.x & 31;
     const int i = a.warp_first[w] + lane;
     float x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
         x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, d));
         y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, d));
     }
-    if (lane == 0) a.bounds[(long long)(o.tile_base + a.warp_first[w] / kBoundTile) * a.n_steps + k] =
+    if (lane == 0) a.bounds[o.bounds_base + (long long)(a.warp_first[w] / kBoundTile) * o.n_steps + k] =
         make_float4(x0, y0, x1, y1);
 }
 
@@ -245,7 +246,7 @@ cudaError_t launch_generate(const GenArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st) {
-    const long long total = (long long)a.n_warps * a.n_steps;
+    const long long total = (long long)a.n_warps * a.max_steps;
     if (total <= 0) return cudaSuccess;
     const long long blocks = (total + 7) / 8;
     bounds_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);

@@ -24,7 +24,7 @@ constexpr int kTile = 64;          // collision tile edge (hypotheses per side)
 constexpr int kBoundTile = 32;     // hypotheses per bounding-box tile (one warp)
 constexpr int16_t kNoHit = 0x7fff; // in-kernel sentinel, stored as -1
 
-// Per-object descriptor (device).
+// Per-object descriptor (device).  Objects of every scenario of a batch are listed one after another.
 struct ObjDesc {
     int kind, flags, n_a, n_b;
     int h;              // hypotheses n_a * n_b
@@ -32,23 +32,50 @@ struct ObjDesc {
     int tile_base;      // first 32-wide bound tile of this object
     int n_tiles32;
     long long traj_off; // global index of hypothesis 0
-    long long pose_base;// n_steps * traj_off
+    long long pose_base;// first pose: poses of the object are [step][hypothesis] from here
+    long long bounds_base;  // first bound box: [tile][step] from here
     float hl, hw, rad;  // half length, half width, disc radius
     float circ;         // circumradius about the pose point
     float x0, y0, psi0, v0, v_max;
     float m, Iz, lf, lr, caf, car;
+    // the object's scenario
+    int scen;           // scenario index in the batch
+    int n_steps, substeps, model;
+    float tau;
+    int pad_;
+    double tau_i_d;     // (double)tau / substeps, the sub-step of the speed recurrence
 };
 
 // Per-object-pair descriptor (device).
 struct PairDesc {
-    int a, b;
+    int a, b;                 // global object indices
     int tiles_a, tiles_b;     // 64-wide tiles along each side
     long long off;            // table offset of the pair's block
     long long tile_start;     // first global collision tile of this pair
     float rc2;                // (R_a + R_b)^2, R = circumradius about the pose point
     float r_cull;             // R_a + R_b plus a margin, for bounding-box culling
     int combo;                // 0 rect-rect, 1 rect(a)-disc(b), 2 disc(a)-rect(b), 3 disc-disc
-    int ego_side;             // 0: a is the EGO object, 1: b is, -1: neither
+    int ego_side;             // 0: a is its scenario's EGO object, 1: b is, -1: neither
+    int n_steps;              // steps of the pair's scenario
+    int scen;
+    long long kofs;           // first of the pair's n_steps entries in the per-step outputs (count_k, H)
+    // accumulators of the scenario's EGO hypotheses (used when ego_side >= 0)
+    long long lsum_base;      // cells [EGO hypothesis][step][CO object of the scenario]
+    long long mass_base;      // [EGO hypothesis][CO object of the scenario]
+    long long hits_base;      // [EGO hypothesis]
+    int n_obj_s;              // objects in the scenario
+    int co_local;             // the CO object's index in its scenario
+};
+
+// Per-scenario descriptor of a batch (device; risk stage).
+struct ScenDesc {
+    int ego;                  // global object index of the EGO object
+    int n_obj, n_steps, h_e;
+    int obj0;                 // global index of the scenario's first object
+    int pad_;
+    long long e_base;         // first global EGO hypothesis (per-EGO-hypothesis outputs, hits)
+    long long lsum_base, mass_base;
+    long long step_base;      // the scenario's n_steps entries of attr_step
 };
 
 struct GenArgs {
@@ -59,16 +86,13 @@ struct GenArgs {
     int n_warps;
     int lanes;                // hypotheses per warp task (1..32): fewer than 32 spreads small workloads
                               // over more warp schedulers, since each hypothesis is a sequential chain
-    int n_steps, substeps, model;
-    float tau;
-    double tau_i_d;           // (double)tau / substeps, the sub-step of the speed recurrence
     float *x, *y, *c, *s;
 };
 
 struct BoundsArgs {
     const ObjDesc *objs;
     const int *warp_obj, *warp_first;
-    int n_warps, n_steps;
+    int n_warps, max_steps;   // grid covers n_warps x max_steps; steps beyond an object's own are skipped
     const float *x, *y;
     float4 *bounds;
 };
@@ -81,15 +105,15 @@ constexpr int kFixLog = 40;    // sums of -log(1 - p): each term capped at 2^22
 
 struct RiskScratch {
     unsigned long long *count;     // [n_pairs]
-    unsigned long long *count_k;   // [n_pairs * N]
-    unsigned long long *P, *H;     // [n_pairs], [n_pairs * N]        sum p_a[i] p_b[j]
-    unsigned long long *hits;      // [h_e]                            colliding (b, j) per EGO hypothesis
-    unsigned long long *lsum;      // [h_e * N * n_obj]                sum -log(1 - p_b[j]) per (i, k, b) cell
-    unsigned long long *mass;      // [h_e * n_obj]                    sum p_b[j] per (i, b)
-    unsigned long long *attr_obj;  // [n_obj]
-    unsigned long long *attr_step; // [N]
-    double *scalars;               // [4]
-    unsigned long long *n_escape;  // [1] collision-free EGO hypotheses
+    unsigned long long *count_k;   // [sum over pairs of N]           (per pair at PairDesc::kofs)
+    unsigned long long *P, *H;     // [n_pairs], [sum over pairs of N] sum p_a[i] p_b[j]
+    unsigned long long *hits;      // [sum h_e]                        colliding (b, j) per EGO hypothesis
+    unsigned long long *lsum;      // [sum h_e N n_obj]                sum -log(1 - p_b[j]) per (i, k, b) cell
+    unsigned long long *mass;      // [sum h_e n_obj]                  sum p_b[j] per (i, b)
+    unsigned long long *attr_obj;  // [total objects]
+    unsigned long long *attr_step; // [sum over scenarios of N]
+    double *scalars;               // [4 per scenario]
+    unsigned long long *n_escape;  // [per scenario] collision-free EGO hypotheses
     unsigned long long *done;      // [1] EGO-walk CTAs finished (the last one converts the totals)
     unsigned long long *base;      // first word of the block
     long long n_words;             // words to zero
@@ -100,7 +124,7 @@ struct CollideArgs {
     const PairDesc *pairs;
     int n_pairs;
     long long n_tiles;        // total collision tiles over all pairs
-    int n_steps;
+    int max_steps;            // the longest horizon of the batch (sizes the per-CTA accumulators)
     int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
     int variant;              // 0: chosen by tile count, 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8
     const float *x, *y, *c, *s;
@@ -110,13 +134,17 @@ struct CollideArgs {
     // fused risk accumulation at first-hit time (probf null: table only)
     const float *probf;            // [n_traj] FP32 probabilities
     RiskScratch acc;               // accumulators, zeroed beforehand
-    int n_obj;
 };
 
 struct RiskArgs {
     const ObjDesc *objs;
     const PairDesc *pairs;
-    int n_pairs, n_obj, n_steps, ego, h_e;
+    const ScenDesc *scens;
+    int n_pairs, n_obj, n_scen;
+    long long h_e;                 // EGO hypotheses over all scenarios
+    long long n_kofs, n_steps_total;   // per-pair step entries, per-scenario step entries
+    int max_steps;                 // the longest horizon of the batch
+    int convert_in_walk;           // set by launch_risk_tail: the EGO walk's last CTA converts the totals
     long long n_tiles;
     const int16_t *table;
     const float *weights;          // [n_traj] raw non-negative weights, or null for uniform
@@ -157,6 +185,7 @@ cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st);
 cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st);   // table[0, n) = -1
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);               // stores first hits only
 cudaError_t launch_risk_prepare(const RiskArgs &a, cudaStream_t st);             // zero + normalise
+int risk_tail_launches(const RiskArgs &a);   // kernels launch_risk_tail launches
 cudaError_t launch_risk_tail(const RiskArgs &a, cudaStream_t st);                // ego walk + finish
 cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st);
 

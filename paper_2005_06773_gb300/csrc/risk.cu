@@ -44,6 +44,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(const RiskArgs a) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < a.acc.n_words; w += stride)
         a.acc.base[w] = 0ull;
+    if (a.escape)   // entries past each scenario's escape routes read -1
+        for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < a.h_e; w += stride) a.escape[w] = -1;
     if (blockIdx.x >= a.n_obj) return;
     const ObjDesc &o = a.objs[blockIdx.x];
     __shared__ double s_part[8];
@@ -86,12 +88,12 @@ __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
     const int i0 = ta * kTile, j0 = tb * kTile;
     const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
     const int tid = threadIdx.x;
-    const int N = a.n_steps;
-    const bool smem_hist = N <= kMaxSmemSteps;
+    const int N = P.n_steps;
+    const bool smem_hist = a.max_steps <= kMaxSmemSteps;
     unsigned long long *s_H = s_dyn64;
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_dyn64 + N);
     unsigned long long *s_L = s_dyn64 + N + (N + 1) / 2;
-    const bool smem_cells = smem_hist && N <= kMaxSmemCells && P.ego_side >= 0;
+    const bool smem_cells = smem_hist && a.max_steps <= kMaxSmemCells && P.ego_side >= 0;
     if (smem_hist)
         for (int k = tid; k < N; k += 64) { s_cnt[k] = 0u; s_H[k] = 0ull; }
     if (smem_cells)
@@ -125,28 +127,28 @@ __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
                     atomicAdd(s_cnt + T, 1u);
                     atomicAdd(s_H + T, w);
                 } else {
-                    atomicAdd(a.acc.count_k + (long long)p * N + T, 1ull);
-                    atomicAdd(a.acc.H + (long long)p * N + T, w);
+                    atomicAdd(a.acc.count_k + P.kofs + T, 1ull);
+                    atomicAdd(a.acc.H + P.kofs + T, w);
                 }
                 if (P.ego_side == 0) {          // row hypothesis belongs to the EGO object, CO = b
                     atomicAdd(s_row_mass + i, pb_fix);
                     atomicAdd(s_row_hits + i, 1u);
                     const unsigned long long lq = to_fixed(neg_log_survival(pb), kFixLog);
                     if (smem_cells) atomicAdd(s_L + i * N + T, lq);
-                    else atomicAdd(a.acc.lsum + ((long long)(i0 + i) * N + T) * a.n_obj + P.b, lq);
+                    else atomicAdd(a.acc.lsum + P.lsum_base + ((long long)(i0 + i) * N + T) * P.n_obj_s + P.co_local, lq);
                 } else if (P.ego_side == 1) {   // column hypothesis belongs to the EGO object, CO = a
                     col_mass += to_fixed(pa, kFixProb);
                     ++col_hits;
                     const unsigned long long lq = to_fixed(neg_log_survival(pa), kFixLog);
                     if (smem_cells) s_L[j * N + T] += lq;   // only this thread owns column j's cells
-                    else atomicAdd(a.acc.lsum + ((long long)(j0 + j) * N + T) * a.n_obj + P.a, lq);
+                    else atomicAdd(a.acc.lsum + P.lsum_base + ((long long)(j0 + j) * N + T) * P.n_obj_s + P.co_local, lq);
                 }
             }
         }
     }
     if (P.ego_side == 1 && col_hits) {
-        atomicAdd(a.acc.mass + (long long)(j0 + j) * a.n_obj + P.a, col_mass);
-        atomicAdd(a.acc.hits + j0 + j, (unsigned long long)col_hits);
+        atomicAdd(a.acc.mass + P.mass_base + (long long)(j0 + j) * P.n_obj_s + P.co_local, col_mass);
+        atomicAdd(a.acc.hits + P.hits_base + j0 + j, (unsigned long long)col_hits);
     }
     cnt = warp_sum(cnt);
     pm = warp_sum(pm);
@@ -158,31 +160,30 @@ __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
     if (smem_hist) {
         for (int k = tid; k < N; k += 64) {
             if (s_cnt[k]) {
-                atomicAdd(a.acc.count_k + (long long)p * N + k, (unsigned long long)s_cnt[k]);
-                atomicAdd(a.acc.H + (long long)p * N + k, s_H[k]);
+                atomicAdd(a.acc.count_k + P.kofs + k, (unsigned long long)s_cnt[k]);
+                atomicAdd(a.acc.H + P.kofs + k, s_H[k]);
             }
         }
     }
     if (smem_cells) {
-        const int e0 = P.ego_side == 0 ? i0 : j0, other = P.ego_side == 0 ? P.b : P.a;
+        const int e0 = P.ego_side == 0 ? i0 : j0;
         for (int q = tid; q < kTile * N; q += 64) {
             const unsigned long long v = s_L[q];
             if (v) {
                 const int e = q / N, k = q - e * N;
-                atomicAdd(a.acc.lsum + ((long long)(e0 + e) * N + k) * a.n_obj + other, v);
+                atomicAdd(a.acc.lsum + P.lsum_base + ((long long)(e0 + e) * N + k) * P.n_obj_s + P.co_local, v);
             }
         }
     }
     if (P.ego_side == 0 && tid < rows && s_row_hits[tid]) {
-        atomicAdd(a.acc.mass + (long long)(i0 + tid) * a.n_obj + P.b, s_row_mass[tid]);
-        atomicAdd(a.acc.hits + i0 + tid, (unsigned long long)s_row_hits[tid]);
+        atomicAdd(a.acc.mass + P.mass_base + (long long)(i0 + tid) * P.n_obj_s + P.co_local, s_row_mass[tid]);
+        atomicAdd(a.acc.hits + P.hits_base + i0 + tid, (unsigned long long)s_row_hits[tid]);
     }
 }
 
 // Writes the totals of the assessment into the caller's outputs (fixed point -> double).
 __device__ void convert_totals(const RiskArgs &a, int t, int nt) {
-    const long long npn = (long long)a.n_pairs * a.n_steps;
-    for (long long q = t; q < npn; q += nt) {
+    for (long long q = t; q < a.n_kofs; q += nt) {
         if (a.count_k) a.count_k[q] = (long long)a.acc.count_k[q];
         if (a.H) a.H[q] = from_fixed(a.acc.H[q], kFixProb);
     }
@@ -192,60 +193,61 @@ __device__ void convert_totals(const RiskArgs &a, int t, int nt) {
     }
     for (int q = t; q < a.n_obj; q += nt)
         if (a.attr_obj) a.attr_obj[q] = from_fixed(a.acc.attr_obj[q], kFixProb);
-    for (int q = t; q < a.n_steps; q += nt)
+    for (long long q = t; q < a.n_steps_total; q += nt)
         if (a.attr_step) a.attr_step[q] = from_fixed(a.acc.attr_step[q], kFixProb);
-    if (t < 4 && a.scalars) a.scalars[t] = t < 3 ? a.acc.scalars[t] : 0.0;
-    if (t == 0 && a.n_escape) *a.n_escape = (int)*a.acc.n_escape;
+    for (int q = t; q < 4 * a.n_scen; q += nt)
+        if (a.scalars) a.scalars[q] = (q & 3) < 3 ? a.acc.scalars[q] : 0.0;
+    for (int q = t; q < a.n_scen; q += nt)
+        if (a.n_escape) a.n_escape[q] = (int)a.acc.n_escape[q];
 }
 
-// One warp per EGO hypothesis.
+// One warp per EGO hypothesis of the batch (its scenario found by binary search).
 //  * collision-free hypothesis: its escape-route rank (Section VI-A) = the number of collision-free
-//    hypotheses more probable than it, ties by index, counted 32 at a time with ballots on integer keys
-//    (probabilities are non-negative, so their bit patterns order like the values);
+//    hypotheses of its scenario more probable than it, ties by index, counted 32 at a time with ballots on
+//    integer keys (probabilities are non-negative, so their bit patterns order like the values);
 //  * otherwise the chronological walk: the (step, object) cells are read in ascending order 32 at a time,
 //    128 per group with the four loads in flight together; a chunk with a non-empty cell gets an exclusive
 //    warp prefix product of the survival factors (1 - q), so each cell knows the survival S of every
 //    earlier cell and contributes S q.
 // The last CTA to finish converts the totals.
 __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
-    extern __shared__ unsigned long long s_attr[];   // [n_obj] then [N], fixed point
-    __shared__ double s_tot[3][2];
     __shared__ bool s_last;
-    const int N = a.n_steps, n_obj = a.n_obj;
-    const bool smem = (n_obj + N) <= 4096;
-    if (smem) {
-        for (int q = threadIdx.x; q < n_obj + N; q += blockDim.x) s_attr[q] = 0ull;
-        __syncthreads();
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
-    double naive = 0.0, cond = 0.0, indep = 0.0, pe = 0.0;
-    unsigned long long hits = 0;
-    if (i < a.h_e) {
-        const ObjDesc &E = a.objs[a.ego];
-        pe = a.prob[E.traj_off + i];
+    const int lane = threadIdx.x & 31;
+    const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g < a.h_e) {
+        int lo = 0, hi = a.n_scen - 1;     // the scenario of EGO hypothesis g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.scens[mid].e_base <= g) lo = mid; else hi = mid - 1;
+        }
+        const ScenDesc sd = a.scens[lo];
+        const int N = sd.n_steps, n_obj = sd.n_obj;
+        const long long i = g - sd.e_base;
+        const ObjDesc &E = a.objs[sd.ego];
+        const double pe = a.prob[E.traj_off + i];
         const float pef = a.probf[E.traj_off + i];
-        hits = a.acc.hits[i];
+        const unsigned long long hits = a.acc.hits[g];
+        double naive = 0.0, cond = 0.0, indep = 0.0;
         if (!hits) {
             if (a.escape) {
                 const long long key = __double_as_longlong(pe);
                 int rank = 0;
-                for (int q0 = 0; q0 < a.h_e; q0 += 32) {
+                for (int q0 = 0; q0 < sd.h_e; q0 += 32) {
                     const int q = q0 + lane;
                     bool above = false;
-                    if (q < a.h_e && a.acc.hits[q] == 0ull) {
+                    if (q < sd.h_e && a.acc.hits[sd.e_base + q] == 0ull) {
                         const long long kq = __double_as_longlong(a.prob[E.traj_off + q]);
                         above = kq > key || (kq == key && q < i);
                     }
                     rank += __popc(__ballot_sync(0xffffffffu, above));
                 }
-                if (lane == 0) a.escape[rank] = i;
+                if (lane == 0) a.escape[sd.e_base + rank] = (int)i;
             }
-            if (lane == 0) atomicAdd(a.acc.n_escape, 1ull);
+            if (lane == 0) atomicAdd(a.acc.n_escape + lo, 1ull);
         } else {
             // per-object masses: naive sum and independence product
             double surv = 1.0, mass_sum = 0.0;
-            const unsigned long long *ms = a.acc.mass + (long long)i * n_obj;
+            const unsigned long long *ms = a.acc.mass + sd.mass_base + i * n_obj;
             for (int b = lane; b < n_obj; b += 32) {
                 const double m = from_fixed(ms[b], kFixProb);
                 mass_sum += m;
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
             naive = warp_sum(mass_sum);
             indep = 1.0 - surv;
             // chronological walk over the cells
-            const unsigned long long *lc = a.acc.lsum + (long long)i * N * n_obj;
+            const unsigned long long *lc = a.acc.lsum + sd.lsum_base + i * N * n_obj;
             const long long cells = (long long)N * n_obj;
             double carry = 1.0, part = 0.0;   // carry: survival product of every cell before the chunk
             for (long long g0 = 0; g0 < cells; g0 += 128) {
@@ -285,13 +287,8 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
                     if (lf) {
                         const int k = (int)(c / n_obj), b = (int)(c - (long long)k * n_obj);
                         const unsigned long long w = to_fixed(pef * (float)eff, kFixProb);
-                        if (smem) {
-                            atomicAdd(s_attr + b, w);
-                            atomicAdd(s_attr + n_obj + k, w);
-                        } else {
-                            atomicAdd(a.acc.attr_obj + b, w);
-                            atomicAdd(a.acc.attr_step + k, w);
-                        }
+                        atomicAdd(a.acc.attr_obj + sd.obj0 + b, w);
+                        atomicAdd(a.acc.attr_step + sd.step_base + k, w);
                     }
                     carry *= __shfl_sync(0xffffffffu, incl, 31);
                 }
@@ -299,26 +296,16 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
             cond = warp_sum(part);
         }
         if (lane == 0) {
-            if (a.naive) a.naive[i] = naive;
-            if (a.cond) a.cond[i] = cond;
-            if (a.indep) a.indep[i] = indep;
-            if (a.hits) a.hits[i] = (int)hits;
+            if (a.naive) a.naive[g] = naive;
+            if (a.cond) a.cond[g] = cond;
+            if (a.indep) a.indep[g] = indep;
+            if (a.hits) a.hits[g] = (int)hits;
+            if (naive != 0.0) atomicAdd(a.acc.scalars + 4 * lo + 0, pe * naive);
+            if (cond != 0.0) atomicAdd(a.acc.scalars + 4 * lo + 1, pe * cond);
+            if (indep != 0.0) atomicAdd(a.acc.scalars + 4 * lo + 2, pe * indep);
         }
     }
-    if (lane == 0) {
-        s_tot[0][warp] = pe * naive; s_tot[1][warp] = pe * cond; s_tot[2][warp] = pe * indep;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        const double t = s_tot[threadIdx.x][0] + s_tot[threadIdx.x][1];
-        if (t != 0.0) atomicAdd(a.acc.scalars + threadIdx.x, t);
-    }
-    if (smem) {
-        for (int q = threadIdx.x; q < n_obj + N; q += blockDim.x) {
-            const unsigned long long v = s_attr[q];
-            if (v) atomicAdd(q < n_obj ? a.acc.attr_obj + q : a.acc.attr_step + (q - n_obj), v);
-        }
-    }
+    if (!a.convert_in_walk) return;
     // the last CTA converts the totals once every CTA's atomics are visible
     __threadfence();
     __syncthreads();
@@ -330,8 +317,18 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
     }
 }
 
-// Without EGO hypotheses to walk (h_e == 0 cannot happen for a valid scenario) the totals still convert.
-__global__ void __launch_bounds__(256) totals_kernel(const RiskArgs a) { convert_totals(a, threadIdx.x, 256); }
+// The totals of a large batch, grid-wide after the walk (or without EGO hypotheses to walk).
+__global__ void __launch_bounds__(256) totals_kernel(const RiskArgs a) {
+    convert_totals(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// Elements the totals conversion writes; up to this many the walk's last CTA converts them (one launch
+// less), beyond it a grid-wide kernel does.
+constexpr long long kConvertInWalk = 32768;
+
+long long convert_elements(const RiskArgs &a) {
+    return 2 * a.n_kofs + 2LL * a.n_pairs + a.n_obj + a.n_steps_total + 5LL * a.n_scen;
+}
 
 }  // namespace
 
@@ -341,12 +338,19 @@ cudaError_t launch_risk_prepare(const RiskArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_risk_tail(const RiskArgs &a, cudaStream_t st) {
-    if (a.h_e > 0) {
-        const size_t smem = (a.n_obj + a.n_steps) <= 4096 ? 8 * (size_t)(a.n_obj + a.n_steps) : 0;
-        ego_kernel<<<(a.h_e + 1) / 2, 64, smem, st>>>(a);
-    } else {
-        totals_kernel<<<1, 256, 0, st>>>(a);
+int risk_tail_launches(const RiskArgs &a) {
+    return (a.h_e > 0 ? 1 : 0) + (a.h_e > 0 && convert_elements(a) <= kConvertInWalk ? 0 : 1);
+}
+
+cudaError_t launch_risk_tail(const RiskArgs &args, cudaStream_t st) {
+    RiskArgs a = args;
+    const long long conv = convert_elements(a);
+    a.convert_in_walk = a.h_e > 0 && conv <= kConvertInWalk;
+    if (a.h_e > 0) ego_kernel<<<(unsigned)((a.h_e + 1) / 2), 64, 0, st>>>(a);
+    if (!a.convert_in_walk) {
+        long long blocks = (conv + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        totals_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -357,8 +361,8 @@ cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st) {
     if (a.n_tiles > 0) {
         if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
         size_t smem = 0;
-        if (a.n_steps <= kMaxSmemSteps) smem = 8 * ((size_t)a.n_steps + (a.n_steps + 1) / 2);
-        if (a.n_steps <= kMaxSmemCells) smem += 8 * (size_t)kTile * a.n_steps;
+        if (a.max_steps <= kMaxSmemSteps) smem = 8 * ((size_t)a.max_steps + (a.max_steps + 1) / 2);
+        if (a.max_steps <= kMaxSmemCells) smem += 8 * (size_t)kTile * a.max_steps;
         if (smem > 48 * 1024) {
             e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;

@@ -112,6 +112,8 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
         d.h = src.n_a * src.n_b;
         d.traj_off = traj;
         d.pose_base = traj * (long long)N;
+        d.bounds_base = (long long)tiles32 * N;
+        d.n_steps = N;
         traj += d.h;
         d.tile_base = tiles32;
         d.n_tiles32 = (d.h + kBoundTile - 1) / kBoundTile;
@@ -153,6 +155,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
             p.r_cull = (float)(R * (1.0 + 1e-6) + 1e-3);
             p.combo = (A.kind == MHC_VEHICLE ? 0 : 2) + (B.kind == MHC_VEHICLE ? 0 : 1);
             p.ego_side = a == sc->ego ? 0 : (b == sc->ego ? 1 : -1);
+            p.n_steps = N;
             entries += (long long)A.h * B.h;
             tiles += (long long)p.tiles_a * p.tiles_b;
         }
@@ -193,7 +196,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
     b.warp_obj = d_warp_obj;
     b.warp_first = d_warp_first;
     b.n_warps = tiles32;
-    b.n_steps = N;
+    b.max_steps = N;
     b.x = poses->x;
     b.y = poses->y;
     b.bounds = d_bounds;
@@ -204,7 +207,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
     c.pairs = d_pairs;
     c.n_pairs = n_pairs;
     c.n_tiles = tiles;
-    c.n_steps = N;
+    c.max_steps = N;
     c.cull = 1;
     c.x = poses->x;
     c.y = poses->y;

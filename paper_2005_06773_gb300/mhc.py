@@ -49,6 +49,20 @@ class MhcPoses(ctypes.Structure):
     _fields_ = [("x", c_void_p), ("y", c_void_p), ("c", c_void_p), ("s", c_void_p)]
 
 
+class MhcBatchInfo(ctypes.Structure):
+    _fields_ = [("n_traj", c_int64), ("n_poses", c_int64), ("n_entries", c_int64), ("n_step_entries", c_int64),
+                ("n_scen_steps", c_int64), ("h_ego", c_int64), ("n_pairs", c_int32), ("n_objects", c_int32),
+                ("n_scenarios", c_int32), ("max_steps", c_int32), ("scratch", c_size_t), ("plan_bytes", c_size_t)]
+
+
+class MhcBatchSlice(ctypes.Structure):
+    _fields_ = [("obj0", c_int32), ("n_objects", c_int32), ("pair0", c_int32), ("n_pairs", c_int32),
+                ("n_steps", c_int32), ("ego", c_int32), ("traj0", c_int64), ("pose0", c_int64),
+                ("entry0", c_int64), ("step_entry0", c_int64), ("ego0", c_int64), ("step0", c_int64)]
+
+
+MHC_PLAN_GRAPH = 1
+
 RISK_FIELDS = ("count", "count_k", "P", "H", "naive", "cond", "indep", "hits", "attr_obj", "attr_step",
                "scalars", "escape", "n_escape")
 
@@ -84,6 +98,18 @@ def _load():
     L.mhc_autotune.argtypes = [c_void_p, POINTER(MhcScenario), POINTER(MhcPoses), c_void_p, c_int,
                                POINTER(c_int32), POINTER(c_int32), c_void_p]
     L.mhc_run_bytes.argtypes = [POINTER(MhcScenario), POINTER(c_size_t)]
+    L.mhc_batch_layout.argtypes = [POINTER(MhcScenario), c_int32, POINTER(MhcBatchInfo), c_void_p]
+    L.mhc_batch_pair_table.argtypes = [POINTER(MhcScenario), c_int32, c_void_p, c_void_p, c_void_p]
+    L.mhc_evaluate_batch.argtypes = [c_void_p, POINTER(MhcScenario), c_int32, c_void_p, POINTER(MhcPoses),
+                                     c_void_p, POINTER(MhcRisk), c_void_p]
+    L.mhc_autotune_batch.argtypes = [c_void_p, POINTER(MhcScenario), c_int32, POINTER(MhcPoses), c_void_p, c_int,
+                                     POINTER(c_int32), POINTER(c_int32), c_void_p]
+    L.mhc_plan_create.argtypes = [c_void_p, POINTER(MhcScenario), c_int32, c_void_p, POINTER(MhcPoses), c_void_p,
+                                  POINTER(MhcRisk), c_void_p, c_size_t, c_int32, POINTER(c_void_p)]
+    L.mhc_plan_update.argtypes = [c_void_p, POINTER(MhcScenario), c_int32]
+    L.mhc_plan_launch.argtypes = [c_void_p, c_void_p]
+    L.mhc_plan_destroy.argtypes = [c_void_p]
+    L.mhc_plan_destroy.restype = None
     L.mhc_run.argtypes = [c_void_p, POINTER(MhcScenario), c_void_p, POINTER(MhcRisk), c_void_p]
     return L
 
@@ -353,3 +379,164 @@ def poses_to_device(sc, arr: np.ndarray, device="cuda") -> torch.Tensor:
         parts.append(np.ascontiguousarray(arr[t: t + h].T).reshape(-1))
         t += h
     return torch.from_numpy(np.concatenate(parts).astype(np.float32)).to(device)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# batches of scenarios
+
+class CBatch:
+    """A list of scenarios marshalled into one contiguous C array (keeps every host array alive)."""
+
+    def __init__(self, scenarios):
+        self.items = [as_c(sc) for sc in scenarios]
+        if not self.items:
+            raise ValueError("a batch needs at least one scenario")
+        arr = (MhcScenario * len(self.items))()
+        for q, cs in enumerate(self.items):
+            arr[q] = cs.c
+        self.arr = arr
+        self.n = len(self.items)
+        self.ref = ctypes.cast(arr, POINTER(MhcScenario))
+
+    @property
+    def scenarios(self):
+        return [cs.sc for cs in self.items]
+
+
+def as_batch(scenarios) -> CBatch:
+    return scenarios if isinstance(scenarios, CBatch) else CBatch(scenarios)
+
+
+SLICE_FIELDS = [f for f, _ in MhcBatchSlice._fields_]
+
+
+def batch_layout(scenarios):
+    """(info dict, slices: list of dicts) of a batch, from mhc_batch_layout."""
+    cb = as_batch(scenarios)
+    info = MhcBatchInfo()
+    sl = (MhcBatchSlice * cb.n)()
+    _check(lib.mhc_batch_layout(cb.ref, cb.n, ctypes.byref(info), ctypes.cast(sl, c_void_p)), "mhc_batch_layout")
+    d = {f: int(getattr(info, f)) for f, _ in MhcBatchInfo._fields_}
+    return d, [{f: int(getattr(x, f)) for f in SLICE_FIELDS} for x in sl]
+
+
+def batch_pair_table(scenarios):
+    cb = as_batch(scenarios)
+    n = batch_layout(cb)[0]["n_pairs"]
+    pa, pb = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    poff = np.zeros(n + 1, np.int64)
+    _check(lib.mhc_batch_pair_table(cb.ref, cb.n, pa.ctypes.data, pb.ctypes.data, poff.ctypes.data),
+           "mhc_batch_pair_table")
+    return pa, pb, poff
+
+
+def batch_risk_shapes(info) -> Dict[str, tuple]:
+    np_, nk, he, no, ns = info["n_pairs"], info["n_step_entries"], info["h_ego"], info["n_objects"], info["n_scenarios"]
+    return dict(count=((np_,), torch.int64), count_k=((nk,), torch.int64), P=((np_,), torch.float64),
+                H=((nk,), torch.float64), naive=((he,), torch.float64), cond=((he,), torch.float64),
+                indep=((he,), torch.float64), hits=((he,), torch.int32), attr_obj=((no,), torch.float64),
+                attr_step=((info["n_scen_steps"],), torch.float64), scalars=((4 * ns,), torch.float64),
+                escape=((he,), torch.int32), n_escape=((ns,), torch.int32))
+
+
+def alloc_batch(info, device="cuda"):
+    """(poses, table, risk outputs) device buffers of a batch."""
+    poses = {k: torch.empty(info["n_poses"], dtype=torch.float32, device=device) for k in ("x", "y", "c", "s")}
+    table = torch.empty(info["n_entries"], dtype=torch.int16, device=device)
+    out = {k: torch.zeros(shape, dtype=dt, device=device) for k, (shape, dt) in batch_risk_shapes(info).items()}
+    return poses, table, out
+
+
+def scenario_view(out: Dict[str, torch.Tensor], sl: dict) -> Dict[str, torch.Tensor]:
+    """Scenario `sl`'s part (a slice from batch_slices) of batch risk outputs, shaped like the
+    single-scenario outputs."""
+    p0, npair, N = sl["pair0"], sl["n_pairs"], sl["n_steps"]
+    k0, e0, he, q = sl["step_entry0"], sl["ego0"], sl["h_ego"], sl["index"]
+    return dict(count=out["count"][p0: p0 + npair], count_k=out["count_k"][k0: k0 + npair * N].view(npair, N),
+                P=out["P"][p0: p0 + npair], H=out["H"][k0: k0 + npair * N].view(npair, N),
+                naive=out["naive"][e0: e0 + he], cond=out["cond"][e0: e0 + he], indep=out["indep"][e0: e0 + he],
+                hits=out["hits"][e0: e0 + he], attr_obj=out["attr_obj"][sl["obj0"]: sl["obj0"] + sl["n_objects"]],
+                attr_step=out["attr_step"][sl["step0"]: sl["step0"] + N], scalars=out["scalars"][4 * q: 4 * q + 4],
+                escape=out["escape"][e0: e0 + he], n_escape=out["n_escape"][q: q + 1])
+
+
+def batch_slices(scenarios):
+    """Per-scenario slices with the scenario's index and EGO hypothesis count added."""
+    cb = as_batch(scenarios)
+    info, sls = batch_layout(cb)
+    for q, (sl, sc) in enumerate(zip(sls, cb.scenarios)):
+        sl["index"] = q
+        e = sc.objects[sc.ego]
+        sl["h_ego"] = int(np.asarray(e.grid_a).size * np.asarray(e.grid_b).size)
+    return info, sls
+
+
+def evaluate_batch(ctx: Context, scenarios, poses=None, table=None, weights=None, out=None, stream=None):
+    """The whole method over a batch in one launch sequence.  Returns (poses, table, risk outputs)."""
+    cb = as_batch(scenarios)
+    info, _ = batch_layout(cb)
+    if poses is None or table is None or out is None:
+        p2, t2, o2 = alloc_batch(info)
+        poses = p2 if poses is None else poses
+        table = t2 if table is None else table
+        out = o2 if out is None else out
+    ps = _poses_struct(poses)
+    rs = _risk_struct(out)
+    w = weights if isinstance(weights, CWeights) else CWeights(weights)
+    _check(lib.mhc_evaluate_batch(ctx.h, cb.ref, cb.n, w.ptr, ctypes.byref(ps), table.data_ptr(), ctypes.byref(rs),
+                                  _stream(stream)), "mhc_evaluate_batch")
+    return poses, table, out
+
+
+def autotune_batch(ctx: Context, scenarios, poses, table, fused: bool = True, stream=None):
+    cb = as_batch(scenarios)
+    ps = _poses_struct(poses)
+    v, c = c_int32(), c_int32()
+    _check(lib.mhc_autotune_batch(ctx.h, cb.ref, cb.n, ctypes.byref(ps), table.data_ptr(), int(fused),
+                                  ctypes.byref(v), ctypes.byref(c), _stream(stream)), "mhc_autotune_batch")
+    return v.value, c.value
+
+
+class Plan:
+    """A batch laid out once (descriptors in a torch-owned scratch buffer) and, with graph=True, its launch
+    sequence captured as a CUDA graph; launch() replays it, update() swaps in scenarios of the same
+    structure (new initial states)."""
+
+    def __init__(self, ctx: Context, scenarios, weights=None, graph: bool = True, buffers=None):
+        self.ctx = ctx
+        self.batch = as_batch(scenarios)
+        self.info, _ = batch_layout(self.batch)
+        dev = f"cuda:{ctx.device}"
+        self.poses, self.table, self.out = alloc_batch(self.info, dev) if buffers is None else buffers
+        self.scratch = torch.empty(int(self.info["plan_bytes"]) + 256, dtype=torch.uint8, device=dev)
+        base = self.scratch.data_ptr()
+        off = (-base) % 256
+        self._w = weights if isinstance(weights, CWeights) else CWeights(weights)
+        ps = _poses_struct(self.poses)
+        rs = _risk_struct(self.out)
+        h = c_void_p()
+        _check(lib.mhc_plan_create(ctx.h, self.batch.ref, self.batch.n, self._w.ptr, ctypes.byref(ps),
+                                   self.table.data_ptr(), ctypes.byref(rs), base + off,
+                                   self.scratch.numel() - off, MHC_PLAN_GRAPH if graph else 0, ctypes.byref(h)),
+               "mhc_plan_create")
+        self.h = h
+
+    def update(self, scenarios):
+        cb = as_batch(scenarios)
+        _check(lib.mhc_plan_update(self.h, cb.ref, cb.n), "mhc_plan_update")
+        self.batch = cb
+
+    def launch(self, stream=None):
+        _check(lib.mhc_plan_launch(self.h, _stream(stream)), "mhc_plan_launch")
+        return self.poses, self.table, self.out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.mhc_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

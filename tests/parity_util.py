@@ -82,8 +82,10 @@ def check_risk(gpu, orc_r, he):
     np.testing.assert_array_equal(g["count"], orc_r["count"])
     np.testing.assert_array_equal(g["count_k"], orc_r["count_k"])
     np.testing.assert_array_equal(g["hits"], orc_r["hits"])
-    np.testing.assert_array_equal(g["escape"][: int(g["n_escape"][0])], orc_r["escape"])
-    assert int(g["n_escape"][0]) == len(orc_r["escape"])
+    n_esc = int(g["n_escape"][0])
+    assert n_esc == len(orc_r["escape"])
+    np.testing.assert_array_equal(g["escape"][:n_esc], orc_r["escape"])
+    assert np.all(g["escape"][n_esc:] == -1)
     for k in ("P", "H", "naive", "cond", "indep", "attr_obj", "attr_step"):
         np.testing.assert_allclose(g[k], orc_r[k], rtol=PROB_RTOL, atol=1e-15, err_msg=k)
     np.testing.assert_allclose(g["scalars"][:3], orc_r["scalars"], rtol=PROB_RTOL, atol=1e-15)
