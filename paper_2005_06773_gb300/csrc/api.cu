@@ -554,7 +554,7 @@ int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
     if (option == MHC_OPT_CULL) { ctx->cull = value != 0; return MHC_OK; }
     if (option == MHC_OPT_PROFILE) { ctx->profile = value != 0; return MHC_OK; }
     if (option == MHC_OPT_COLLIDE_VARIANT) {
-        if (value < 0 || value > 3) return fail(MHC_E_INVALID, "collide variant must be 0 to 3");
+        if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 4");
         ctx->variant = (int)value;
         return MHC_OK;
     }
@@ -739,7 +739,7 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
     int bv = 1, bc = 1, rc = MHC_OK;
     ctx->profile = true;
     for (int cull = 1; cull >= 0 && rc == MHC_OK; --cull) {
-        for (int v = 1; v <= 3 && rc == MHC_OK; ++v) {
+        for (int v = 1; v <= kCollideVariants && rc == MHC_OK; ++v) {
             ctx->variant = v;
             ctx->cull = cull;
             double ms[MHC_K_COUNT];

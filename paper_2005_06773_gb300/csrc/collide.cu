@@ -668,6 +668,242 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
     }
 }
 
+// Warp-per-tile layout: each warp owns one 64 x 64 tile and walks its active steps in ascending order on
+// its own (no CTA barrier anywhere).  A lane holds an 8 x 16 micro-tile (rows lr + 8 m, columns lc + 4 n,
+// lr = lane / 4, lc = lane % 4) and a 128-bit register mask of its pairs that have already hit: because
+// the steps come in order, the first narrow-phase hit of a pair is its first collision step, it is stored
+// at once, and later candidates of that pair are dropped before any further work.  The warp stages each
+// step's 64 + 64 poses in its own shared-memory slot; the next active step's poses are loaded into
+// registers while the current step is tested.  Activity (tile-level culling) is decided 32 steps at a
+// time with one ballot.  Fused risk terms are added per hit with global atomics; the per-step histogram
+// terms of one step's hits are summed over the warp first.
+template <int WARPS, bool FUSED>
+__global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const CollideArgs a) {
+    constexpr int QCAP = 256;
+    __shared__ float4 s_pa[WARPS][kTile];                 // x, y, h_a
+    __shared__ float4 s_pb[WARPS][kTile];                 // x, y, h_b
+    __shared__ float2 s_ra[WARPS][kTile];                 // c, s
+    __shared__ float2 s_rb[WARPS][kTile];
+    __shared__ unsigned short s_queue[WARPS][QCAP];       // candidates: owner lane << 7 | bit
+    __shared__ unsigned long long s_new[WARPS][32][2];     // pairs found in this step, in owner-lane layout
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long g = (long long)blockIdx.x * WARPS + warp;
+    if (g >= a.n_tiles) return;                            // whole warps leave; no CTA barrier follows
+    int lo = 0, hi = a.n_pairs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
+    }
+    const PairDesc P = a.pairs[lo];
+    const ObjDesc &A = a.objs[P.a];
+    const ObjDesc &B = a.objs[P.b];
+    const long long t = g - P.tile_start;
+    const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
+    const int i0 = ta * kTile, j0 = tb * kTile;
+    const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
+    const int lr = lane >> 2, lc = lane & 3;
+    const int N = P.n_steps;
+    const int na = (rows + kBoundTile - 1) / kBoundTile, nb = (cols + kBoundTile - 1) / kBoundTile;
+    const float4 *bA0 = a.bounds + A.bounds_base + (long long)(ta * 2) * N;
+    const float4 *bB0 = a.bounds + B.bounds_base + (long long)(tb * 2) * N;
+    const float la = A.hl, wa = A.hw, ra = A.rad, lb = B.hl, wb = B.hw, rb = B.rad;
+    const float rc2 = P.rc2 + kEps0;
+    const float ka = 0.5f * (1.0f - kEps);
+    const float r_cull = P.r_cull;
+    float4 *pa_s = s_pa[warp], *pb_s = s_pb[warp];
+    float2 *ra_s = s_ra[warp], *rb_s = s_rb[warp];
+    unsigned short *queue = s_queue[warp];
+    unsigned long long *newf = s_new[warp][lane];
+    newf[0] = newf[1] = 0ull;
+
+    // activity of the 32 steps from k0 (one ballot)
+    auto chunk_mask = [&](int k0) -> unsigned {
+        const int k = k0 + lane;
+        bool act = k < N;
+        if (act && a.cull) {
+            float4 ba = bA0[k];
+            if (na > 1) {
+                const float4 q = bA0[N + k];
+                ba = make_float4(fminf(ba.x, q.x), fminf(ba.y, q.y), fmaxf(ba.z, q.z), fmaxf(ba.w, q.w));
+            }
+            float4 bb = bB0[k];
+            if (nb > 1) {
+                const float4 q = bB0[N + k];
+                bb = make_float4(fminf(bb.x, q.x), fminf(bb.y, q.y), fmaxf(bb.z, q.z), fmaxf(bb.w, q.w));
+            }
+            act = (ba.x - r_cull <= bb.z) && (bb.x - r_cull <= ba.z) && (ba.y - r_cull <= bb.w) &&
+                  (bb.y - r_cull <= ba.w);
+        }
+        return __ballot_sync(0xffffffffu, act);
+    };
+    int k0 = 0;
+    unsigned mask = chunk_mask(0);
+    // next active step after k (-1: none); advances k0 / mask (warp-uniform)
+    auto next_step = [&](int k) -> int {
+        unsigned m = k < k0 ? mask : mask & ~((2u << (k - k0)) - 1u);
+        while (!m) {
+            k0 += 32;
+            if (k0 >= N) return -1;
+            mask = chunk_mask(k0);
+            m = mask;
+        }
+        return k0 + __ffs(m) - 1;
+    };
+    // this lane's share of a step's poses: rows lane, lane + 32 of A and columns lane, lane + 32 of B
+    float px[4], py[4], pc[4], ps[4];
+    auto load_step = [&](int k) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = lane + 32 * (u & 1);
+            const bool isA = u < 2;
+            const bool ok = isA ? r < rows : r < cols;
+            const long long idx = isA ? A.pose_base + (long long)k * A.h + i0 + r
+                                      : B.pose_base + (long long)k * B.h + j0 + r;
+            px[u] = ok ? __ldg(a.x + idx) : (isA ? kFar : -kFar);
+            py[u] = ok ? __ldg(a.y + idx) : 0.0f;
+            pc[u] = ok ? __ldg(a.c + idx) : 1.0f;
+            ps[u] = ok ? __ldg(a.s + idx) : 0.0f;
+        }
+    };
+
+    unsigned long long found_lo = 0ull, found_hi = 0ull;   // bit 16 m + n (m < 4), 16 (m - 4) + n
+    unsigned long long narrow = 0, hit_cnt = 0, hit_mass = 0;
+    int active_steps = 0;
+    int k = next_step(-1);
+    if (k >= 0) load_step(k);
+    while (k >= 0) {
+        __syncwarp();                       // the previous step's slot is no longer read
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = lane + 32 * (u & 1);
+            const float q2 = fmaf(px[u], px[u], py[u] * py[u]);
+            if (u < 2) {
+                pa_s[r] = make_float4(px[u], py[u], ka * q2, 0.0f);
+                ra_s[r] = make_float2(pc[u], ps[u]);
+            } else {
+                pb_s[r] = make_float4(px[u], py[u], 0.5f * fmaf(1.0f - kEps, q2, -rc2), 0.0f);
+                rb_s[r] = make_float2(pc[u], ps[u]);
+            }
+        }
+        __syncwarp();
+        const int kn = next_step(k);
+        if (kn >= 0) load_step(kn);         // in flight while this step is tested
+        ++active_steps;
+        // broad phase: candidate bit of (m, n) = 16 m + n, rows 0-3 in c_lo, 4-7 in c_hi
+        float ax[8], ay[8], ah[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const float4 q = pa_s[lr + 8 * m];
+            ax[m] = q.x; ay[m] = q.y; ah[m] = q.z;
+        }
+        unsigned long long c_lo = 0ull, c_hi = 0ull;
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+            const float4 qb = pb_s[lc + 4 * n];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                if (fmaf(ax[m], qb.x, fmaf(ay[m], qb.y, -qb.z)) >= ah[m]) {
+                    if (m < 4) c_lo |= 1ull << (16 * m + n);
+                    else c_hi |= 1ull << (16 * (m - 4) + n);
+                }
+            }
+        }
+        c_lo &= ~found_lo;
+        c_hi &= ~found_hi;
+        if (__ballot_sync(0xffffffffu, (c_lo | c_hi) != 0ull)) {
+            bool any_hit = false;
+            unsigned long long step_cnt = 0, step_mass = 0;
+            // compact and test one candidate per lane, in rounds of at most 8 per lane
+            for (;;) {
+                const int cnt = min(__popcll(c_lo) + __popcll(c_hi), 8);
+                if (!__ballot_sync(0xffffffffu, cnt != 0)) break;
+                int off = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, off, d);
+                    if (lane >= d) off += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, off, 31);
+                off -= cnt;
+                for (int q = 0; q < cnt; ++q) {
+                    int bit;
+                    if (c_lo) { bit = __ffsll((long long)c_lo) - 1; c_lo &= c_lo - 1ull; }
+                    else { bit = 64 + __ffsll((long long)c_hi) - 1; c_hi &= c_hi - 1ull; }
+                    queue[off + q] = (unsigned short)((lane << 7) | bit);
+                }
+                __syncwarp();
+                narrow += total;
+                for (int e = lane; e < total; e += 32) {
+                    const int ent = queue[e];
+                    const int owner = ent >> 7, bit = ent & 127;
+                    const int m = bit >> 4, n = bit & 15;
+                    const int i = (owner >> 2) + 8 * m, j = (owner & 3) + 4 * n;
+                    const float4 qa4 = pa_s[i], qb4 = pb_s[j];
+                    const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
+                    const float2 qa = ra_s[i], qb = rb_s[j];
+                    bool hit;
+                    switch (P.combo) {
+                        case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
+                        case 1: hit = rect_disc(dx, dy, qa.x, qa.y, la, wa, rb); break;
+                        case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
+                        default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
+                    }
+                    if (hit) {
+                        any_hit = true;
+                        atomicOr(s_new[warp][owner] + (bit >> 6), 1ull << (bit & 63));
+                        a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
+                        if (FUSED) {
+                            const float pa_ = a.probf[A.traj_off + i0 + i], pb_ = a.probf[B.traj_off + j0 + j];
+                            const unsigned long long w = to_fixed(pa_ * pb_, kFixProb);
+                            ++step_cnt;
+                            step_mass += w;
+                            if (P.ego_side >= 0) {
+                                const int e = P.ego_side == 0 ? i0 + i : j0 + j;     // the EGO hypothesis
+                                const float pco = P.ego_side == 0 ? pb_ : pa_;       // the CO hypothesis
+                                atomicAdd(a.acc.mass + P.mass_base + (long long)e * P.n_obj_s + P.co_local,
+                                          to_fixed(pco, kFixProb));
+                                atomicAdd(a.acc.hits + P.hits_base + e, 1ull);
+                                atomicAdd(a.acc.lsum + P.lsum_base + ((long long)e * N + k) * P.n_obj_s + P.co_local,
+                                          to_fixed(neg_log_survival(pco), kFixLog));
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (__any_sync(0xffffffffu, any_hit)) {
+                __syncwarp();
+                found_lo |= newf[0];
+                found_hi |= newf[1];
+                newf[0] = newf[1] = 0ull;
+                if (FUSED) {
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) {
+                        step_cnt += __shfl_xor_sync(0xffffffffu, step_cnt, d);
+                        step_mass += __shfl_xor_sync(0xffffffffu, step_mass, d);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(a.acc.count_k + P.kofs + k, step_cnt);
+                        atomicAdd(a.acc.H + P.kofs + k, step_mass);
+                    }
+                    hit_cnt += step_cnt;
+                    hit_mass += step_mass;
+                }
+            }
+        }
+        k = kn;
+    }
+    if (a.counters && lane == 0) {
+        if (narrow) atomicAdd(a.counters + 1, narrow);
+        if (active_steps) atomicAdd(a.counters, (unsigned long long)active_steps * kTile * kTile);
+    }
+    if (FUSED && lane == 0 && hit_cnt) {
+        atomicAdd(a.acc.count + lo, hit_cnt);
+        atomicAdd(a.acc.P + lo, hit_mass);
+    }
+}
+
 // table[0, n) = -1 (no collision), 16-byte stores on the aligned body
 __global__ void __launch_bounds__(256) fill_kernel(int16_t *table, long long n) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -723,9 +959,18 @@ cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int WARPS, bool FUSED>
+cudaError_t launch_tile_variant(const CollideArgs &a, cudaStream_t st) {
+    const long long blocks = (a.n_tiles + WARPS - 1) / WARPS;
+    collide_tile_kernel<WARPS, FUSED><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (a.variant == 4)
+        return a.probf ? launch_tile_variant<4, true>(a, st) : launch_tile_variant<4, false>(a, st);
     // variant 1: 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests); variant 2: 8 x 8 with
     // 64 threads; variant 3: one warp per step (8 x 16 lanes).  The caller picks one (autotuned per size).
     const bool many = a.variant == 2;
