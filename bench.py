@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the stress32 / paper_s2 measurements")
-    ap.add_argument("--collide-variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--collide-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="collision kernel layout; 0 = chosen by mhc_autotune in the set-up (profiling fixes one)")
     ap.add_argument("--workload", default="intersection11", choices=sorted(WORKLOADS),
                     help="the timed workload (the default is the benchmark's; the others serve profiling)")

@@ -168,6 +168,7 @@ void mhc_destroy(mhc_ctx *ctx);
  *                 3: 4 warps per tile, each warp testing whole steps (8 x 16 micro-tiles per lane);
  *                 4: one warp per tile walking its steps in order (8 x 16 micro-tiles per lane, pairs that
  *                    already hit dropped from later steps, first hits stored at once);
+ *                 5: as 4 with one warp per 32 x 32 quarter tile (4 x 8 micro-tiles, culling per quarter);
  *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 3 for at
  *                 least 32 tiles per SM and 1 below. */
 #define MHC_OPT_COLLIDE_VARIANT 3

@@ -554,7 +554,7 @@ int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
     if (option == MHC_OPT_CULL) { ctx->cull = value != 0; return MHC_OK; }
     if (option == MHC_OPT_PROFILE) { ctx->profile = value != 0; return MHC_OK; }
     if (option == MHC_OPT_COLLIDE_VARIANT) {
-        if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 4");
+        if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 5");
         ctx->variant = (int)value;
         return MHC_OK;
     }

@@ -668,28 +668,34 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
     }
 }
 
-// Warp-per-tile layout: each warp owns one 64 x 64 tile and walks its active steps in ascending order on
-// its own (no CTA barrier anywhere).  A lane holds an 8 x 16 micro-tile (rows lr + 8 m, columns lc + 4 n,
-// lr = lane / 4, lc = lane % 4) and a 128-bit register mask of its pairs that have already hit: because
-// the steps come in order, the first narrow-phase hit of a pair is its first collision step, it is stored
-// at once, and later candidates of that pair are dropped before any further work.  The warp stages each
-// step's 64 + 64 poses in its own shared-memory slot; the next active step's poses are loaded into
-// registers while the current step is tested.  Activity (tile-level culling) is decided 32 steps at a
-// time with one ballot.  Fused risk terms are added per hit with global atomics; the per-step histogram
-// terms of one step's hits are summed over the warp first.
-template <int WARPS, bool FUSED>
-__global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const CollideArgs a) {
+// Warp-per-tile layouts: each warp owns one TE x TE block of hypothesis pairs (a whole 64 x 64 tile, or
+// one 32 x 32 quarter of it) and walks its active steps in ascending order on its own (no CTA barrier
+// anywhere).  A lane holds an MI x MJ micro-block (rows lr + 8 m, columns lc + 4 n, lr = lane / 4,
+// lc = lane % 4; 8 x 16 for TE = 64, 4 x 8 for TE = 32) and a register mask of its pairs that have
+// already hit: because the steps come in order, the first narrow-phase hit of a pair is its first
+// collision step, it is stored at once, and later candidates of that pair are dropped before any further
+// work.  The warp stages each step's poses in its own shared-memory slot; the next active step's poses
+// are loaded into registers while the current step is tested.  Activity (culling against the blocks'
+// bounding boxes) is decided 32 steps at a time with one ballot.  Fused risk terms are added per hit with
+// global atomics; the per-step histogram terms of one step's hits are summed over the warp first.
+template <int WARPS, int TE, bool FUSED>
+__global__ void __launch_bounds__(WARPS * 32, TE == 64 ? 4 : 6) collide_tile_kernel(const CollideArgs a) {
+    static_assert(TE == 64 || TE == 32, "block edge");
+    constexpr int MI = TE / 8, MJ = TE / 4;       // micro-block of a lane
+    constexpr int SUB = kTile / TE;               // blocks per tile edge
     constexpr int QCAP = 256;
-    __shared__ float4 s_pa[WARPS][kTile];                 // x, y, h_a
-    __shared__ float4 s_pb[WARPS][kTile];                 // x, y, h_b
-    __shared__ float2 s_ra[WARPS][kTile];                 // c, s
-    __shared__ float2 s_rb[WARPS][kTile];
+    __shared__ float4 s_pa[WARPS][TE];            // x, y, h_a
+    __shared__ float4 s_pb[WARPS][TE];            // x, y, h_b
+    __shared__ float2 s_ra[WARPS][TE];            // c, s
+    __shared__ float2 s_rb[WARPS][TE];
     __shared__ unsigned short s_queue[WARPS][QCAP];       // candidates: owner lane << 7 | bit
     __shared__ unsigned long long s_new[WARPS][32][2];     // pairs found in this step, in owner-lane layout
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long g = (long long)blockIdx.x * WARPS + warp;
+    const long long gw = (long long)blockIdx.x * WARPS + warp;
+    const long long g = gw / (SUB * SUB);                 // the 64 x 64 tile
     if (g >= a.n_tiles) return;                            // whole warps leave; no CTA barrier follows
+    const int quarter = (int)(gw - g * (SUB * SUB));
     int lo = 0, hi = a.n_pairs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -700,13 +706,15 @@ __global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const Colli
     const ObjDesc &B = a.objs[P.b];
     const long long t = g - P.tile_start;
     const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
-    const int i0 = ta * kTile, j0 = tb * kTile;
-    const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
+    const int ba_idx = ta * SUB + quarter / SUB, bb_idx = tb * SUB + quarter % SUB;   // blocks along a, b
+    const int i0 = ba_idx * TE, j0 = bb_idx * TE;
+    const int rows = min(TE, A.h - i0), cols = min(TE, B.h - j0);
+    if (rows <= 0 || cols <= 0) return;                    // a quarter past a ragged edge
     const int lr = lane >> 2, lc = lane & 3;
     const int N = P.n_steps;
     const int na = (rows + kBoundTile - 1) / kBoundTile, nb = (cols + kBoundTile - 1) / kBoundTile;
-    const float4 *bA0 = a.bounds + A.bounds_base + (long long)(ta * 2) * N;
-    const float4 *bB0 = a.bounds + B.bounds_base + (long long)(tb * 2) * N;
+    const float4 *bA0 = a.bounds + A.bounds_base + (long long)(i0 / kBoundTile) * N;
+    const float4 *bB0 = a.bounds + B.bounds_base + (long long)(j0 / kBoundTile) * N;
     const float la = A.hl, wa = A.hw, ra = A.rad, lb = B.hl, wb = B.hw, rb = B.rad;
     const float rc2 = P.rc2 + kEps0;
     const float ka = 0.5f * (1.0f - kEps);
@@ -750,13 +758,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const Colli
         }
         return k0 + __ffs(m) - 1;
     };
-    // this lane's share of a step's poses: rows lane, lane + 32 of A and columns lane, lane + 32 of B
-    float px[4], py[4], pc[4], ps[4];
+    // this lane's share of a step's poses: rows lane (+ 32) of A, then columns lane (+ 32) of B
+    constexpr int NU = 2 * (TE / 32);
+    float px[NU], py[NU], pc[NU], ps[NU];
     auto load_step = [&](int k) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int r = lane + 32 * (u & 1);
-            const bool isA = u < 2;
+        for (int u = 0; u < NU; ++u) {
+            const bool isA = u < NU / 2;
+            const int r = lane + 32 * (isA ? u : u - NU / 2);
             const bool ok = isA ? r < rows : r < cols;
             const long long idx = isA ? A.pose_base + (long long)k * A.h + i0 + r
                                       : B.pose_base + (long long)k * B.h + j0 + r;
@@ -767,7 +776,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const Colli
         }
     };
 
-    unsigned long long found_lo = 0ull, found_hi = 0ull;   // bit 16 m + n (m < 4), 16 (m - 4) + n
+    unsigned long long found_lo = 0ull, found_hi = 0ull;   // bit MJ m + n of the lane's pairs
     unsigned long long narrow = 0, hit_cnt = 0, hit_mass = 0;
     int active_steps = 0;
     int k = next_step(-1);
@@ -775,10 +784,11 @@ __global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const Colli
     while (k >= 0) {
         __syncwarp();                       // the previous step's slot is no longer read
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int r = lane + 32 * (u & 1);
+        for (int u = 0; u < NU; ++u) {
+            const bool isA = u < NU / 2;
+            const int r = lane + 32 * (isA ? u : u - NU / 2);
             const float q2 = fmaf(px[u], px[u], py[u] * py[u]);
-            if (u < 2) {
+            if (isA) {
                 pa_s[r] = make_float4(px[u], py[u], ka * q2, 0.0f);
                 ra_s[r] = make_float2(pc[u], ps[u]);
             } else {
@@ -790,22 +800,23 @@ __global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const Colli
         const int kn = next_step(k);
         if (kn >= 0) load_step(kn);         // in flight while this step is tested
         ++active_steps;
-        // broad phase: candidate bit of (m, n) = 16 m + n, rows 0-3 in c_lo, 4-7 in c_hi
-        float ax[8], ay[8], ah[8];
+        // broad phase: candidate bit MJ m + n (bits 0-63 in c_lo, 64-127 in c_hi)
+        float ax[MI], ay[MI], ah[MI];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
+        for (int m = 0; m < MI; ++m) {
             const float4 q = pa_s[lr + 8 * m];
             ax[m] = q.x; ay[m] = q.y; ah[m] = q.z;
         }
         unsigned long long c_lo = 0ull, c_hi = 0ull;
 #pragma unroll
-        for (int n = 0; n < 16; ++n) {
+        for (int n = 0; n < MJ; ++n) {
             const float4 qb = pb_s[lc + 4 * n];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
+            for (int m = 0; m < MI; ++m) {
                 if (fmaf(ax[m], qb.x, fmaf(ay[m], qb.y, -qb.z)) >= ah[m]) {
-                    if (m < 4) c_lo |= 1ull << (16 * m + n);
-                    else c_hi |= 1ull << (16 * (m - 4) + n);
+                    const int bit = MJ * m + n;
+                    if (bit < 64) c_lo |= 1ull << bit;
+                    else c_hi |= 1ull << (bit - 64);
                 }
             }
         }
@@ -837,7 +848,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const Colli
                 for (int e = lane; e < total; e += 32) {
                     const int ent = queue[e];
                     const int owner = ent >> 7, bit = ent & 127;
-                    const int m = bit >> 4, n = bit & 15;
+                    const int m = bit / MJ, n = bit % MJ;
                     const int i = (owner >> 2) + 8 * m, j = (owner & 3) + 4 * n;
                     const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                     const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
@@ -896,7 +907,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) collide_tile_kernel(const Colli
     }
     if (a.counters && lane == 0) {
         if (narrow) atomicAdd(a.counters + 1, narrow);
-        if (active_steps) atomicAdd(a.counters, (unsigned long long)active_steps * kTile * kTile);
+        if (active_steps) atomicAdd(a.counters, (unsigned long long)active_steps * TE * TE);
     }
     if (FUSED && lane == 0 && hit_cnt) {
         atomicAdd(a.acc.count + lo, hit_cnt);
@@ -959,10 +970,13 @@ cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int WARPS, bool FUSED>
+template <int WARPS, int TE, bool FUSED>
 cudaError_t launch_tile_variant(const CollideArgs &a, cudaStream_t st) {
-    const long long blocks = (a.n_tiles + WARPS - 1) / WARPS;
-    collide_tile_kernel<WARPS, FUSED><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
+    constexpr int SUB = kTile / TE;
+    const long long warps = a.n_tiles * SUB * SUB;
+    const long long blocks = (warps + WARPS - 1) / WARPS;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    collide_tile_kernel<WARPS, TE, FUSED><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -970,7 +984,9 @@ cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a.variant == 4)
-        return a.probf ? launch_tile_variant<4, true>(a, st) : launch_tile_variant<4, false>(a, st);
+        return a.probf ? launch_tile_variant<4, 64, true>(a, st) : launch_tile_variant<4, 64, false>(a, st);
+    if (a.variant == 5)
+        return a.probf ? launch_tile_variant<4, 32, true>(a, st) : launch_tile_variant<4, 32, false>(a, st);
     // variant 1: 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests); variant 2: 8 x 8 with
     // 64 threads; variant 3: one warp per step (8 x 16 lanes).  The caller picks one (autotuned per size).
     const bool many = a.variant == 2;

@@ -21,7 +21,7 @@ constexpr float kVMin = 2.0f;      // below this speed the one-track model gives
 constexpr double kVMinD = 2.0;
 
 constexpr int kTile = 64;           // collision tile edge (hypotheses per side)
-constexpr int kCollideVariants = 4; // thread layouts of the collision kernel (MHC_OPT_COLLIDE_VARIANT 1..4)
+constexpr int kCollideVariants = 5; // thread layouts of the collision kernel (MHC_OPT_COLLIDE_VARIANT 1..5)
 constexpr int kBoundTile = 32;     // hypotheses per bounding-box tile (one warp)
 constexpr int16_t kNoHit = 0x7fff; // in-kernel sentinel, stored as -1
 
@@ -127,7 +127,7 @@ struct CollideArgs {
     long long n_tiles;        // total collision tiles over all pairs
     int max_steps;            // the longest horizon of the batch (sizes the per-CTA accumulators)
     int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
-    int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile
+    int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile, 5: warp per quarter tile
     const float *x, *y, *c, *s;
     const float4 *bounds;
     int16_t *table;

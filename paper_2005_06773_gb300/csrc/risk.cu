@@ -181,23 +181,43 @@ __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
     }
 }
 
-// Writes the totals of the assessment into the caller's outputs (fixed point -> double).
-__device__ void convert_totals(const RiskArgs &a, int t, int nt) {
-    for (long long q = t; q < a.n_kofs; q += nt) {
-        if (a.count_k) a.count_k[q] = (long long)a.acc.count_k[q];
-        if (a.H) a.H[q] = from_fixed(a.acc.H[q], kFixProb);
+// The caller's outputs from the accumulators (fixed point -> double), in two parts: the pair totals
+// (count, P, count_k, H), final once the collision / scan launch has finished, and the totals the EGO walk
+// itself accumulates (attr_obj, attr_step, scalars, n_escape).  Threads t of nt; each pass loads four
+// elements before storing any, so the loads overlap.
+__device__ void convert_pair_totals(const RiskArgs &a, long long t, long long nt) {
+    const long long n = a.n_kofs + a.n_pairs;
+    for (long long q0 = t; q0 < n; q0 += 4 * nt) {
+        unsigned long long c[4], h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long q = q0 + u * nt;
+            c[u] = h[u] = 0ull;
+            if (q < a.n_kofs) { c[u] = a.acc.count_k[q]; h[u] = a.acc.H[q]; }
+            else if (q < n) { c[u] = a.acc.count[q - a.n_kofs]; h[u] = a.acc.P[q - a.n_kofs]; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long q = q0 + u * nt;
+            if (q < a.n_kofs) {
+                if (a.count_k) a.count_k[q] = (long long)c[u];
+                if (a.H) a.H[q] = from_fixed(h[u], kFixProb);
+            } else if (q < n) {
+                if (a.count) a.count[q - a.n_kofs] = (long long)c[u];
+                if (a.P) a.P[q - a.n_kofs] = from_fixed(h[u], kFixProb);
+            }
+        }
     }
-    for (int q = t; q < a.n_pairs; q += nt) {
-        if (a.count) a.count[q] = (long long)a.acc.count[q];
-        if (a.P) a.P[q] = from_fixed(a.acc.P[q], kFixProb);
-    }
-    for (int q = t; q < a.n_obj; q += nt)
+}
+
+__device__ void convert_walk_totals(const RiskArgs &a, long long t, long long nt) {
+    for (long long q = t; q < a.n_obj; q += nt)
         if (a.attr_obj) a.attr_obj[q] = from_fixed(a.acc.attr_obj[q], kFixProb);
     for (long long q = t; q < a.n_steps_total; q += nt)
         if (a.attr_step) a.attr_step[q] = from_fixed(a.acc.attr_step[q], kFixProb);
-    for (int q = t; q < 4 * a.n_scen; q += nt)
+    for (long long q = t; q < 4LL * a.n_scen; q += nt)
         if (a.scalars) a.scalars[q] = (q & 3) < 3 ? a.acc.scalars[q] : 0.0;
-    for (int q = t; q < a.n_scen; q += nt)
+    for (long long q = t; q < a.n_scen; q += nt)
         if (a.n_escape) a.n_escape[q] = (int)a.acc.n_escape[q];
 }
 
@@ -209,10 +229,12 @@ __device__ void convert_totals(const RiskArgs &a, int t, int nt) {
 //    128 per group with the four loads in flight together; a chunk with a non-empty cell gets an exclusive
 //    warp prefix product of the survival factors (1 - q), so each cell knows the survival S of every
 //    earlier cell and contributes S q.
-// The last CTA to finish converts the totals.
+// Every CTA first converts a slice of the pair totals; the last CTA to finish converts the walk's own
+// totals (or a separate grid-wide kernel does, for large batches).
 __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31;
+    convert_pair_totals(a, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (g < a.h_e) {
         int lo = 0, hi = a.n_scen - 1;     // the scenario of EGO hypothesis g
@@ -313,21 +335,24 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
     __syncthreads();
     if (s_last) {
         __threadfence();
-        convert_totals(a, threadIdx.x, blockDim.x);
+        convert_walk_totals(a, threadIdx.x, blockDim.x);
     }
 }
 
-// The totals of a large batch, grid-wide after the walk (or without EGO hypotheses to walk).
+// The walk's totals of a large batch, grid-wide after the walk (and the pair totals too when there is no
+// EGO hypothesis to walk, which a valid scenario never has).
 __global__ void __launch_bounds__(256) totals_kernel(const RiskArgs a) {
-    convert_totals(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    if (a.h_e == 0) convert_pair_totals(a, t, nt);
+    convert_walk_totals(a, t, nt);
 }
 
-// Elements the totals conversion writes; up to this many the walk's last CTA converts them (one launch
-// less), beyond it a grid-wide kernel does.
-constexpr long long kConvertInWalk = 32768;
+// Up to this many walk totals the walk's last CTA (64 threads) converts them, saving a launch; beyond it a
+// grid-wide kernel does.
+constexpr long long kConvertInWalk = 512;
 
 long long convert_elements(const RiskArgs &a) {
-    return 2 * a.n_kofs + 2LL * a.n_pairs + a.n_obj + a.n_steps_total + 5LL * a.n_scen;
+    return a.n_obj + a.n_steps_total + 5LL * a.n_scen + (a.h_e == 0 ? 2 * (a.n_kofs + a.n_pairs) : 0);
 }
 
 }  // namespace
