@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the stress32 / paper_s2 measurements")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the stress32 / paper_s2 / batch / serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="window of the serving measurement")
     ap.add_argument("--collide-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="collision kernel layout; 0 = chosen by mhc_autotune in the set-up (profiling fixes one)")
     ap.add_argument("--workload", default="intersection11", choices=sorted(WORKLOADS),
@@ -348,6 +350,118 @@ def measure_batch(mhc, torch, dev, steps, flush, count=256):
     }
 
 
+def arrivals(rate: float, seconds: float, large_share: float, seed: int = 5):
+    """Poisson arrival times (s) and request kinds (0 = 11-object scene, 1 = 32-vehicle scene)."""
+    from paper_2005_06773_gb300 import scenarios as S
+    rng = S.SplitMix64(seed)
+    t, out = 0.0, []
+    while True:
+        t += -math.log(1.0 - rng.uniform(0.0, 1.0)) / rate
+        if t >= seconds:
+            return out
+        out.append((t, 1 if rng.uniform(0.0, 1.0) < large_share else 0))
+
+
+def measure_serving(mhc, torch, dev, seconds: float, rate: float = 2000.0, large_share: float = 0.05):
+    """Served requests (continuous batching, mhc_submit / mhc_poll) against the plain path (one synchronous
+    mhc_run per request in arrival order) at the same offered load: Poisson arrivals at `rate`, 95 % shaped
+    like the 11-object scene (64 placements, cycled) and 5 % like the 32-vehicle scene (4 placements).
+    Latency = arrival (submission) to the risk outputs on the host; the queue of the plain path counts."""
+    import threading
+    from paper_2005_06773_gb300 import scenarios as S
+    small = [mhc.as_c(S.intersection11(100 + q)) for q in range(64)]
+    large = [mhc.as_c(S.stress32(200 + q)) for q in range(4)]
+    plan = arrivals(rate, seconds, large_share)
+    reqs = [(t, kind, (large[q % 4] if kind else small[q % 64])) for q, (t, kind) in enumerate(plan)]
+    ctx = mhc.Context(dev.index or 0, 256 << 20)
+    # the collision layouts for both shapes, then the serving loop
+    for cs in (small[0], large[0]):
+        lay = mhc.layout(cs)
+        p = mhc.alloc_poses(cs.sc, dev)
+        tb = torch.empty(lay["n_entries"], dtype=torch.int16, device=dev)
+        mhc.generate(ctx, cs, p)
+        mhc.autotune(ctx, cs, p, tb)
+        del p, tb
+    torch.cuda.empty_cache()
+    srv = mhc.Server(ctx, 48 << 30)
+    for cs in small[:8] + large[:1]:                    # warm-up (stream, pinned buffers, module load)
+        t = srv.submit(cs)
+        if not srv.poll(t, None, timeout_us=120_000_000):
+            raise RuntimeError("warm-up request not finished after 120 s")
+        srv.release(t)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for q, (t, kind, cs) in enumerate(reqs):
+            d = t0 + t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[q] = srv.submit(cs)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = {0: [], 1: []}
+    first_sub, last_done = None, 0
+    batch_sizes = []
+    for q in range(len(reqs)):
+        while tickets[q] is None:
+            time.sleep(0.0001)
+        if not srv.poll(tickets[q], None, timeout_us=120_000_000):
+            raise RuntimeError(f"served request {q} not finished after 120 s")
+        ns, bs = srv.times(tickets[q])
+        srv.release(tickets[q])
+        lat[reqs[q][1]].append((ns[2] - ns[0]) / 1e6)
+        first_sub = ns[0] if first_sub is None else min(first_sub, ns[0])
+        last_done = max(last_done, ns[2])
+        batch_sizes.append(bs)
+    th.join()
+    stats = srv.stats()
+    srv.stop()
+    served_s = (last_done - first_sub) / 1e9
+
+    # plain path: one mhc_run per request, in arrival order, on one host thread
+    run_ctx = mhc.Context(dev.index or 0, max(mhc.layout(large[0])["run_bytes"], mhc.layout(small[0])["run_bytes"]) + (64 << 20))
+    for cs in (small[0], large[0]):
+        run_ctx_p = mhc.alloc_poses(cs.sc, dev)
+        run_ctx_t = torch.empty(mhc.layout(cs)["n_entries"], dtype=torch.int16, device=dev)
+        mhc.generate(run_ctx, cs, run_ctx_p)
+        mhc.autotune(run_ctx, cs, run_ctx_p, run_ctx_t)
+        del run_ctx_p, run_ctx_t
+    torch.cuda.empty_cache()
+    outs = {id(cs): mhc.alloc_risk(cs, device="cpu", pin=True) for cs in small + large}
+    for cs in small[:4] + large[:1]:
+        mhc.run(run_ctx, cs, out=outs[id(cs)])
+    plat = {0: [], 1: []}
+    t0 = time.perf_counter()
+    for t, kind, cs in reqs:
+        d = t0 + t - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        mhc.run(run_ctx, cs, out=outs[id(cs)])
+        plat[kind].append(1e3 * (time.perf_counter() - (t0 + t)))
+    plain_s = time.perf_counter() - t0 - reqs[0][0]
+    run_ctx.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+
+    def summary(v):
+        return {"n": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99), "max_ms": max(v) if v else None}
+
+    n = len(reqs)
+    return {
+        "offered": {"rate_per_s": rate, "seconds": seconds, "requests": n, "large_share": large_share,
+                    "small": "11-object intersection shape (1.70e8 tests), 64 placements",
+                    "large": "32-vehicle shape (1.04e11 tests, 4.2 GB table), 4 placements"},
+        "served": {"scenarios_per_s": n / served_s, "small": summary(lat[0]), "large": summary(lat[1]),
+                   "all": summary(lat[0] + lat[1]), "batches": stats["batches"],
+                   "mean_batch": statistics.mean(batch_sizes) if batch_sizes else None},
+        "plain": {"scenarios_per_s": n / plain_s, "small": summary(plat[0]), "large": summary(plat[1]),
+                  "all": summary(plat[0] + plat[1]),
+                  "path": "mhc_run per request in arrival order (host in, host out, synchronous)"},
+    }
+
+
 def run_mhc(args):
     import torch
     import torch.distributed as dist
@@ -481,6 +595,7 @@ def run_mhc(args):
                              workload="paper Table I S2 shape: EGO 2058 x 10 CO 42, 100 steps of 20 ms, EGO-only"),
         }
         line["batch"] = measure_batch(mhc, torch, dev, 10, flush)
+        line["serving"] = measure_serving(mhc, torch, dev, args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD == "intersection11":
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:

@@ -169,8 +169,8 @@ void mhc_destroy(mhc_ctx *ctx);
  *                 4: one warp per tile walking its steps in order (8 x 16 micro-tiles per lane, pairs that
  *                    already hit dropped from later steps, first hits stored at once);
  *                 5: as 4 with one warp per 32 x 32 quarter tile (4 x 8 micro-tiles, culling per quarter);
- *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 3 for at
- *                 least 32 tiles per SM and 1 below. */
+ *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 4 for at
+ *                 least 32 tiles per SM and 5 below. */
 #define MHC_OPT_COLLIDE_VARIANT 3
 int mhc_set_option(mhc_ctx *ctx, int option, long long value);
 
@@ -336,6 +336,79 @@ int mhc_plan_create(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, con
 int mhc_plan_update(mhc_plan *plan, const mhc_scenario *scens, int32_t n_scen);
 int mhc_plan_launch(mhc_plan *plan, void *stream);
 void mhc_plan_destroy(mhc_plan *plan);
+
+/*
+ * Serving (no counterpart in the paper beyond its real-time setting, Section I: a criticality answer per
+ * sensor frame).  Continuous batching of scenario requests on one context: mhc_submit copies a scenario
+ * and queues it; a scheduler thread of the library admits queued requests into batches while stream slots
+ * and pool memory are free, launches each batch (the mhc_evaluate_batch kernels) on its slot's stream and
+ * copies the batch's risk outputs to pinned host memory; requests that arrive while other batches run are
+ * admitted into the next batch on another slot, so their work overlaps on the device.  Requests up to
+ * `small_tests` nominal pose tests go to the small lane (high-priority streams), larger ones to the large
+ * lane, so small requests never wait behind a large batch.  A request's poses, table and risk outputs
+ * stay resident in the pool until mhc_release.
+ *
+ * The pool is a device buffer the caller owns (e.g. a torch tensor), at least 1 MiB; admission is by its
+ * free bytes (first fit).  One serving loop per context; while it runs, use the context for nothing else
+ * but the calls below and mhc_set_option / mhc_autotune before mhc_serve_start (the loop keeps a copy of
+ * the collision configuration).  mhc_submit / mhc_poll / mhc_release / mhc_request_* / mhc_serve_stats_read
+ * are thread-safe.
+ */
+typedef struct {
+    int32_t small_slots;         /* streams of the small lane, 1..8 (default 3) */
+    int32_t large_slots;         /* streams of the large lane, 1..8 (default 1) */
+    int32_t max_batch;           /* scenarios per batch, 1..4096 (default 64) */
+    int32_t max_queue;           /* queued requests beyond which mhc_submit returns MHC_E_BUSY (default 4096) */
+    int64_t small_tests;         /* nominal pose tests up to which a request is small (default 2^31) */
+    int64_t max_batch_tests;     /* nominal pose tests per batch of the small lane (default 2^34) */
+} mhc_serve_config;
+
+int mhc_serve_start(mhc_ctx *ctx, void *pool, size_t pool_bytes, const mhc_serve_config *cfg /* NULL: defaults */);
+
+/* Stops the scheduler after the batches in flight; queued requests are dropped (their tickets become
+   unknown).  Called by mhc_destroy if still running. */
+int mhc_serve_stop(mhc_ctx *ctx);
+
+/* Queues a scenario (host inputs copied; weights as for mhc_evaluate).  *ticket identifies the request.
+   Errors: MHC_E_INVALID (scenario / weights), MHC_E_NOMEM (the request alone is larger than the pool),
+   MHC_E_BUSY (max_queue requests waiting), MHC_E_NOTFOUND (no serving loop). */
+int mhc_submit(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_weights, uint64_t *ticket);
+
+/* Waits up to timeout_us (0: no wait, < 0: forever) for the request.  MHC_OK: done, and the host pointers
+   of `out` (may be NULL; the single-scenario sizes of mhc_layout, each pointer may be NULL) receive its
+   risk outputs; MHC_PENDING: not finished yet; MHC_E_NOTFOUND: unknown or released ticket; MHC_E_CUDA:
+   its batch failed. */
+int mhc_poll(mhc_ctx *ctx, uint64_t ticket, const mhc_risk *out, int32_t timeout_us);
+
+/* Frees the request's resident device memory (its batch's block once every request of it is released).
+   A request still queued is withdrawn; one in flight is released when its batch completes. */
+int mhc_release(mhc_ctx *ctx, uint64_t ticket);
+
+/* Device views of a finished request, valid until mhc_release: pose planes and first-collision table in
+   the single-scenario layout, and the device risk outputs (NULL arguments skipped). */
+int mhc_request_buffers(mhc_ctx *ctx, uint64_t ticket, mhc_poses *poses, int16_t **table, mhc_risk *dev_out);
+
+/* Host steady-clock times (ns) of a request: ns[0] submitted, ns[1] launched in a batch, ns[2] outputs on
+   the host (0 where not reached); *batch_size = scenarios in its batch. */
+int mhc_request_times(mhc_ctx *ctx, uint64_t ticket, int64_t ns[3], int32_t *batch_size);
+
+typedef struct {
+    int64_t submitted, completed, batches, queued, running;
+    size_t pool_free, pool_largest;
+} mhc_serve_stats;
+int mhc_serve_stats_read(mhc_ctx *ctx, mhc_serve_stats *stats);
+
+/* While paused (paused != 0) the scheduler admits nothing; batches in flight complete. */
+int mhc_serve_pause(mhc_ctx *ctx, int32_t paused);
+
+/* The pool's first-fit allocator on its own (host only, offsets into a buffer of `bytes`; 256-byte
+   blocks).  Errors: MHC_E_NOMEM (no free block fits), MHC_E_NOTFOUND (no block at that offset). */
+typedef struct mhc_pool mhc_pool;
+int mhc_pool_create(size_t bytes, mhc_pool **out);
+int mhc_pool_alloc(mhc_pool *pool, size_t bytes, size_t *offset);
+int mhc_pool_free(mhc_pool *pool, size_t offset);
+int mhc_pool_info(mhc_pool *pool, size_t *free_bytes, size_t *largest_free, int32_t *n_free_blocks);
+void mhc_pool_destroy(mhc_pool *pool);
 
 /*
  * Collision recognition without any allocation (no counterpart in the paper: it serves deployment).

@@ -371,7 +371,7 @@ int log2_floor(long long v) {
 }
 
 // Collision configuration for a scenario: the forced variant, else the tuned one of its size class, else
-// the default (warp-per-step layout for at least 32 tiles per SM, else 256 threads x 4 x 4).
+// the default (a warp per tile for at least 32 tiles per SM, else a warp per quarter tile).
 void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &variant, int &cull) {
     cull = ctx->cull;
     if (ctx->variant != 0) { variant = ctx->variant; return; }
@@ -382,7 +382,7 @@ void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &v
             cull = t.cull;
             return;
         }
-    variant = L.n_tiles >= 32LL * ctx->n_sm ? 3 : 1;
+    variant = L.n_tiles >= 32LL * ctx->n_sm ? 4 : 5;
 }
 
 // Device buffers for the risk outputs of one assessment, carved from the arena.
@@ -536,6 +536,7 @@ int mhc_create(mhc_ctx **out, int device, void *arena, size_t arena_bytes) {
 
 void mhc_destroy(mhc_ctx *c) {
     if (!c) return;
+    if (c->server) serve_shutdown(c);
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (int s = 0; s < kSlots; ++s) {

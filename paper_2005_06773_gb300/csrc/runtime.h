@@ -114,6 +114,7 @@ struct mhc_ctx {
     double prof_ms[MHC_K_COUNT] = {};
     long long prof_n[MHC_K_COUNT] = {};
     long long h2d = 0, d2h = 0;
+    void *server = nullptr;          // the serving loop (serve.cu), if started
 };
 
 namespace mhc {
@@ -161,6 +162,15 @@ int evaluate_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const floa
                   const mhc_poses *poses, int16_t *table, const mhc_risk *out, void *stream);
 int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_poses *poses, int16_t *table,
                   int fused, int32_t *best_variant, int32_t *best_cull, void *stream);
+
+// first-fit allocator of pool.cu
+bool pool_alloc(mhc_pool *p, size_t bytes, size_t *offset);
+bool pool_free(mhc_pool *p, size_t offset);
+size_t pool_largest(const mhc_pool *p);
+size_t pool_free_bytes(const mhc_pool *p);
+mhc_pool *pool_new(size_t bytes);
+void pool_delete(mhc_pool *p);
+void serve_shutdown(mhc_ctx *ctx);   // stops the serving loop of ctx (serve.cu)
 
 }  // namespace host
 }  // namespace mhc

@@ -63,6 +63,16 @@ class MhcBatchSlice(ctypes.Structure):
 
 MHC_PLAN_GRAPH = 1
 
+
+class MhcServeConfig(ctypes.Structure):
+    _fields_ = [("small_slots", c_int32), ("large_slots", c_int32), ("max_batch", c_int32), ("max_queue", c_int32),
+                ("small_tests", c_int64), ("max_batch_tests", c_int64)]
+
+
+class MhcServeStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("batches", c_int64), ("queued", c_int64),
+                ("running", c_int64), ("pool_free", c_size_t), ("pool_largest", c_size_t)]
+
 RISK_FIELDS = ("count", "count_k", "P", "H", "naive", "cond", "indep", "hits", "attr_obj", "attr_step",
                "scalars", "escape", "n_escape")
 
@@ -110,6 +120,21 @@ def _load():
     L.mhc_plan_launch.argtypes = [c_void_p, c_void_p]
     L.mhc_plan_destroy.argtypes = [c_void_p]
     L.mhc_plan_destroy.restype = None
+    L.mhc_serve_start.argtypes = [c_void_p, c_void_p, c_size_t, POINTER(MhcServeConfig)]
+    L.mhc_serve_stop.argtypes = [c_void_p]
+    L.mhc_submit.argtypes = [c_void_p, POINTER(MhcScenario), c_void_p, POINTER(c_uint64)]
+    L.mhc_poll.argtypes = [c_void_p, c_uint64, POINTER(MhcRisk), c_int32]
+    L.mhc_release.argtypes = [c_void_p, c_uint64]
+    L.mhc_request_buffers.argtypes = [c_void_p, c_uint64, POINTER(MhcPoses), POINTER(c_void_p), POINTER(MhcRisk)]
+    L.mhc_request_times.argtypes = [c_void_p, c_uint64, POINTER(c_int64), POINTER(c_int32)]
+    L.mhc_serve_stats_read.argtypes = [c_void_p, POINTER(MhcServeStats)]
+    L.mhc_serve_pause.argtypes = [c_void_p, c_int32]
+    L.mhc_pool_create.argtypes = [c_size_t, POINTER(c_void_p)]
+    L.mhc_pool_alloc.argtypes = [c_void_p, c_size_t, POINTER(c_size_t)]
+    L.mhc_pool_free.argtypes = [c_void_p, c_size_t]
+    L.mhc_pool_info.argtypes = [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_int32)]
+    L.mhc_pool_destroy.argtypes = [c_void_p]
+    L.mhc_pool_destroy.restype = None
     L.mhc_run.argtypes = [c_void_p, POINTER(MhcScenario), c_void_p, POINTER(MhcRisk), c_void_p]
     return L
 
@@ -533,6 +558,128 @@ class Plan:
     def close(self):
         if getattr(self, "h", None):
             lib.mhc_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------------------------------------
+# serving loop
+
+class Server:
+    """Continuous batching on a context (mhc_serve_start ... mhc_serve_stop) with a torch-owned device pool."""
+
+    def __init__(self, ctx: Context, pool_bytes: int, small_slots=3, large_slots=1, max_batch=64, max_queue=4096,
+                 small_tests=1 << 31, max_batch_tests=1 << 34):
+        self.ctx = ctx
+        self.pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=f"cuda:{ctx.device}")
+        base = self.pool.data_ptr()
+        off = (-base) % 256
+        self.cfg = MhcServeConfig(small_slots, large_slots, max_batch, max_queue, small_tests, max_batch_tests)
+        _check(lib.mhc_serve_start(ctx.h, base + off, int(pool_bytes), ctypes.byref(self.cfg)), "mhc_serve_start")
+        self.running = True
+        self._keep = {}
+
+    def submit(self, sc, weights=None) -> int:
+        cs = as_c(sc)
+        w = weights if isinstance(weights, CWeights) else CWeights(weights)
+        t = c_uint64()
+        _check(lib.mhc_submit(self.ctx.h, cs.ref, w.ptr, ctypes.byref(t)), "mhc_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, out=None, timeout_us: int = -1) -> bool:
+        """True when done (outputs copied into `out`, host tensors of the single-scenario shapes), False if
+        still pending after timeout_us."""
+        rs = _risk_struct(out) if out is not None else None
+        code = lib.mhc_poll(self.ctx.h, ticket, ctypes.byref(rs) if rs is not None else None, int(timeout_us))
+        if code == MHC_PENDING:
+            return False
+        _check(code, "mhc_poll")
+        return True
+
+    def release(self, ticket: int):
+        _check(lib.mhc_release(self.ctx.h, ticket), "mhc_release")
+
+    def times(self, ticket: int):
+        ns = (c_int64 * 3)()
+        bs = c_int32()
+        _check(lib.mhc_request_times(self.ctx.h, ticket, ns, ctypes.byref(bs)), "mhc_request_times")
+        return (int(ns[0]), int(ns[1]), int(ns[2])), int(bs.value)
+
+    def buffers(self, ticket: int):
+        """Raw device addresses of a finished request: ({x, y, c, s}, table, MhcRisk of device pointers)."""
+        ps = MhcPoses()
+        tb = c_void_p()
+        rs = MhcRisk()
+        _check(lib.mhc_request_buffers(self.ctx.h, ticket, ctypes.byref(ps), ctypes.byref(tb), ctypes.byref(rs)),
+               "mhc_request_buffers")
+        return {k: getattr(ps, k) for k in ("x", "y", "c", "s")}, tb.value, rs
+
+    def stats(self):
+        st = MhcServeStats()
+        _check(lib.mhc_serve_stats_read(self.ctx.h, ctypes.byref(st)), "mhc_serve_stats_read")
+        return {f: int(getattr(st, f)) for f, _ in MhcServeStats._fields_}
+
+    def pause(self, paused: bool = True):
+        _check(lib.mhc_serve_pause(self.ctx.h, int(paused)), "mhc_serve_pause")
+
+    def stop(self):
+        if self.running:
+            _check(lib.mhc_serve_stop(self.ctx.h), "mhc_serve_stop")
+            self.running = False
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+
+class _DevArray:
+    _TYPESTR = {torch.float32: "<f4", torch.float64: "<f8", torch.int16: "<i2", torch.int32: "<i4",
+                torch.int64: "<i8"}
+
+    def __init__(self, addr: int, n: int, dtype):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": self._TYPESTR[dtype],
+                                         "data": (int(addr), False), "version": 3, "strides": None}
+
+
+def device_view(addr: int, n: int, dtype) -> torch.Tensor:
+    """A torch tensor over n elements of library-owned device memory at addr (no copy; valid as long as
+    that memory is, e.g. until mhc_release of a served request)."""
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DevArray(addr, n, dtype), device="cuda")
+
+
+class Pool:
+    """The serving loop's first-fit allocator on its own (host offsets)."""
+
+    def __init__(self, nbytes: int):
+        h = c_void_p()
+        _check(lib.mhc_pool_create(int(nbytes), ctypes.byref(h)), "mhc_pool_create")
+        self.h = h
+
+    def alloc(self, nbytes: int) -> int:
+        off = c_size_t()
+        _check(lib.mhc_pool_alloc(self.h, int(nbytes), ctypes.byref(off)), "mhc_pool_alloc")
+        return int(off.value)
+
+    def free(self, offset: int):
+        _check(lib.mhc_pool_free(self.h, int(offset)), "mhc_pool_free")
+
+    def info(self):
+        f, l, n = c_size_t(), c_size_t(), c_int32()
+        _check(lib.mhc_pool_info(self.h, ctypes.byref(f), ctypes.byref(l), ctypes.byref(n)), "mhc_pool_info")
+        return int(f.value), int(l.value), int(n.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.mhc_pool_destroy(self.h)
             self.h = None
 
     def __del__(self):
