@@ -78,7 +78,7 @@ def workload(rank: int = 0):
         return S.stress32(4 + rank, n_cars=12)
     if WORKLOAD == "paper_s2":
         return S.paper_s1s2(10, 6, seed=6 + rank)
-    return S.intersection11(2 + rank)
+    return S.intersection11(replica_seed(rank))
 
 
 def config_of(sc, rank0_seed=2):
@@ -462,6 +462,25 @@ def measure_serving(mhc, torch, dev, seconds: float, rate: float = 2000.0, large
     }
 
 
+def aggregate(units: float, seconds: float, world: int, device):
+    """Whole-job throughput of a weak-scaling run: every rank's units (its own replica's pose tests) summed,
+    divided by the slowest rank's time.  Returns (units per second, total units, max seconds)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    t_max, total = float(t.item()), float(u.item())
+    return total / t_max, total, t_max
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank runs its own scene replica: the benchmark scene's placement seed plus the rank."""
+    return 2 + rank
+
+
 def run_mhc(args):
     import torch
     import torch.distributed as dist
@@ -526,12 +545,7 @@ def run_mhc(args):
     dev_s = sum(step_ms) / 1e3
     prof = ctx.profile_read(reset=True)
     executed, narrow = ctx.counters(reset=True)
-    t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    tests_all = sc.n_tests() * args.steps * world
-    value = tests_all / t_max
+    value, tests_all, t_max = aggregate(sc.n_tests() * args.steps, dev_s, world, dev)
 
     # end to end through mhc_run: host scenario in, host (pinned) risk out, copies inside the timed region
     host_out = mhc.alloc_risk(cs, device="cpu", pin=True)
@@ -547,10 +561,7 @@ def run_mhc(args):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     h2d, d2h = e2e_ctx.transfer_bytes()
     e2e_ctx.close()
-    te = torch.tensor([sum(e2e_ms) / 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = sc.n_tests() * args.e2e_steps * world / float(te.item())
+    e2e_value, _, _ = aggregate(sc.n_tests() * args.e2e_steps, sum(e2e_ms) / 1e3, world, dev)
 
     coll_ms, coll_n = prof["collide"]
     avg_coll_s = coll_ms / 1e3 / max(coll_n, 1)
