@@ -1,5 +1,6 @@
 // api.cu -- host runtime behind the C ABI of mhc.h: scenario validation and layout, the context arena,
 // descriptor upload through a ring of pinned staging buffers, and the launch sequence of each entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -141,6 +142,7 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
         p.hits_base = S.e_base;
         p.n_obj_s = n_obj_s;
         p.co_local = p.ego_side == 0 ? lb : (p.ego_side == 1 ? la : 0);
+        p.index = (int)L.pairs.size();
         L.n_entries += (long long)A.h * B.h;
         L.n_tiles += (long long)p.tiles_a * p.tiles_b;
         L.n_kofs += N;
@@ -168,6 +170,23 @@ int build_layout(const mhc_scenario *sc, int n_scen, Layout &L) {
     for (int s = 0; s < n_scen; ++s)
         if (int r = append_scenario(sc + s, s, n_scen > 1, L)) return r;
     L.entry0.push_back(L.n_entries);
+    // collision-grid order: pairs by the distance of their objects' initial positions, closest first (the
+    // pairs that stay close longest carry the most active steps and candidates; starting them first keeps
+    // them off the end of the launch)
+    std::vector<std::pair<float, int>> key(L.pairs.size());
+    for (size_t p = 0; p < L.pairs.size(); ++p) {
+        const ObjDesc &A = L.objs[L.pairs[p].a], &B = L.objs[L.pairs[p].b];
+        key[p] = {std::hypot(A.x0 - B.x0, A.y0 - B.y0) - A.circ - B.circ, (int)p};
+    }
+    std::stable_sort(key.begin(), key.end());
+    L.pairs_c.resize(L.pairs.size());
+    long long tiles = 0;
+    for (size_t q = 0; q < key.size(); ++q) {
+        PairDesc d = L.pairs[key[q].second];
+        d.tile_start = tiles;
+        tiles += (long long)d.tiles_a * d.tiles_b;
+        L.pairs_c[q] = d;
+    }
     return MHC_OK;
 }
 
@@ -197,7 +216,7 @@ long long acc_words(const Layout &L) {
 Scratch scratch_of(const Layout &L, bool with_weights) {
     Scratch s;
     const size_t gen_tasks = (size_t)L.n_traj / 4 + L.objs.size();   // the most generation tasks (4 lanes)
-    s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
+    s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + 2 * align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
              align_up(sizeof(ScenDesc) * L.scens.size()) + align_up(sizeof(float) * L.grids.size()) +
              2 * align_up(sizeof(int) * L.warp_obj.size()) + 2 * align_up(sizeof(int) * gen_tasks);
     s.bounds = align_up(sizeof(float4) * (size_t)L.n_bounds);
@@ -235,10 +254,11 @@ int end_call(mhc_ctx *ctx, cudaStream_t st) {
 }
 
 size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char *host, char *dev, DevDesc &out) {
-    constexpr int kParts = 8;
+    constexpr int kParts = 9;
     const std::pair<const void *, size_t> parts[kParts] = {
         {L.objs.data(), sizeof(ObjDesc) * L.objs.size()},
         {L.pairs.data(), sizeof(PairDesc) * L.pairs.size()},
+        {L.pairs_c.data(), sizeof(PairDesc) * L.pairs_c.size()},
         {L.scens.data(), sizeof(ScenDesc) * L.scens.size()},
         {L.grids.data(), sizeof(float) * L.grids.size()},
         {L.warp_obj.data(), sizeof(int) * L.warp_obj.size()},
@@ -249,6 +269,7 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
     size_t caps[kParts];
     for (int q = 0; q < kParts; ++q) caps[q] = align_up(parts[q].second);
     caps[1] = align_up(sizeof(PairDesc) * (L.pairs.size() + 1));
+    caps[2] = align_up(sizeof(PairDesc) * (L.pairs.size() + 1));
     size_t off = 0;
     char *ptrs[kParts + 1];
     for (int q = 0; q < kParts; ++q) {
@@ -263,12 +284,13 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
     }
     out.objs = reinterpret_cast<ObjDesc *>(ptrs[0]);
     out.pairs = reinterpret_cast<PairDesc *>(ptrs[1]);
-    out.scens = reinterpret_cast<ScenDesc *>(ptrs[2]);
-    out.grids = reinterpret_cast<float *>(ptrs[3]);
-    out.warp_obj = reinterpret_cast<int *>(ptrs[4]);
-    out.warp_first = reinterpret_cast<int *>(ptrs[5]);
-    out.gen_obj = reinterpret_cast<int *>(ptrs[6]);
-    out.gen_first = reinterpret_cast<int *>(ptrs[7]);
+    out.pairs_c = reinterpret_cast<PairDesc *>(ptrs[2]);
+    out.scens = reinterpret_cast<ScenDesc *>(ptrs[3]);
+    out.grids = reinterpret_cast<float *>(ptrs[4]);
+    out.warp_obj = reinterpret_cast<int *>(ptrs[5]);
+    out.warp_first = reinterpret_cast<int *>(ptrs[6]);
+    out.gen_obj = reinterpret_cast<int *>(ptrs[7]);
+    out.gen_first = reinterpret_cast<int *>(ptrs[8]);
     out.weights = weights ? reinterpret_cast<float *>(ptrs[kParts]) : nullptr;
     return off;
 }
@@ -442,9 +464,12 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         pick_collide_config(ctx, L, fused, variant, cull);
         float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_bounds));
         if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
+        // small tables: the quarter-tile layout writes the -1s of its own blocks (one launch less); large ones
+        // are filled by the HBM-rate fill kernel (in-kernel 2-byte row stores cost issue slots there)
+        const bool fill_in_collide = variant == 5 && L.n_entries <= kFillInCollideMax;
         {
-            TimedScope ts(ctx, st, MHC_K_BOUNDS, cull ? 2 : 1);
-            cudaError_t e = launch_fill_table(table, L.n_entries, st);
+            TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_in_collide ? 0 : 1));
+            cudaError_t e = fill_in_collide ? cudaSuccess : launch_fill_table(table, L.n_entries, st);
             if (e != cudaSuccess) return cuda_fail(e, "table fill launch");
             if (cull) {
                 BoundsArgs b;
@@ -456,8 +481,8 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
             }
         }
         CollideArgs c{};
-        c.objs = D.objs; c.pairs = D.pairs; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
-        c.max_steps = L.max_steps; c.cull = cull; c.variant = variant;
+        c.objs = D.objs; c.pairs = D.pairs_c; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
+        c.max_steps = L.max_steps; c.cull = cull; c.variant = variant; c.fill_blocks = fill_in_collide;
         c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
         c.bounds = bounds; c.table = table; c.counters = ctx->counters;
         if (fused) {

@@ -318,8 +318,8 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
             hit_mass += __shfl_xor_sync(0xffffffffu, hit_mass, d);
         }
         if ((tid & 31) == 0 && hit_cnt) {
-            atomicAdd(a.acc.count + lo, hit_cnt);
-            atomicAdd(a.acc.P + lo, hit_mass);
+            atomicAdd(a.acc.count + P.index, hit_cnt);
+            atomicAdd(a.acc.P + P.index, hit_mass);
         }
         if (smem_hist) {
             for (int q = tid; q < N; q += THREADS) {
@@ -635,8 +635,8 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
             hit_mass += __shfl_xor_sync(0xffffffffu, hit_mass, d);
         }
         if (lane == 0 && hit_cnt) {
-            atomicAdd(a.acc.count + lo, hit_cnt);
-            atomicAdd(a.acc.P + lo, hit_mass);
+            atomicAdd(a.acc.count + P.index, hit_cnt);
+            atomicAdd(a.acc.P + P.index, hit_mass);
         }
         __syncthreads();
         if (R.hist) {
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
 // bounding boxes) is decided 32 steps at a time with one ballot.  Fused risk terms are added per hit with
 // global atomics; the per-step histogram terms of one step's hits are summed over the warp first.
 template <int WARPS, int TE, bool FUSED>
-__global__ void __launch_bounds__(WARPS * 32, TE == 64 ? 4 : 6) collide_tile_kernel(const CollideArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) collide_tile_kernel(const CollideArgs a) {
     static_assert(TE == 64 || TE == 32, "block edge");
     constexpr int MI = TE / 8, MJ = TE / 4;       // micro-block of a lane
     constexpr int SUB = kTile / TE;               // blocks per tile edge
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(WARPS * 32, TE == 64 ? 4 : 6) collide_tile_ker
         const int mid = (lo + hi + 1) >> 1;
         if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
     }
-    const PairDesc P = a.pairs[lo];
+    const PairDesc &P = a.pairs[lo];   // fields read where used (fewer live registers)
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
     const long long t = g - P.tile_start;
@@ -724,6 +724,12 @@ __global__ void __launch_bounds__(WARPS * 32, TE == 64 ? 4 : 6) collide_tile_ker
     unsigned short *queue = s_queue[warp];
     unsigned long long *newf = s_new[warp][lane];
     newf[0] = newf[1] = 0ull;
+    if (TE == 32 && a.fill_blocks) {   // this block's table entries start as -1 (coalesced 64-byte row stores)
+        int16_t *row = a.table + P.off + (long long)i0 * B.h + j0;
+        for (int r = 0; r < rows; ++r, row += B.h)
+            for (int c = lane; c < cols; c += 32) row[c] = (int16_t)-1;
+        __syncwarp();      // the fill is ordered before this warp's first-hit stores
+    }
 
     // activity of the 32 steps from k0 (one ballot)
     auto chunk_mask = [&](int k0) -> unsigned {
@@ -910,8 +916,8 @@ __global__ void __launch_bounds__(WARPS * 32, TE == 64 ? 4 : 6) collide_tile_ker
         if (active_steps) atomicAdd(a.counters, (unsigned long long)active_steps * TE * TE);
     }
     if (FUSED && lane == 0 && hit_cnt) {
-        atomicAdd(a.acc.count + lo, hit_cnt);
-        atomicAdd(a.acc.P + lo, hit_mass);
+        atomicAdd(a.acc.count + P.index, hit_cnt);
+        atomicAdd(a.acc.P + P.index, hit_mass);
     }
 }
 
@@ -985,8 +991,8 @@ cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a.variant == 4)
         return a.probf ? launch_tile_variant<4, 64, true>(a, st) : launch_tile_variant<4, 64, false>(a, st);
-    if (a.variant == 5)
-        return a.probf ? launch_tile_variant<4, 32, true>(a, st) : launch_tile_variant<4, 32, false>(a, st);
+    if (a.variant == 5)   // one warp per CTA: a finished warp frees its slot at once (small, uneven grids)
+        return a.probf ? launch_tile_variant<1, 32, true>(a, st) : launch_tile_variant<1, 32, false>(a, st);
     // variant 1: 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests); variant 2: 8 x 8 with
     // 64 threads; variant 3: one warp per step (8 x 16 lanes).  The caller picks one (autotuned per size).
     const bool many = a.variant == 2;

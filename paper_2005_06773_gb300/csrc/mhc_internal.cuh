@@ -66,6 +66,8 @@ struct PairDesc {
     long long hits_base;      // [EGO hypothesis]
     int n_obj_s;              // objects in the scenario
     int co_local;             // the CO object's index in its scenario
+    int index;                // the pair's position in table order (per-pair outputs count, P)
+    int pad_;
 };
 
 // Per-scenario descriptor of a batch (device; risk stage).
@@ -122,11 +124,12 @@ struct RiskScratch {
 
 struct CollideArgs {
     const ObjDesc *objs;
-    const PairDesc *pairs;
+    const PairDesc *pairs;    // in collision-grid order (tile_start over that order; index = table order)
     int n_pairs;
     long long n_tiles;        // total collision tiles over all pairs
     int max_steps;            // the longest horizon of the batch (sizes the per-CTA accumulators)
     int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
+    int fill_blocks;          // 1: each warp writes -1 to its own block first (variant 5; no fill launch)
     int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile, 5: warp per quarter tile
     const float *x, *y, *c, *s;
     const float4 *bounds;

@@ -254,14 +254,21 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
             if (a.escape) {
                 const long long key = __double_as_longlong(pe);
                 int rank = 0;
-                for (int q0 = 0; q0 < sd.h_e; q0 += 32) {
-                    const int q = q0 + lane;
-                    bool above = false;
-                    if (q < sd.h_e && a.acc.hits[sd.e_base + q] == 0ull) {
-                        const long long kq = __double_as_longlong(a.prob[E.traj_off + q]);
-                        above = kq > key || (kq == key && q < i);
+                for (int q0 = 0; q0 < sd.h_e; q0 += 128) {   // 4 x 32 entries, every load issued first
+                    unsigned long long hq[4];
+                    long long kq[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + 32 * u + lane;
+                        hq[u] = q < sd.h_e ? a.acc.hits[sd.e_base + q] : 1ull;
+                        kq[u] = q < sd.h_e ? __double_as_longlong(a.prob[E.traj_off + q]) : 0ll;
                     }
-                    rank += __popc(__ballot_sync(0xffffffffu, above));
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + 32 * u + lane;
+                        const bool above = hq[u] == 0ull && (kq[u] > key || (kq[u] == key && q < i));
+                        rank += __popc(__ballot_sync(0xffffffffu, above));
+                    }
                 }
                 if (lane == 0) a.escape[sd.e_base + rank] = (int)i;
             }

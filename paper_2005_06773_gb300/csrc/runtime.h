@@ -23,6 +23,7 @@ int cuda_fail(cudaError_t e, const char *what);
 constexpr size_t kAlign = 256;
 constexpr size_t kReserved = 4096;    // persistent words at the start of the arena (counters)
 constexpr int kSlots = 4;
+constexpr long long kFillInCollideMax = 1LL << 25;   // table entries up to which the collision kernel fills
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 inline bool finite(float v) { return std::isfinite(v); }
@@ -34,6 +35,7 @@ struct Layout {
     int n_obj = 0, n_scen = 0, max_steps = 0;
     std::vector<ObjDesc> objs;
     std::vector<PairDesc> pairs;
+    std::vector<PairDesc> pairs_c;                   // the same in collision-grid order (closest pairs first)
     std::vector<ScenDesc> scens;
     std::vector<float> grids;
     std::vector<int> warp_obj, warp_first;          // 32-hypothesis bound tiles
@@ -76,6 +78,7 @@ struct Bump {
 struct DevDesc {
     ObjDesc *objs;
     PairDesc *pairs;
+    PairDesc *pairs_c;
     ScenDesc *scens;
     float *grids;
     int *warp_obj, *warp_first;

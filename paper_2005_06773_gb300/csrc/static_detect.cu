@@ -156,6 +156,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
             p.combo = (A.kind == MHC_VEHICLE ? 0 : 2) + (B.kind == MHC_VEHICLE ? 0 : 1);
             p.ego_side = a == sc->ego ? 0 : (b == sc->ego ? 1 : -1);
             p.n_steps = N;
+            p.index = n_pairs - 1;
             entries += (long long)A.h * B.h;
             tiles += (long long)p.tiles_a * p.tiles_b;
         }
