@@ -172,6 +172,12 @@ void mhc_destroy(mhc_ctx *ctx);
  *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 4 for at
  *                 least 32 tiles per SM and 5 below. */
 #define MHC_OPT_COLLIDE_VARIANT 3
+/*   MHC_OPT_GEN_SCAN  trajectory generation: 1 one warp per hypothesis, its sub-steps in parallel (warp
+ *                 scans of the state maps and of the heading / position increments); 0 one thread per
+ *                 hypothesis, sub-steps in order; 2 (default) the first up to 16,384 hypotheses per call,
+ *                 the second beyond.  Both follow Eqs. onetrack, EulerVelocity and pedestrianmotion; they
+ *                 differ in FP32 rounding only. */
+#define MHC_OPT_GEN_SCAN 4
 int mhc_set_option(mhc_ctx *ctx, int option, long long value);
 
 /* Work counters of the collision kernel since the last reset, summed over calls on this context:

@@ -194,15 +194,33 @@ int build_layout(const mhc_scenario *sc, Layout &L) { return build_layout(sc, 1,
 
 // Generation warp tasks: a hypothesis is a sequential chain of sub-steps, so with fewer hypotheses than
 // warp schedulers (4 per SM) each warp takes fewer of them (down to 4) to occupy every scheduler.
-void plan_generation(Layout &L, int n_sm) {
-    const long long schedulers = 4LL * (n_sm > 0 ? n_sm : 152);
-    int lanes = 32;
-    while (lanes > 4 && (L.n_traj + lanes - 1) / lanes < schedulers) lanes >>= 1;
-    L.gen_lanes = lanes;
+void plan_generation(Layout &L, int n_sm, int mode) {
     L.gen_obj.clear();
     L.gen_first.clear();
+    // one warp per hypothesis (parallel in time) for the objects of scenarios with few hypotheses, so that
+    // a scenario gets the same poses alone and in any batch
+    std::vector<char> scan(L.n_obj, 0);
+    for (const ScenDesc &S : L.scens) {
+        long long traj = 0;
+        for (int o = S.obj0; o < S.obj0 + S.n_obj; ++o) traj += L.objs[o].h;
+        const bool sc = mode == 1 || (mode == 2 && traj <= kGenScanMaxTraj);
+        for (int o = S.obj0; o < S.obj0 + S.n_obj; ++o) scan[o] = sc;
+    }
+    long long seq_traj = 0;
+    for (int o = 0; o < L.n_obj; ++o) {
+        if (!scan[o]) { seq_traj += L.objs[o].h; continue; }
+        for (int q = 0; q < L.objs[o].h; ++q) { L.gen_obj.push_back(o); L.gen_first.push_back(q); }
+    }
+    L.n_gen_scan = (int)L.gen_obj.size();
+    // the others: one thread per hypothesis, `lanes` per warp; with fewer hypotheses than warp schedulers
+    // (4 per SM) each warp takes fewer of them (down to 4) to occupy every scheduler
+    const long long schedulers = 4LL * (n_sm > 0 ? n_sm : 152);
+    int lanes = 32;
+    while (lanes > 4 && (seq_traj + lanes - 1) / lanes < schedulers) lanes >>= 1;
+    L.gen_lanes = lanes;
     for (int o = 0; o < L.n_obj; ++o)
-        for (int q = 0; q < L.objs[o].h; q += lanes) { L.gen_obj.push_back(o); L.gen_first.push_back(q); }
+        if (!scan[o])
+            for (int q = 0; q < L.objs[o].h; q += lanes) { L.gen_obj.push_back(o); L.gen_first.push_back(q); }
 }
 
 // Device scratch each call needs (besides caller buffers).
@@ -215,7 +233,7 @@ long long acc_words(const Layout &L) {
 
 Scratch scratch_of(const Layout &L, bool with_weights) {
     Scratch s;
-    const size_t gen_tasks = (size_t)L.n_traj / 4 + L.objs.size();   // the most generation tasks (4 lanes)
+    const size_t gen_tasks = (size_t)L.n_traj + L.objs.size();   // the most generation tasks (a warp each)
     s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + 2 * align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
              align_up(sizeof(ScenDesc) * L.scens.size()) + align_up(sizeof(float) * L.grids.size()) +
              2 * align_up(sizeof(int) * L.warp_obj.size()) + 2 * align_up(sizeof(int) * gen_tasks);
@@ -454,6 +472,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         GenArgs g;
         g.objs = D.objs; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
         g.n_warps = (int)L.gen_obj.size(); g.lanes = L.gen_lanes;
+        g.n_scan = L.n_gen_scan;
         g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
         cudaError_t e = launch_generate(g, st);
@@ -579,6 +598,11 @@ int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
     if (int r = check_ctx(ctx)) return r;
     if (option == MHC_OPT_CULL) { ctx->cull = value != 0; return MHC_OK; }
     if (option == MHC_OPT_PROFILE) { ctx->profile = value != 0; return MHC_OK; }
+    if (option == MHC_OPT_GEN_SCAN) {
+        if (value < 0 || value > 2) return fail(MHC_E_INVALID, "generation layout must be 0, 1 or 2");
+        ctx->gen_scan = (int)value;
+        return MHC_OK;
+    }
     if (option == MHC_OPT_COLLIDE_VARIANT) {
         if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 5");
         ctx->variant = (int)value;
@@ -658,7 +682,7 @@ int mhc_generate_trajectories(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_
     if (!out || !out->x || !out->y || !out->c || !out->s) return fail(MHC_E_INVALID, "pose planes must be non-NULL");
     Layout L;
     if (int r = build_layout(scen, L)) return r;
-    plan_generation(L, ctx->n_sm);
+    plan_generation(L, ctx->n_sm, ctx->gen_scan);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Scratch S = scratch_of(L, false);
     Bump bump{ctx->arena, ctx->arena_bytes, kReserved};
@@ -732,7 +756,7 @@ int evaluate_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const floa
         return fail(MHC_E_INVALID, "poses, table and out must be non-NULL");
     Layout L;
     if (int r = build_layout(scen, n_scen, L)) return r;
-    plan_generation(L, ctx->n_sm);
+    plan_generation(L, ctx->n_sm, ctx->gen_scan);
     std::vector<float> w;
     if (int r = gather_weights(L, traj_weights, w)) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -754,7 +778,7 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
         return fail(MHC_E_INVALID, "poses and table must be non-NULL");
     Layout L;
     if (int r = build_layout(scen, n_scen, L)) return r;
-    plan_generation(L, ctx->n_sm);
+    plan_generation(L, ctx->n_sm, ctx->gen_scan);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int saved_variant = ctx->variant, saved_cull = ctx->cull;
     const bool saved_profile = ctx->profile;
@@ -837,7 +861,7 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     if (!out) return fail(MHC_E_INVALID, "out is NULL");
     Layout L;
     if (int r = build_layout(scen, L)) return r;
-    plan_generation(L, ctx->n_sm);
+    plan_generation(L, ctx->n_sm, ctx->gen_scan);
     std::vector<float> w;
     if (int r = gather_weights(L, traj_weights, w)) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -146,7 +146,7 @@ int mhc_plan_create(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, con
     int rc = build_layout(scens, n_scen, p->L);
     if (rc == MHC_OK) rc = gather_weights(p->L, traj_weights, p->w);
     if (rc != MHC_OK) { delete p; return rc; }
-    plan_generation(p->L, ctx->n_sm);
+    plan_generation(p->L, ctx->n_sm, ctx->gen_scan);
     p->has_w = !p->w.empty();
     const Scratch S = scratch_of(p->L, p->has_w);
     if (scratch_bytes < S.total) {
@@ -203,7 +203,7 @@ int mhc_plan_update(mhc_plan *p, const mhc_scenario *scens, int32_t n_scen) {
     Layout L;
     if (int r = build_layout(scens, n_scen, L)) return r;
     if (!same_structure(L, p->L)) return fail(MHC_E_INVALID, "scenarios differ from the plan's in structure");
-    plan_generation(L, p->ctx->n_sm);
+    plan_generation(L, p->ctx->n_sm, p->ctx->gen_scan);
     MHC_CUDA(cudaSetDevice(p->ctx->device));
     if (p->launched) MHC_CUDA(cudaEventSynchronize(p->done));   // the previous launch has read the copy
     p->L = std::move(L);

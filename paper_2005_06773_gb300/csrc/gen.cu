@@ -1,4 +1,5 @@
-// gen.cu -- trajectory generation (Section IV-B): one thread per hypothesis, sub-steps in order.
+// gen.cu -- trajectory generation (Section IV-B): a warp per hypothesis with its sub-steps in parallel
+// (scenarios with few hypotheses), or a thread per hypothesis with its sub-steps in order.
 //
 // Vehicles: one-track model (Eq. onetrack) with constant steering and acceleration, integrated by
 // Eq. (EulerVelocity) with sub-step tau / K; the low-speed kinematic limit and the stop rule are applied
@@ -165,8 +166,9 @@ __device__ void vehicle(const ObjDesc &o, float acc, float delta, int model, int
     }
 }
 
+// output steps k0, k0 + dk, ... of one pedestrian hypothesis (closed form)
 __device__ void pedestrian(const ObjDesc &o, float ga, float gb, int N, float tau, long long base, int h, int i,
-                           float *X, float *Y, float *C, float *S) {
+                           float *X, float *Y, float *C, float *S, int k0 = 0, int dk = 1) {
     const bool accel = (o.flags & kPedAccelGrid) != 0;
     const float v0 = accel ? o.v0 : ga;
     const float a = accel ? ga : 0.0f;
@@ -181,7 +183,7 @@ __device__ void pedestrian(const ObjDesc &o, float ga, float gb, int N, float ta
     } else if (a < 0.0f) {
         ts = v0 / -a; s_sat = v0 * v0 / (-2.0f * a); v_sat = 0.0f;
     }
-    for (int k = 0; k < N; ++k) {
+    for (int k = k0; k < N; k += dk) {
         const float t = (float)(k + 1) * tau;
         const float s = t < ts ? fmaf(0.5f * a * t, t, v0 * t) : fmaf(v_sat, t - ts, s_sat);
         const long long idx = base + (long long)k * h + i;
@@ -192,9 +194,301 @@ __device__ void pedestrian(const ObjDesc &o, float ga, float gb, int N, float ta
     }
 }
 
+// ---- parallel-in-time generation: one warp per hypothesis ----------------------------------------------
+//
+// Every sub-step maps the lateral state s = (beta, r) affinely: s' = M_n s + c_n, with M_n, c_n functions of
+// the speed v_n alone (one-track model: M = I + tau_i A(v_n), c = tau_i b(v_n); kinematic limit: M = 0,
+// c = (beta_kin, v_n kappa); stopped: M = I, c = 0).  The warp's lanes take 8 consecutive sub-steps each,
+// compose their maps, and one warp scan of the compositions gives every lane its start state; each lane
+// then runs its sub-steps in order.  Heading and position are sums of per-sub-step increments, so they
+// are prefix sums (double-float: an FP32 (hi, lo) pair per value, exact two-sum additions) over the lanes.
+
+// (hi, lo) + (bh, bl), renormalised
+__device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    e = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// inclusive warp scan of double-float values (lane order = time order)
+__device__ __forceinline__ void df_scan(float &hi, float &lo, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float h2 = __shfl_up_sync(0xffffffffu, hi, d), l2 = __shfl_up_sync(0xffffffffu, lo, d);
+        if (lane >= d) {
+            float th = h2, tl = l2;
+            df_add(th, tl, hi, lo);
+            hi = th;
+            lo = tl;
+        }
+    }
+}
+
+// Affine map of the lateral state: s' = [m00 m01; m10 m11] s + (c0, c1).
+struct Aff {
+    float m00, m01, m10, m11, c0, c1;
+};
+
+// second after first: the map that applies `first`, then `second`
+__device__ __forceinline__ Aff aff_then(const Aff &first, const Aff &second) {
+    Aff r;
+    r.m00 = fmaf(second.m00, first.m00, second.m01 * first.m10);
+    r.m01 = fmaf(second.m00, first.m01, second.m01 * first.m11);
+    r.m10 = fmaf(second.m10, first.m00, second.m11 * first.m10);
+    r.m11 = fmaf(second.m10, first.m01, second.m11 * first.m11);
+    r.c0 = fmaf(second.m00, first.c0, fmaf(second.m01, first.c1, second.c0));
+    r.c1 = fmaf(second.m10, first.c0, fmaf(second.m11, first.c1, second.c1));
+    return r;
+}
+
+// Sub-steps of the low-speed regime [low_lo, low_hi) and the stop sub-step, decided exactly as the
+// sequential integration decides them (FP64 speed v_0 + n vdot tau_i).
+struct Regime {
+    int low_lo, low_hi, n_stop;
+};
+
+__device__ Regime regime_of(const ObjDesc &o, float acc, int model, int NK, double tau_i_d) {
+    const double dv_d = __dmul_rn((double)acc, tau_i_d);
+    const double v0_d = (double)o.v0;
+    const float dvf = (float)dv_d;
+    Regime g{0, 0, NK};
+    if (model == kModelKin) {
+        g.low_hi = NK;
+    } else if (acc > 0.0f) {
+        g.low_hi = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) >= kVMinD; });
+    } else if (acc < 0.0f) {
+        g.low_lo = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) < kVMinD; });
+        g.low_hi = NK;
+    } else if (v0_d < kVMinD) {
+        g.low_hi = NK;
+    }
+    if (acc < 0.0f)
+        g.n_stop = first_true(NK, -o.v0 / dvf - 1.0f, [&](int n) { return speed_at(v0_d, dv_d, n + 1) < 0.0; });
+    return g;
+}
+
+// One vehicle hypothesis by the whole warp (every lane calls it).  Rounds of 32 x 8 sub-steps; lane L
+// takes sub-steps L*8 .. L*8+7 of the round.  Per round: compose and scan the lanes' state maps, run the
+// lanes' sub-steps from their start states (the same per-sub-step arithmetic as the sequential
+// integration), scan the heading increments, form the position increments (heading trig exact at the
+// lane's first sub-step, then rotated by each increment as the sequential integration rotates it), scan
+// them, and store the poses of the output steps that end in each lane's sub-steps (exact heading trig).
+__device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, int N, int K, int lane, long long base,
+                             int h, int i, float *X, float *Y, float *C, float *S) {
+    constexpr int CS = 8;
+    const int NK = N * K;
+    const Regime g = regime_of(o, acc, o.model, NK, o.tau_i_d);
+    const float ti = (float)o.tau_i_d;
+    const float hti2 = 0.5f * ti * ti;
+    const float dv = (float)__dmul_rn((double)acc, o.tau_i_d);
+    const float L = o.lf + o.lr;
+    const float inv_m = 1.0f / o.m, inv_iz = 1.0f / o.Iz;
+    const float k11 = -(o.caf + o.car) * inv_m;
+    const float k12 = (o.car * o.lr - o.caf * o.lf) * inv_m;
+    const float k21 = (o.car * o.lr - o.caf * o.lf) * inv_iz;
+    const float k22 = -(o.caf * o.lf * o.lf + o.car * o.lr * o.lr) * inv_iz;
+    const float kb1 = o.caf * inv_m * delta;
+    const float kb2 = o.caf * o.lf * inv_iz * delta;
+    const float tdel = tanf(delta);
+    const float beta_kin = atanf(o.lr * tdel / L);
+    const float kappa = cosf(beta_kin) * tdel / L;
+    const float stop_den = 0.5f / fabsf(acc == 0.0f ? 1.0f : acc);
+
+    float beta = 0.0f, r = 0.0f;                      // lateral state at the round's first sub-step
+    float ax = acc, ay = 0.0f;                        // acceleration used by the round's first sub-step
+    float ph = o.psi0, pl = 0.0f, xh = o.x0, xl = 0.0f, yh = o.y0, yl = 0.0f;
+    for (int nr = 0; nr < NK; nr += 32 * CS) {
+        // sub-steps per lane this round: 8 for full rounds, fewer for the last (150 sub-steps: 5 per lane)
+        const int csa = min(CS, (min(NK - nr, 32 * CS) + 31) / 32);
+        const int n0 = nr + lane * csa;
+        // 1. the lane's state map, composed over its sub-steps, and the warp scan of the maps
+        Aff F{1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+            const int n = n0 + c;
+            if (c >= csa || n >= NK || n >= g.n_stop) continue;   // outside the lane / frozen state: identity
+            const float v = fmaf((float)n, dv, o.v0);
+            Aff m;
+            if (n >= g.low_lo && n < g.low_hi) {
+                m = Aff{0.0f, 0.0f, 0.0f, 0.0f, beta_kin, v * kappa};
+            } else {
+                const float iv = __fdividef(1.0f, fmaxf(v, 1e-3f));
+                m = Aff{fmaf(ti, k11 * iv, 1.0f), ti * fmaf(k12 * iv, iv, -1.0f), ti * k21, fmaf(ti, k22 * iv, 1.0f),
+                        ti * (kb1 * iv), ti * kb2};
+            }
+            F = aff_then(F, m);
+        }
+        Aff P = F;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            Aff q;
+            q.m00 = __shfl_up_sync(0xffffffffu, P.m00, d); q.m01 = __shfl_up_sync(0xffffffffu, P.m01, d);
+            q.m10 = __shfl_up_sync(0xffffffffu, P.m10, d); q.m11 = __shfl_up_sync(0xffffffffu, P.m11, d);
+            q.c0 = __shfl_up_sync(0xffffffffu, P.c0, d);   q.c1 = __shfl_up_sync(0xffffffffu, P.c1, d);
+            if (lane >= d) P = aff_then(q, P);
+        }
+        Aff E;   // the maps of the earlier lanes (identity for lane 0)
+        E.m00 = __shfl_up_sync(0xffffffffu, P.m00, 1); E.m01 = __shfl_up_sync(0xffffffffu, P.m01, 1);
+        E.m10 = __shfl_up_sync(0xffffffffu, P.m10, 1); E.m11 = __shfl_up_sync(0xffffffffu, P.m11, 1);
+        E.c0 = __shfl_up_sync(0xffffffffu, P.c0, 1);   E.c1 = __shfl_up_sync(0xffffffffu, P.c1, 1);
+        if (lane == 0) E = Aff{1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
+        float bs = fmaf(E.m00, beta, fmaf(E.m01, r, E.c0));
+        float rs = fmaf(E.m10, beta, fmaf(E.m11, r, E.c1));
+
+        // 2. the lane's sub-steps in order: slip trig, heading increments, next accelerations
+        float sbv[CS], cbv[CS], dps[CS], axn[CS], ayn[CS];
+        float ax_last = 0.0f, ay_last = 0.0f;             // the acceleration after the lane's last sub-step
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+            sbv[c] = 0.0f; cbv[c] = 1.0f; dps[c] = 0.0f; axn[c] = 0.0f; ayn[c] = 0.0f;
+            if (c >= csa) continue;
+            const int n = n0 + c;
+            const bool move = n < NK && n < g.n_stop;
+            const bool low = n >= g.low_lo && n < g.low_hi;
+            const float v = fmaf((float)n, dv, o.v0);
+            const float iv = __fdividef(1.0f, fmaxf(v, 1e-3f));
+            const float bd_ot = fmaf(k11 * iv, bs, fmaf(fmaf(k12 * iv, iv, -1.0f), rs, kb1 * iv));
+            const float rd_ot = fmaf(k21, bs, fmaf(k22 * iv, rs, kb2));
+            const float b_use = low ? beta_kin : bs;
+            const float r_use = low ? v * kappa : rs;
+            const float bd = low ? 0.0f : bd_ot;
+            const float rd = low ? 0.0f : rd_ot;
+            float sb, cb;
+            sincos_half(b_use, sb, cb);
+            sbv[c] = sb;
+            cbv[c] = cb;
+            const float w = v * (bd + r_use);
+            axn[c] = fmaf(cb, acc, -sb * w);
+            ayn[c] = fmaf(sb, acc, cb * w);
+            dps[c] = move ? fmaf(r_use, ti, rd * hti2) : 0.0f;
+            if (move) {
+                bs = fmaf(bd, ti, b_use);
+                rs = fmaf(rd, ti, r_use);
+            }
+            ax_last = axn[c];
+            ay_last = ayn[c];
+        }
+        // the next round starts from the state after every lane's maps
+        {
+            const float m00 = __shfl_sync(0xffffffffu, P.m00, 31), m01 = __shfl_sync(0xffffffffu, P.m01, 31);
+            const float m10 = __shfl_sync(0xffffffffu, P.m10, 31), m11 = __shfl_sync(0xffffffffu, P.m11, 31);
+            const float c0 = __shfl_sync(0xffffffffu, P.c0, 31), c1 = __shfl_sync(0xffffffffu, P.c1, 31);
+            const float b2 = fmaf(m00, beta, fmaf(m01, r, c0));
+            r = fmaf(m10, beta, fmaf(m11, r, c1));
+            beta = b2;
+        }
+
+        // 3. heading at every sub-step start: lane sums, scanned
+        float dh = 0.0f, dl = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CS; ++c) df_add(dh, dl, dps[c], 0.0f);
+        float ih = dh, il = dl;
+        df_scan(ih, il, lane);
+        float hh = ph, hl = pl;                                       // heading at the lane's first sub-step
+        {
+            const float eh = __shfl_up_sync(0xffffffffu, ih, 1), el = __shfl_up_sync(0xffffffffu, il, 1);
+            if (lane > 0) df_add(hh, hl, eh, el);
+        }
+        const float th = __shfl_sync(0xffffffffu, ih, 31), tl = __shfl_sync(0xffffffffu, il, 31);
+        const float h_start = hh, l_start = hl;
+
+        // 4. position increments
+        float ax_in = __shfl_up_sync(0xffffffffu, ax_last, 1), ay_in = __shfl_up_sync(0xffffffffu, ay_last, 1);
+        if (lane == 0) { ax_in = ax; ay_in = ay; }
+        float dxv[CS], dyv[CS];
+        float sxh = 0.0f, sxl = 0.0f, syh = 0.0f, syl = 0.0f;
+        float sp, cp;                                  // heading trig: exact at the lane start, then rotated
+        sincos2(hh, hl, sp, cp);
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+            dxv[c] = dyv[c] = 0.0f;
+            if (c >= csa) continue;
+            const int n = n0 + c;
+            const float cpb = fmaf(cp, cbv[c], -sp * sbv[c]);
+            const float spb = fmaf(sp, cbv[c], cp * sbv[c]);
+            const float axu = c ? axn[c - 1] : ax_in, ayu = c ? ayn[c - 1] : ay_in;
+            const float v = fmaf((float)n, dv, o.v0);
+            const bool stop_now = n == g.n_stop;
+            const float d_stop = v * v * stop_den;
+            float dx = stop_now ? cpb * d_stop : fmaf(cpb * v, ti, fmaf(cp, axu, -sp * ayu) * hti2);
+            float dy = stop_now ? spb * d_stop : fmaf(spb * v, ti, fmaf(sp, axu, cp * ayu) * hti2);
+            if (n >= NK || n > g.n_stop) dx = dy = 0.0f;
+            dxv[c] = dx;
+            dyv[c] = dy;
+            df_add(sxh, sxl, dx, 0.0f);
+            df_add(syh, syl, dy, 0.0f);
+            if (dps[c] != 0.0f) {                      // rotate (cos, sin) of the heading by the increment
+                float sd, cd;
+                sincos_tenth(dps[c], sd, cd);
+                const float c2 = fmaf(cp, cd, -sp * sd);
+                sp = fmaf(sp, cd, cp * sd);
+                cp = c2;
+            }
+        }
+        float ixh = sxh, ixl = sxl, iyh = syh, iyl = syl;
+        df_scan(ixh, ixl, lane);
+        df_scan(iyh, iyl, lane);
+
+        // 5. poses of the output steps ending in this lane's sub-steps
+        float px = xh, pxl = xl, py = yh, pyl = yl;
+        {
+            const float eh = __shfl_up_sync(0xffffffffu, ixh, 1), el = __shfl_up_sync(0xffffffffu, ixl, 1);
+            const float fh = __shfl_up_sync(0xffffffffu, iyh, 1), fl = __shfl_up_sync(0xffffffffu, iyl, 1);
+            if (lane > 0) {
+                df_add(px, pxl, eh, el);
+                df_add(py, pyl, fh, fl);
+            }
+        }
+        hh = h_start;
+        hl = l_start;
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+            if (c >= csa) continue;
+            const int n = n0 + c;
+            df_add(px, pxl, dxv[c], 0.0f);
+            df_add(py, pyl, dyv[c], 0.0f);
+            df_add(hh, hl, dps[c], 0.0f);
+            if (n < NK && (n + 1) % K == 0) {                // the pose stores the exact heading trig
+                const int k = (n + 1) / K - 1;
+                float sp, cp;
+                sincos2(hh, hl, sp, cp);
+                const long long idx = base + (long long)k * h + i;
+                X[idx] = __fadd_rn(px, pxl);
+                Y[idx] = __fadd_rn(py, pyl);
+                C[idx] = cp;
+                S[idx] = sp;
+            }
+        }
+
+        // 6. carried into the next round
+        df_add(ph, pl, th, tl);
+        df_add(xh, xl, __shfl_sync(0xffffffffu, ixh, 31), __shfl_sync(0xffffffffu, ixl, 31));
+        df_add(yh, yl, __shfl_sync(0xffffffffu, iyh, 31), __shfl_sync(0xffffffffu, iyl, 31));
+        ax = __shfl_sync(0xffffffffu, ax_last, 31);       // used only after a full round (csa = 8)
+        ay = __shfl_sync(0xffffffffu, ay_last, 31);
+    }
+}
+
 __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= a.n_warps || (threadIdx.x & 31) >= a.lanes) return;
+    if (w >= a.n_warps) return;                          // whole warps leave
+    if (w < a.n_scan) {                                  // one hypothesis by the whole warp
+        const int lane = threadIdx.x & 31;
+        const ObjDesc &o = a.objs[a.warp_obj[w]];
+        const int i = a.warp_first[w];
+        const int ia = i / o.n_b, ib = i - ia * o.n_b;
+        const float ga = a.grids[o.grid_off + ia];
+        const float gb = a.grids[o.grid_off + o.n_a + ib];
+        if (o.kind == kVehicle)
+            vehicle_scan(o, ga, gb, o.n_steps, o.substeps, lane, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
+        else
+            pedestrian(o, ga, gb, o.n_steps, o.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s, lane, 32);
+        return;
+    }
+    if ((threadIdx.x & 31) >= a.lanes) return;
     const ObjDesc &o = a.objs[a.warp_obj[w]];
     const int i = a.warp_first[w] + (threadIdx.x & 31);
     if (i >= o.h) return;

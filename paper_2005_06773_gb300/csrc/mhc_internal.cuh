@@ -89,6 +89,8 @@ struct GenArgs {
     int n_warps;
     int lanes;                // hypotheses per warp task (1..32): fewer than 32 spreads small workloads
                               // over more warp schedulers, since each hypothesis is a sequential chain
+    int n_scan;               // warp tasks [0, n_scan): one hypothesis each, parallel in time (warp_first =
+                              // the hypothesis); the rest: `lanes` hypotheses each, one thread per hypothesis
     float *x, *y, *c, *s;
 };
 

@@ -24,6 +24,7 @@ constexpr size_t kAlign = 256;
 constexpr size_t kReserved = 4096;    // persistent words at the start of the arena (counters)
 constexpr int kSlots = 4;
 constexpr long long kFillInCollideMax = 1LL << 25;   // table entries up to which the collision kernel fills
+constexpr long long kGenScanMaxTraj = 16384;          // a scenario's hypotheses up to which generation is parallel in time
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 inline bool finite(float v) { return std::isfinite(v); }
@@ -43,6 +44,7 @@ struct Layout {
     std::vector<int> pair0;                         // first pair of each scenario (n_scen + 1 entries)
     std::vector<long long> entry0;                  // first table entry of each scenario
     int gen_lanes = 32;
+    int n_gen_scan = 0;                              // the first n_gen_scan generation tasks: a warp per hypothesis
     long long n_traj = 0, n_pose = 0, n_entries = 0, n_tiles = 0, n_bounds = 0;
     long long h_e = 0, n_kofs = 0, n_steps_total = 0, n_lsum = 0, n_mass = 0;
     int n_tiles32 = 0;
@@ -50,7 +52,7 @@ struct Layout {
 
 int build_layout(const mhc_scenario *sc, int n_scen, Layout &L);
 int build_layout(const mhc_scenario *sc, Layout &L);
-void plan_generation(Layout &L, int n_sm);
+void plan_generation(Layout &L, int n_sm, int mode);   // mode: MHC_OPT_GEN_SCAN
 long long acc_words(const Layout &L);
 
 // Device scratch each call needs (besides caller buffers).
@@ -104,6 +106,7 @@ struct mhc_ctx {
     bool has_last = false;
     int cull = 1;
     int variant = 0;
+    int gen_scan = 2;                // generation: 1 a warp per hypothesis (parallel in time), 0 a thread each, 2 auto
     int n_sm = 152;
     // autotuned collision configuration per size class (log2 of the tile count, log2 of the steps)
     struct Tuned { int tiles_log2, steps_log2, fused, variant, cull; };

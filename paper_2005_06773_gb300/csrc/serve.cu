@@ -177,7 +177,7 @@ Batch *form_batch(Server *S, Slot &sl) {
     }
     bool ok = build_layout(scs.data(), (int)scs.size(), b->L) == MHC_OK;
     if (ok) {
-        plan_generation(b->L, S->shadow.n_sm);
+        plan_generation(b->L, S->shadow.n_sm, S->shadow.gen_scan);
         ok = gather_weights(b->L, any_w ? wp.data() : nullptr, b->w) == MHC_OK;
     }
     if (ok) {
@@ -349,6 +349,7 @@ int mhc_serve_start(mhc_ctx *ctx, void *pool, size_t pool_bytes, const mhc_serve
     S->shadow.n_sm = ctx->n_sm;
     S->shadow.cull = ctx->cull;
     S->shadow.variant = ctx->variant;
+    S->shadow.gen_scan = ctx->gen_scan;
     S->shadow.tuned = ctx->tuned;
     S->slots.resize(c.small_slots + c.large_slots);
     for (size_t s = 0; s < S->slots.size(); ++s) {

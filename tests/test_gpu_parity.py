@@ -89,11 +89,18 @@ def scene(name):
 
 
 @pytest.mark.parametrize("name", SCENE_NAMES)
-def test_generation_matches_oracle(mhc, ctx, orc, name):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_generation_matches_oracle(mhc, ctx, orc, name, layout):
+    """Both generation layouts: a thread per hypothesis (sub-steps in order) and a warp per hypothesis
+    (sub-steps in parallel: scans of the state maps and of the heading / position increments)."""
     sc = scene(name)
     ref = orc.generate(sc)
-    p = mhc.generate(ctx, sc)
-    torch.cuda.synchronize()
+    ctx.set_option(mhc.MHC_OPT_GEN_SCAN, layout)
+    try:
+        p = mhc.generate(ctx, sc)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_option(mhc.MHC_OPT_GEN_SCAN, 2)
     g = {k: mhc.poses_by_trajectory(sc, p[k]).astype(np.float64) for k in ("x", "y", "c", "s")}
     err = corner_error(sc, ref, g["x"], g["y"], g["c"], g["s"])
     assert err < POSE_TOL, err
