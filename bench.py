@@ -33,12 +33,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pose-pair tests/s"
 UNIT = "tests/s"
-PROFILE_NOTE = os.path.join(ROOT, "profiles", "collide_kernel_intersection11.md")
+PROFILE_NOTE = os.path.join(ROOT, "profiles", "collide_tile_kernel_intersection11.md")
 COLLIDE_SRC = os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", "collide.cu")
 # algorithmic FP32-pipe lane instructions per unit of collision work (roofline section)
 OPS_PER_BROAD_TEST = 3.0      # 2 FFMA (expanded squared distance) + 1 compare
 OPS_PER_NARROW_TEST = 30.0    # separating-axis test of two rectangles, worst shape combination
 FP32_LANES_PER_SM = 128
+# the kernel behind each collision layout (MHC_OPT_COLLIDE_VARIANT)
+COLLIDE_KERNELS = {1: "collide_kernel<256, 4, 4, 16>", 2: "collide_kernel<64, 8, 8, 8>", 3: "collide_warp_kernel<4, 8>",
+                   4: "collide_tile_kernel<4, 64>", 5: "collide_tile_kernel<1, 32>"}
 
 
 def parse():
@@ -100,8 +103,9 @@ def load_peaks():
         return {}
 
 
-def traffic_from_profile():
-    """DRAM bytes per collide launch from the committed ncu summary, if it was taken on this source."""
+def traffic_from_profile(variant: int):
+    """DRAM bytes per collide launch from the committed ncu summary, if it was taken on this source and
+    this collision layout."""
     try:
         text = open(PROFILE_NOTE).read()
         sha = hashlib.sha256(open(COLLIDE_SRC, "rb").read()).hexdigest()
@@ -109,7 +113,8 @@ def traffic_from_profile():
         return None
     m_sha = re.search(r"collide_source_sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != sha:
+    m_v = re.search(r"collide_variant:\s*([0-9]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha or not m_v or int(m_v.group(1)) != variant:
         return None
     return float(m_b.group(1))
 
@@ -571,7 +576,7 @@ def run_mhc(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     achieved = ops_per_launch / avg_coll_s / 1e12
-    traffic = traffic_from_profile()
+    traffic = traffic_from_profile(tuned[0])
     launches = sum(n for _, n in prof.values())
 
     line = {
@@ -587,7 +592,7 @@ def run_mhc(args):
         "collision_work": {"nominal_tests_per_launch": sc.n_tests(), "executed_tests_per_launch": executed / max(coll_n, 1),
                            "narrow_tests_per_launch": narrow / max(coll_n, 1),
                            "nominal_tests_per_s_collide_only": sc.n_tests() / avg_coll_s},
-        "roofline": {"bound": "alu", "kernel": "collide_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": COLLIDE_KERNELS.get(tuned[0], "collide"), "achieved": achieved, "peak": peak,
                      "unit": "T FP32-lane-instr/s", "frac": achieved / peak, "traffic": traffic,
                      "avg_launch_ms": 1e3 * avg_coll_s, "ops_per_launch": ops_per_launch,
                      "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "

@@ -174,9 +174,10 @@ void mhc_destroy(mhc_ctx *ctx);
 #define MHC_OPT_COLLIDE_VARIANT 3
 /*   MHC_OPT_GEN_SCAN  trajectory generation: 1 one warp per hypothesis, its sub-steps in parallel (warp
  *                 scans of the state maps and of the heading / position increments); 0 one thread per
- *                 hypothesis, sub-steps in order; 2 (default) the first up to 16,384 hypotheses per call,
- *                 the second beyond.  Both follow Eqs. onetrack, EulerVelocity and pedestrianmotion; they
- *                 differ in FP32 rounding only. */
+ *                 hypothesis, sub-steps in order; 2 (default) the first for the objects of scenarios with
+ *                 up to 4096 hypotheses, the second for larger scenarios (chosen per scenario, so that a
+ *                 scenario gets the same poses alone and in any batch).  Both follow Eqs. onetrack,
+ *                 EulerVelocity and pedestrianmotion; they differ in FP32 rounding only. */
 #define MHC_OPT_GEN_SCAN 4
 int mhc_set_option(mhc_ctx *ctx, int option, long long value);
 

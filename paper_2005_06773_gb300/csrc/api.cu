@@ -502,6 +502,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         CollideArgs c{};
         c.objs = D.objs; c.pairs = D.pairs_c; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
         c.max_steps = L.max_steps; c.cull = cull; c.variant = variant; c.fill_blocks = fill_in_collide;
+        c.max_ctas = ctx->collide_max_ctas;
         c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
         c.bounds = bounds; c.table = table; c.counters = ctx->counters;
         if (fused) {
@@ -785,8 +786,11 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
     double saved_ms[MHC_K_COUNT];
     int64_t saved_n[MHC_K_COUNT];
     if (int r = mhc_profile_read(ctx, saved_ms, saved_n, 1)) return r;   // keep the caller's totals aside
-    float best = 1e30f;
+    float best = 1e30f, t_default = 1e30f;
     int bv = 1, bc = 1, rc = MHC_OK;
+    // the layout used without tuning (culling on); kept unless another is at least 10 % faster, so that
+    // near-ties do not flip the choice from run to run
+    const int v_default = L.n_tiles >= 32LL * ctx->n_sm ? 4 : 5;
     ctx->profile = true;
     for (int cull = 1; cull >= 0 && rc == MHC_OK; --cull) {
         for (int v = 1; v <= kCollideVariants && rc == MHC_OK; ++v) {
@@ -823,6 +827,7 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
             const float t = (float)ms[MHC_K_COLLIDE];
             mhc_profile_read(ctx, nullptr, nullptr, 1);
             if (t < best) { best = t; bv = v; bc = cull; }
+            if (v == v_default && cull == 1) t_default = t;
         }
     }
     ctx->variant = saved_variant;
@@ -830,6 +835,7 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
     ctx->profile = saved_profile;
     for (int k = 0; k < MHC_K_COUNT; ++k) { ctx->prof_ms[k] = saved_ms[k]; ctx->prof_n[k] = saved_n[k]; }
     if (rc != MHC_OK) return rc;
+    if (best > 0.90f * t_default) { bv = v_default; bc = 1; }
     const int tl = log2_floor(L.n_tiles), sl = log2_floor(L.max_steps);
     bool stored = false;
     for (auto &t : ctx->tuned)

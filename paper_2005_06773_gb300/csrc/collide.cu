@@ -678,23 +678,16 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
 // are loaded into registers while the current step is tested.  Activity (culling against the blocks'
 // bounding boxes) is decided 32 steps at a time with one ballot.  Fused risk terms are added per hit with
 // global atomics; the per-step histogram terms of one step's hits are summed over the warp first.
-template <int WARPS, int TE, bool FUSED>
-__global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) collide_tile_kernel(const CollideArgs a) {
+// One TE x TE block (warp task gw) walked by the calling warp; pa_s .. s_new are the warp's own slots.
+template <int TE, bool FUSED>
+__device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, int lane, float4 *pa_s, float4 *pb_s,
+                                           float2 *ra_s, float2 *rb_s, unsigned short *queue,
+                                           unsigned long long (*s_new)[2]) {
     static_assert(TE == 64 || TE == 32, "block edge");
     constexpr int MI = TE / 8, MJ = TE / 4;       // micro-block of a lane
     constexpr int SUB = kTile / TE;               // blocks per tile edge
-    constexpr int QCAP = 256;
-    __shared__ float4 s_pa[WARPS][TE];            // x, y, h_a
-    __shared__ float4 s_pb[WARPS][TE];            // x, y, h_b
-    __shared__ float2 s_ra[WARPS][TE];            // c, s
-    __shared__ float2 s_rb[WARPS][TE];
-    __shared__ unsigned short s_queue[WARPS][QCAP];       // candidates: owner lane << 7 | bit
-    __shared__ unsigned long long s_new[WARPS][32][2];     // pairs found in this step, in owner-lane layout
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long g = gw / (SUB * SUB);                 // the 64 x 64 tile
-    if (g >= a.n_tiles) return;                            // whole warps leave; no CTA barrier follows
+    if (g >= a.n_tiles) return;
     const int quarter = (int)(gw - g * (SUB * SUB));
     int lo = 0, hi = a.n_pairs - 1;
     while (lo < hi) {
@@ -719,10 +712,7 @@ __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) coll
     const float rc2 = P.rc2 + kEps0;
     const float ka = 0.5f * (1.0f - kEps);
     const float r_cull = P.r_cull;
-    float4 *pa_s = s_pa[warp], *pb_s = s_pb[warp];
-    float2 *ra_s = s_ra[warp], *rb_s = s_rb[warp];
-    unsigned short *queue = s_queue[warp];
-    unsigned long long *newf = s_new[warp][lane];
+    unsigned long long *newf = s_new[lane];
     newf[0] = newf[1] = 0ull;
     if (TE == 32 && a.fill_blocks) {   // this block's table entries start as -1 (coalesced 64-byte row stores)
         int16_t *row = a.table + P.off + (long long)i0 * B.h + j0;
@@ -868,7 +858,7 @@ __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) coll
                     }
                     if (hit) {
                         any_hit = true;
-                        atomicOr(s_new[warp][owner] + (bit >> 6), 1ull << (bit & 63));
+                        atomicOr(s_new[owner] + (bit >> 6), 1ull << (bit & 63));
                         a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
                         if (FUSED) {
                             const float pa_ = a.probf[A.traj_off + i0 + i], pb_ = a.probf[B.traj_off + j0 + j];
@@ -919,6 +909,25 @@ __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) coll
         atomicAdd(a.acc.count + P.index, hit_cnt);
         atomicAdd(a.acc.P + P.index, hit_mass);
     }
+}
+
+// The warp-per-block layouts: each warp takes blocks gw = blockIdx.x * WARPS + warp, then every
+// gridDim.x * WARPS further (a grid smaller than the work, max_ctas, leaves SM room to other streams).
+template <int WARPS, int TE, bool FUSED>
+__global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) collide_tile_kernel(const CollideArgs a) {
+    constexpr int SUB = kTile / TE;
+    constexpr int QCAP = 256;
+    __shared__ float4 s_pa[WARPS][TE];            // x, y, h_a
+    __shared__ float4 s_pb[WARPS][TE];            // x, y, h_b
+    __shared__ float2 s_ra[WARPS][TE];            // c, s
+    __shared__ float2 s_rb[WARPS][TE];
+    __shared__ unsigned short s_queue[WARPS][QCAP];       // candidates: owner lane << 7 | bit
+    __shared__ unsigned long long s_new[WARPS][32][2];     // pairs found in this step, in owner-lane layout
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long total = a.n_tiles * (SUB * SUB);
+    for (long long gw = (long long)blockIdx.x * WARPS + warp; gw < total; gw += (long long)gridDim.x * WARPS)
+        tile_block<TE, FUSED>(a, gw, lane, s_pa[warp], s_pb[warp], s_ra[warp], s_rb[warp], s_queue[warp],
+                              s_new[warp]);
 }
 
 // table[0, n) = -1 (no collision), 16-byte stores on the aligned body
@@ -980,7 +989,8 @@ template <int WARPS, int TE, bool FUSED>
 cudaError_t launch_tile_variant(const CollideArgs &a, cudaStream_t st) {
     constexpr int SUB = kTile / TE;
     const long long warps = a.n_tiles * SUB * SUB;
-    const long long blocks = (warps + WARPS - 1) / WARPS;
+    long long blocks = (warps + WARPS - 1) / WARPS;
+    if (a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     collide_tile_kernel<WARPS, TE, FUSED><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();

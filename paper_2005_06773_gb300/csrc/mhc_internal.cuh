@@ -132,6 +132,7 @@ struct CollideArgs {
     int max_steps;            // the longest horizon of the batch (sizes the per-CTA accumulators)
     int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
     int fill_blocks;          // 1: each warp writes -1 to its own block first (variant 5; no fill launch)
+    int max_ctas;             // > 0: at most this many CTAs for variants 4, 5 (the warps loop over the blocks)
     int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile, 5: warp per quarter tile
     const float *x, *y, *c, *s;
     const float4 *bounds;

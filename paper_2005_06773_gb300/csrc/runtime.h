@@ -24,7 +24,7 @@ constexpr size_t kAlign = 256;
 constexpr size_t kReserved = 4096;    // persistent words at the start of the arena (counters)
 constexpr int kSlots = 4;
 constexpr long long kFillInCollideMax = 1LL << 25;   // table entries up to which the collision kernel fills
-constexpr long long kGenScanMaxTraj = 16384;          // a scenario's hypotheses up to which generation is parallel in time
+constexpr long long kGenScanMaxTraj = 4096;           // a scenario's hypotheses up to which generation is parallel in time
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 inline bool finite(float v) { return std::isfinite(v); }
@@ -106,6 +106,7 @@ struct mhc_ctx {
     bool has_last = false;
     int cull = 1;
     int variant = 0;
+    int collide_max_ctas = 0;        // > 0: CTA cap of the warp-per-block collision layouts (serving's large lane)
     int gen_scan = 2;                // generation: 1 a warp per hypothesis (parallel in time), 0 a thread each, 2 auto
     int n_sm = 152;
     // autotuned collision configuration per size class (log2 of the tile count, log2 of the steps)

@@ -29,6 +29,8 @@ int64_t now_ns() {
         .count();
 }
 
+constexpr size_t kSlotPinned = 4u << 20;   // initial pinned staging per slot and direction
+
 struct Server;
 struct Batch;
 
@@ -73,11 +75,13 @@ struct Slot {
     Batch *busy = nullptr;
     char *stage = nullptr;   size_t stage_cap = 0;     // pinned: descriptors of the batch
     char *pinned = nullptr;  size_t pinned_cap = 0;    // pinned: risk outputs of the batch
+    std::vector<char *> retired;                        // outgrown pinned buffers (freed at stop)
 };
 
 struct Server {
     mhc_ctx *ctx = nullptr;
     mhc_ctx shadow;                               // collision configuration for the loop's launches
+    mhc_ctx shadow_large;                         // the same with the large lane's CTA cap
     char *base = nullptr;
     mhc_pool *pool = nullptr;
     size_t pool_bytes = 0;
@@ -226,26 +230,29 @@ bool launch_batch(Server *S, Batch *b, Slot &sl) {
     DevDesc D;
     const std::vector<float> *w = b->w.empty() ? nullptr : &b->w;
     const size_t desc = pack_descriptors(b->L, w, nullptr, scr, D);
+    // pinned buffers only grow, and a replaced one is freed at mhc_serve_stop: cudaFreeHost waits for the
+    // device, which would hold this thread (and every admission) behind the batches in flight
     if (sl.stage_cap < desc) {
-        if (sl.stage) cudaFreeHost(sl.stage);
-        sl.stage = nullptr;
-        sl.stage_cap = 0;
-        if (cudaHostAlloc(reinterpret_cast<void **>(&sl.stage), desc * 2, cudaHostAllocDefault) != cudaSuccess) return false;
+        char *nb = nullptr;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&nb), desc * 2, cudaHostAllocDefault) != cudaSuccess) return false;
+        if (sl.stage) sl.retired.push_back(sl.stage);
+        sl.stage = nb;
         sl.stage_cap = desc * 2;
     }
     if (sl.pinned_cap < b->out_bytes) {
-        if (sl.pinned) cudaFreeHost(sl.pinned);
-        sl.pinned = nullptr;
-        sl.pinned_cap = 0;
-        if (cudaHostAlloc(reinterpret_cast<void **>(&sl.pinned), b->out_bytes * 2, cudaHostAllocDefault) != cudaSuccess)
+        char *nb = nullptr;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&nb), b->out_bytes * 2, cudaHostAllocDefault) != cudaSuccess)
             return false;
+        if (sl.pinned) sl.retired.push_back(sl.pinned);
+        sl.pinned = nb;
         sl.pinned_cap = b->out_bytes * 2;
     }
     pack_descriptors(b->L, w, sl.stage, scr, D);
     e = cudaMemcpyAsync(scr, sl.stage, desc, cudaMemcpyHostToDevice, sl.st);
     if (e == cudaSuccess) {
         Bump sb{scr, b->scr_bytes, align_up(desc)};
-        rc = launch_all(&S->shadow, b->L, D, sb, &b->poses, &b->poses, b->table, true, &b->dev, sl.st, true);
+        rc = launch_all(sl.small ? &S->shadow : &S->shadow_large, b->L, D, sb, &b->poses, &b->poses, b->table, true,
+                        &b->dev, sl.st, true);
     }
     if (e == cudaSuccess && rc == MHC_OK)
         e = cudaMemcpyAsync(sl.pinned, b->dev.count, b->out_bytes, cudaMemcpyDeviceToHost, sl.st);
@@ -350,17 +357,30 @@ int mhc_serve_start(mhc_ctx *ctx, void *pool, size_t pool_bytes, const mhc_serve
     S->shadow.cull = ctx->cull;
     S->shadow.variant = ctx->variant;
     S->shadow.gen_scan = ctx->gen_scan;
+    // the large lane may cap its collision kernels' CTAs (collide_max_ctas) to leave SM room to the small
+    // lane; measured at 2000 requests/s, a cap of 3 CTAs per SM slowed the large requests past their
+    // arrival rate, so it is off
+    S->shadow_large = S->shadow;
     S->shadow.tuned = ctx->tuned;
     S->slots.resize(c.small_slots + c.large_slots);
     for (size_t s = 0; s < S->slots.size(); ++s) {
         Slot &sl = S->slots[s];
         sl.small = (int)s < c.small_slots;
-        const cudaError_t e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.small ? greatest : least);
+        cudaError_t e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.small ? greatest : least);
+        // pinned staging sized for typical batches up front (growth allocates, see launch_batch)
+        if (e == cudaSuccess && (e = cudaHostAlloc(reinterpret_cast<void **>(&sl.stage), kSlotPinned, 0)) == cudaSuccess)
+            sl.stage_cap = kSlotPinned;
+        if (e == cudaSuccess && (e = cudaHostAlloc(reinterpret_cast<void **>(&sl.pinned), kSlotPinned, 0)) == cudaSuccess)
+            sl.pinned_cap = kSlotPinned;
         if (e != cudaSuccess) {
+            for (Slot &x : S->slots) {
+                if (x.stage) cudaFreeHost(x.stage);
+                if (x.pinned) cudaFreeHost(x.pinned);
+            }
             for (Slot &x : S->slots) if (x.st) cudaStreamDestroy(x.st);
             pool_delete(S->pool);
             delete S;
-            return cuda_fail(e, "cudaStreamCreateWithPriority");
+            return cuda_fail(e, "serving streams and pinned staging");
         }
     }
     ctx->server = S;
@@ -395,6 +415,7 @@ int mhc_serve_stop(mhc_ctx *ctx) {
         if (sl.st) cudaStreamDestroy(sl.st);
         if (sl.stage) cudaFreeHost(sl.stage);
         if (sl.pinned) cudaFreeHost(sl.pinned);
+        for (char *p : sl.retired) cudaFreeHost(p);
     }
     pool_delete(S->pool);
     ctx->server = nullptr;

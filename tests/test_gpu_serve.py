@@ -52,9 +52,12 @@ def test_results_alone_and_in_the_mix(mhc):
         mix = _mix()
         ws = [S.random_weights(sc, 100 + q) if q % 3 == 0 else None for q, sc in enumerate(mix)]
         tickets = []
-        for q, sc in enumerate(mix):          # arrivals spread so that batches overlap
+        srv.pause(True)                       # the first eight queue up and share a batch
+        for q, sc in enumerate(mix):          # the rest arrive while batches run
             tickets.append(srv.submit(sc, ws[q]))
-            if q % 5 == 4:
+            if q == 7:
+                srv.pause(False)
+            if q > 7 and q % 5 == 4:
                 time.sleep(0.0005)
         outs = []
         for t, sc in zip(tickets, mix):
