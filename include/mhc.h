@@ -188,10 +188,12 @@ int mhc_collision_counters(mhc_ctx *ctx, uint64_t out[2], int reset, void *strea
 
 /* Kernel timing (mhc_set_option(ctx, MHC_OPT_PROFILE, 1)): the library records a CUDA event pair on the
    launching stream around every kernel it launches.  mhc_profile_read synchronises those events and
-   returns, per kernel class (MHC_K_GENERATE; MHC_K_BOUNDS = the table fill and the tile-bounds kernel;
-   MHC_K_COLLIDE; MHC_K_RISK = the risk kernels: prepare, table scan (not in the fused mhc_evaluate /
-   mhc_run path) and the EGO walk), the summed milliseconds and the launch counts
-   since the last reset; reset != 0 clears them.  Disabled by default (no events recorded). */
+   returns, per kernel class (MHC_K_GENERATE, which on the fused mhc_evaluate / mhc_run path also runs the
+   risk preparation in extra CTAs; MHC_K_BOUNDS = the table fill (unless the collision kernel fills) and the
+   tile-bounds kernel; MHC_K_COLLIDE; MHC_K_RISK = the risk kernels: prepare (unfused path), table scan
+   (unfused path), the EGO walk and, for large batches, the totals conversion), the summed milliseconds and
+   the launch counts since the last reset; reset != 0 clears them.  Disabled by default (no events
+   recorded); the events add GPU time, so time steps with it off. */
 #define MHC_OPT_PROFILE 2
 enum { MHC_K_GENERATE = 0, MHC_K_BOUNDS = 1, MHC_K_COLLIDE = 2, MHC_K_RISK = 3, MHC_K_COUNT = 4 };
 int mhc_profile_read(mhc_ctx *ctx, double ms[4], int64_t launches[4], int reset);

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "runtime.h"
+#include "prepare.cuh"
 
 using namespace mhc;
 using namespace mhc::host;
@@ -26,6 +27,36 @@ int fail(int code, const std::string &why) {
 
 int cuda_fail(cudaError_t e, const char *what) {
     return fail(MHC_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Speed regimes of a vehicle hypothesis with acceleration acc (Eq. EulerVelocity, readings of the low-speed
+// limit and the stop rule): the first sub-steps at which the FP64 speed v_0 + n vdot tau_i reaches or leaves
+// 2 m/s and at which the next speed turns negative, by binary search on these monotone predicates.
+Regime speed_regime(float v0f, float acc, int model, int NK, double tau_i_d) {
+    const double dv = (double)acc * tau_i_d;
+    const double v0 = (double)v0f;
+    auto speed = [&](int n) { return v0 + (double)n * dv; };
+    auto first = [&](auto pred) {   // smallest n in [0, NK) with pred(n), NK if none
+        int lo = 0, hi = NK;
+        while (lo < hi) {
+            const int mid = lo + (hi - lo) / 2;
+            if (pred(mid)) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    Regime g{0, 0, NK, 0};
+    if (model == MHC_MODEL_KIN) {
+        g.low_hi = NK;
+    } else if (acc > 0.0f) {
+        g.low_hi = first([&](int n) { return speed(n) >= kVMinD; });
+    } else if (acc < 0.0f) {
+        g.low_lo = first([&](int n) { return speed(n) < kVMinD; });
+        g.low_hi = NK;
+    } else if (v0 < kVMinD) {
+        g.low_hi = NK;
+    }
+    if (acc < 0.0f) g.n_stop = first([&](int n) { return speed(n + 1) < 0.0; });
+    return g;
 }
 
 // Validates scenario `si` and appends it to the layout.
@@ -99,6 +130,11 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
         }
         d.scen = si; d.n_steps = N; d.substeps = sc->substeps; d.model = sc->model; d.tau = sc->tau;
         d.tau_i_d = (double)sc->tau / (double)sc->substeps;
+        if (src.kind == MHC_VEHICLE) {
+            d.regime_off = (int)L.regimes.size();
+            for (int q = 0; q < src.n_a; ++q)
+                L.regimes.push_back(speed_regime(src.v0, src.grid_a[q], sc->model, N * sc->substeps, d.tau_i_d));
+        }
         for (int q = 0; q < d.n_tiles32; ++q) { L.warp_obj.push_back(L.n_obj); L.warp_first.push_back(q * kBoundTile); }
         L.objs.push_back(d);
         ++L.n_obj;
@@ -236,7 +272,8 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
     const size_t gen_tasks = (size_t)L.n_traj + L.objs.size();   // the most generation tasks (a warp each)
     s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + 2 * align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
              align_up(sizeof(ScenDesc) * L.scens.size()) + align_up(sizeof(float) * L.grids.size()) +
-             2 * align_up(sizeof(int) * L.warp_obj.size()) + 2 * align_up(sizeof(int) * gen_tasks);
+             2 * align_up(sizeof(int) * L.warp_obj.size()) + 2 * align_up(sizeof(int) * gen_tasks) +
+             align_up(sizeof(Regime) * L.regimes.size());
     s.bounds = align_up(sizeof(float4) * (size_t)L.n_bounds);
     s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj);
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
@@ -272,7 +309,7 @@ int end_call(mhc_ctx *ctx, cudaStream_t st) {
 }
 
 size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char *host, char *dev, DevDesc &out) {
-    constexpr int kParts = 9;
+    constexpr int kParts = 10;
     const std::pair<const void *, size_t> parts[kParts] = {
         {L.objs.data(), sizeof(ObjDesc) * L.objs.size()},
         {L.pairs.data(), sizeof(PairDesc) * L.pairs.size()},
@@ -283,6 +320,7 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
         {L.warp_first.data(), sizeof(int) * L.warp_first.size()},
         {L.gen_obj.data(), sizeof(int) * L.gen_obj.size()},
         {L.gen_first.data(), sizeof(int) * L.gen_first.size()},
+        {L.regimes.data(), sizeof(Regime) * L.regimes.size()},
     };
     size_t caps[kParts];
     for (int q = 0; q < kParts; ++q) caps[q] = align_up(parts[q].second);
@@ -309,6 +347,7 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
     out.warp_first = reinterpret_cast<int *>(ptrs[6]);
     out.gen_obj = reinterpret_cast<int *>(ptrs[7]);
     out.gen_first = reinterpret_cast<int *>(ptrs[8]);
+    out.regimes = reinterpret_cast<Regime *>(ptrs[9]);
     out.weights = weights ? reinterpret_cast<float *>(ptrs[kParts]) : nullptr;
     return off;
 }
@@ -463,16 +502,23 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     if (risk) {
         if (int rc = make_risk_args(L, D, bump, table, rout, r)) return rc;
     }
-    if (fused) {
+    if (fused && !gen_out) {   // else the preparation runs inside the generation launch
         TimedScope ts(ctx, st, MHC_K_RISK, 1);
         cudaError_t e = launch_risk_prepare(r, st);
         if (e != cudaSuccess) return cuda_fail(e, "risk prepare launch");
     }
     if (gen_out) {
         GenArgs g;
-        g.objs = D.objs; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
+        g.objs = D.objs; g.regimes = D.regimes; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
         g.n_warps = (int)L.gen_obj.size(); g.lanes = L.gen_lanes;
         g.n_scan = L.n_gen_scan;
+        g.gen_blocks = 0;
+        g.prep_blocks = 0;
+        std::memset(&g.prep, 0, sizeof g.prep);
+        if (fused) {
+            g.prep = prep_of(r);
+            g.prep_blocks = L.n_obj > 304 ? L.n_obj : 304;
+        }
         g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
         cudaError_t e = launch_generate(g, st);

@@ -3,12 +3,13 @@
 //
 // Vehicles: one-track model (Eq. onetrack) with constant steering and acceleration, integrated by
 // Eq. (EulerVelocity) with sub-step tau / K; the low-speed kinematic limit and the stop rule are applied
-// on the sub-steps where the FP64 speed v_0 + n vdot tau_i crosses 2 m/s / zero (the same FP64 decision
-// the method's reference arithmetic takes).  Arithmetic is FP32; x, y and psi are carried as
+// on the sub-steps where the FP64 speed v_0 + n vdot tau_i crosses 2 m/s / zero (decided on the host in
+// FP64, per object and acceleration value, and read from a table: no FP64 arithmetic runs here).  Arithmetic is FP32; x, y and psi are carried as
 // compensated (hi, lo) sums so that 250+ sub-steps add no more than ~1e-6 m of rounding.
 // Pedestrians: Eq. (pedestrianmotion) with a constant acceleration integrates exactly, so every output
 // pose is evaluated in closed form (speed saturating at 0 or at the cap).
 #include "mhc_internal.cuh"
+#include "prepare.cuh"
 
 namespace mhc {
 namespace {
@@ -58,41 +59,10 @@ __device__ __forceinline__ void sincos_tenth(float x, float &sn, float &cs) {
     cs = fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f), 1.0f);
 }
 
-__device__ __forceinline__ double speed_at(double v0, double dv, int n) {
-    return __dadd_rn(v0, __dmul_rn((double)n, dv));
-}
-
-// Smallest n in [0, NK] with pred(n) (pred monotone false..true; NK if it never holds before NK), found
-// from an FP32 estimate and settled by evaluating the FP64 predicate next to it.
-template <class P>
-__device__ int first_true(int NK, float estimate, P pred) {
-    int n = estimate <= 0.0f ? 0 : (estimate >= (float)NK ? NK : (int)ceilf(estimate));
-    while (n > 0 && pred(n - 1)) --n;
-    while (n < NK && !pred(n)) ++n;
-    return n;
-}
-
-__device__ void vehicle(const ObjDesc &o, float acc, float delta, int model, int N, int K, double tau_i_d,
+__device__ void vehicle(const ObjDesc &o, float acc, float delta, const Regime &g, int N, int K, double tau_i_d,
                         long long base, int h, int i, float *X, float *Y, float *C, float *S) {
-    const double dv_d = __dmul_rn((double)acc, tau_i_d);
-    const double v0_d = (double)o.v0;
-    const int NK = N * K;
-    const float dvf = (float)dv_d;
-    // low-speed regime: sub-steps with v_n < kVMin (a prefix when accelerating, a suffix when braking)
-    int low_lo = 0, low_hi = 0;   // low regime on [low_lo, low_hi)
-    if (model == kModelKin) {
-        low_hi = NK;
-    } else if (acc > 0.0f) {
-        low_hi = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) >= kVMinD; });
-    } else if (acc < 0.0f) {
-        low_lo = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) < kVMinD; });
-        low_hi = NK;
-    } else if (v0_d < kVMinD) {
-        low_hi = NK;
-    }
-    int n_stop = NK;   // sub-step at which v_{n+1} < 0 first holds
-    if (acc < 0.0f)
-        n_stop = first_true(NK, -o.v0 / dvf - 1.0f, [&](int n) { return speed_at(v0_d, dv_d, n + 1) < 0.0; });
+    const float dvf = (float)__dmul_rn((double)acc, tau_i_d);
+    const int low_lo = g.low_lo, low_hi = g.low_hi, n_stop = g.n_stop;   // low regime on [low_lo, low_hi)
 
     const float ti = (float)tau_i_d;
     const float hti2 = 0.5f * ti * ti;
@@ -244,43 +214,16 @@ __device__ __forceinline__ Aff aff_then(const Aff &first, const Aff &second) {
     return r;
 }
 
-// Sub-steps of the low-speed regime [low_lo, low_hi) and the stop sub-step, decided exactly as the
-// sequential integration decides them (FP64 speed v_0 + n vdot tau_i).
-struct Regime {
-    int low_lo, low_hi, n_stop;
-};
-
-__device__ Regime regime_of(const ObjDesc &o, float acc, int model, int NK, double tau_i_d) {
-    const double dv_d = __dmul_rn((double)acc, tau_i_d);
-    const double v0_d = (double)o.v0;
-    const float dvf = (float)dv_d;
-    Regime g{0, 0, NK};
-    if (model == kModelKin) {
-        g.low_hi = NK;
-    } else if (acc > 0.0f) {
-        g.low_hi = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) >= kVMinD; });
-    } else if (acc < 0.0f) {
-        g.low_lo = first_true(NK, (kVMin - o.v0) / dvf, [&](int n) { return speed_at(v0_d, dv_d, n) < kVMinD; });
-        g.low_hi = NK;
-    } else if (v0_d < kVMinD) {
-        g.low_hi = NK;
-    }
-    if (acc < 0.0f)
-        g.n_stop = first_true(NK, -o.v0 / dvf - 1.0f, [&](int n) { return speed_at(v0_d, dv_d, n + 1) < 0.0; });
-    return g;
-}
-
 // One vehicle hypothesis by the whole warp (every lane calls it).  Rounds of 32 x 8 sub-steps; lane L
 // takes sub-steps L*8 .. L*8+7 of the round.  Per round: compose and scan the lanes' state maps, run the
 // lanes' sub-steps from their start states (the same per-sub-step arithmetic as the sequential
 // integration), scan the heading increments, form the position increments (heading trig exact at the
 // lane's first sub-step, then rotated by each increment as the sequential integration rotates it), scan
 // them, and store the poses of the output steps that end in each lane's sub-steps (exact heading trig).
-__device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, int N, int K, int lane, long long base,
-                             int h, int i, float *X, float *Y, float *C, float *S) {
+__device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Regime &g, int N, int K, int lane,
+                             long long base, int h, int i, float *X, float *Y, float *C, float *S) {
     constexpr int CS = 8;
     const int NK = N * K;
-    const Regime g = regime_of(o, acc, o.model, NK, o.tau_i_d);
     const float ti = (float)o.tau_i_d;
     const float hti2 = 0.5f * ti * ti;
     const float dv = (float)__dmul_rn((double)acc, o.tau_i_d);
@@ -473,6 +416,10 @@ __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, int N, in
 }
 
 __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
+    if ((int)blockIdx.x >= a.gen_blocks) {               // the risk preparation, independent of generation
+        prepare_block(a.prep, blockIdx.x - a.gen_blocks, a.prep_blocks);
+        return;
+    }
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= a.n_warps) return;                          // whole warps leave
     if (w < a.n_scan) {                                  // one hypothesis by the whole warp
@@ -483,7 +430,8 @@ __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
         const float ga = a.grids[o.grid_off + ia];
         const float gb = a.grids[o.grid_off + o.n_a + ib];
         if (o.kind == kVehicle)
-            vehicle_scan(o, ga, gb, o.n_steps, o.substeps, lane, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
+            vehicle_scan(o, ga, gb, a.regimes[o.regime_off + ia], o.n_steps, o.substeps, lane, o.pose_base, o.h, i,
+                         a.x, a.y, a.c, a.s);
         else
             pedestrian(o, ga, gb, o.n_steps, o.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s, lane, 32);
         return;
@@ -496,7 +444,8 @@ __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
     const float ga = a.grids[o.grid_off + ia];
     const float gb = a.grids[o.grid_off + o.n_a + ib];
     if (o.kind == kVehicle)
-        vehicle(o, ga, gb, o.model, o.n_steps, o.substeps, o.tau_i_d, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
+        vehicle(o, ga, gb, a.regimes[o.regime_off + ia], o.n_steps, o.substeps, o.tau_i_d, o.pose_base, o.h, i,
+                a.x, a.y, a.c, a.s);
     else
         pedestrian(o, ga, gb, o.n_steps, o.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
 }
@@ -530,12 +479,16 @@ __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
 
 }  // namespace
 
-cudaError_t launch_generate(const GenArgs &a, cudaStream_t st) {
-    if (a.n_warps <= 0) return cudaSuccess;
-    // few warps: one warp per block so that the latency-bound integration spreads over all SMs
+cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
+    GenArgs a = args;
+    if (a.n_warps <= 0 && a.prep_blocks <= 0) return cudaSuccess;
+    // few warps: one warp per block so that the latency-bound integration spreads over all SMs; the
+    // preparation CTAs (if any) then have 128 threads as well
     const int warps_per_block = a.n_warps < 4 * 152 ? 1 : 4;
-    const int blocks = (a.n_warps + warps_per_block - 1) / warps_per_block;
-    gen_kernel<<<blocks, 32 * warps_per_block, 0, st>>>(a);
+    a.gen_blocks = (a.n_warps + warps_per_block - 1) / warps_per_block;
+    const long long blocks = (long long)a.gen_blocks + (a.prep_blocks > 0 ? a.prep_blocks : 0);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    gen_kernel<<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
     return cudaGetLastError();
 }
 

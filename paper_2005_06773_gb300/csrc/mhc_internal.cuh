@@ -43,7 +43,7 @@ struct ObjDesc {
     int scen;           // scenario index in the batch
     int n_steps, substeps, model;
     float tau;
-    int pad_;
+    int regime_off;     // vehicles: the speed regimes of grid_a[0..n_a) at regimes[regime_off ..]
     double tau_i_d;     // (double)tau / substeps, the sub-step of the speed recurrence
 };
 
@@ -81,14 +81,37 @@ struct ScenDesc {
     long long step_base;      // the scenario's n_steps entries of attr_step
 };
 
+// Sub-steps of a vehicle hypothesis's low-speed regime [low_lo, low_hi) and its stop sub-step (n_stop = N K
+// if it never stops), decided on the FP64 speed v_0 + n vdot tau_i; one entry per acceleration value.
+struct Regime {
+    int low_lo, low_hi, n_stop, pad_;
+};
+
+// The risk preparation (prepare.cuh): accumulators to zero, escape lists to fill, weights to normalise.
+struct PrepArgs {
+    unsigned long long *base;      // accumulator words to zero
+    long long n_words;
+    int *escape;                   // [h_e] escape lists (may be null)
+    long long h_e;
+    const ObjDesc *objs;
+    int n_obj;
+    const float *weights;          // [n_traj] raw weights, or null for uniform
+    double *prob;                  // [n_traj] normalised probabilities
+    float *probf;                  // [n_traj] the same rounded to FP32
+};
+
 struct GenArgs {
     const ObjDesc *objs;
+    const Regime *regimes;
     const float *grids;
     const int *warp_obj;      // object of each warp task
     const int *warp_first;    // first hypothesis of each warp task
     int n_warps;
     int lanes;                // hypotheses per warp task (1..32): fewer than 32 spreads small workloads
                               // over more warp schedulers, since each hypothesis is a sequential chain
+    int gen_blocks;           // set by launch_generate: CTAs of the generation tasks
+    int prep_blocks;          // > 0: that many further CTAs run the risk preparation `prep` (fused path)
+    PrepArgs prep;
     int n_scan;               // warp tasks [0, n_scan): one hypothesis each, parallel in time (warp_first =
                               // the hypothesis); the rest: `lanes` hypotheses each, one thread per hypothesis
     float *x, *y, *c, *s;

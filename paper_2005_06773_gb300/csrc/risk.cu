@@ -16,6 +16,7 @@
 // 64-bit fixed point by integer atomics (exact, order-independent, bitwise reproducible).  FP64 -- a
 // narrow pipe on this GPU -- runs only in dense per-warp steps.
 #include "mhc_internal.cuh"
+#include "prepare.cuh"
 
 namespace mhc {
 namespace {
@@ -40,32 +41,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // blocks [0, n_obj) normalise one object each; every block zeroes a slice of the accumulators
-__global__ void __launch_bounds__(256) prepare_kernel(const RiskArgs a) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < a.acc.n_words; w += stride)
-        a.acc.base[w] = 0ull;
-    if (a.escape)   // entries past each scenario's escape routes read -1
-        for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < a.h_e; w += stride) a.escape[w] = -1;
-    if (blockIdx.x >= a.n_obj) return;
-    const ObjDesc &o = a.objs[blockIdx.x];
-    __shared__ double s_part[8];
-    double sum = 0.0;
-    if (a.weights) {
-        for (int i = threadIdx.x; i < o.h; i += blockDim.x) sum += (double)a.weights[o.traj_off + i];
-        sum = warp_sum(sum);
-        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
-        __syncthreads();
-        sum = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += s_part[q];
-    } else {
-        sum = (double)o.h;
-    }
-    for (int i = threadIdx.x; i < o.h; i += blockDim.x) {
-        const double p = (a.weights ? (double)a.weights[o.traj_off + i] : 1.0) / sum;
-        a.prob[o.traj_off + i] = p;
-        a.probf[o.traj_off + i] = (float)p;
-    }
-}
+__global__ void __launch_bounds__(256) prepare_kernel(const PrepArgs a) { prepare_block(a, blockIdx.x, gridDim.x); }
 
 __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
     // dynamic: [N] u64 masses | [N] u32 counts | [64][N] u64 log-survival cells of the tile's EGO hypotheses
@@ -366,7 +342,7 @@ long long convert_elements(const RiskArgs &a) {
 
 cudaError_t launch_risk_prepare(const RiskArgs &a, cudaStream_t st) {
     const int prep_blocks = a.n_obj > 304 ? a.n_obj : 304;
-    prepare_kernel<<<prep_blocks, 256, 0, st>>>(a);
+    prepare_kernel<<<prep_blocks, 256, 0, st>>>(prep_of(a));
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ struct Layout {
     std::vector<PairDesc> pairs_c;                   // the same in collision-grid order (closest pairs first)
     std::vector<ScenDesc> scens;
     std::vector<float> grids;
+    std::vector<Regime> regimes;                     // per vehicle and acceleration value
     std::vector<int> warp_obj, warp_first;          // 32-hypothesis bound tiles
     std::vector<int> gen_obj, gen_first;            // generation warp tasks of gen_lanes hypotheses
     std::vector<int> pair0;                         // first pair of each scenario (n_scen + 1 entries)
@@ -85,6 +86,7 @@ struct DevDesc {
     float *grids;
     int *warp_obj, *warp_first;
     int *gen_obj, *gen_first;
+    Regime *regimes;
     float *weights;
 };
 
