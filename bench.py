@@ -41,7 +41,7 @@ OPS_PER_NARROW_TEST = 30.0    # separating-axis test of two rectangles, worst sh
 FP32_LANES_PER_SM = 128
 # the kernel behind each collision layout (MHC_OPT_COLLIDE_VARIANT)
 COLLIDE_KERNELS = {1: "collide_kernel<256, 4, 4, 16>", 2: "collide_kernel<64, 8, 8, 8>", 3: "collide_warp_kernel<4, 8>",
-                   4: "collide_tile_kernel<4, 64>", 5: "collide_tile_kernel<1, 32>"}
+                   4: "collide_tile_kernel<4, 64>", 5: "collide_tile_kernel<1, 32>", 6: "items_kernel"}
 
 
 def parse():
@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the stress32 / paper_s2 / batch / serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="window of the serving measurement")
-    ap.add_argument("--collide-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--collide-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="collision kernel layout; 0 = chosen by mhc_autotune in the set-up (profiling fixes one)")
     ap.add_argument("--workload", default="intersection11", choices=sorted(WORKLOADS),
                     help="the timed workload (the default is the benchmark's; the others serve profiling)")

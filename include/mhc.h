@@ -169,6 +169,9 @@ void mhc_destroy(mhc_ctx *ctx);
  *                 4: one warp per tile walking its steps in order (8 x 16 micro-tiles per lane, pairs that
  *                    already hit dropped from later steps, first hits stored at once);
  *                 5: as 4 with one warp per 32 x 32 quarter tile (4 x 8 micro-tiles, culling per quarter);
+ *                 6: every active (quarter tile, step) an item, all tested in parallel by persistent warps (a
+ *                    pair's first step by atomicMin in scratch, the table and the risk terms written after);
+ *                    for small scenes (at most 2^22 items and 2^26 table entries; larger ones use 5);
  *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 4 for at
  *                 least 32 tiles per SM and 5 below. */
 #define MHC_OPT_COLLIDE_VARIANT 3

@@ -259,6 +259,13 @@ void plan_generation(Layout &L, int n_sm, int mode) {
             for (int q = 0; q < L.objs[o].h; q += lanes) { L.gen_obj.push_back(o); L.gen_first.push_back(q); }
 }
 
+// The step-item layout (collision variant 6) applies while its item list (4 x tiles x steps entries) stays
+// small; the list lives in the call's scratch.
+bool items_eligible(const Layout &L) {
+    return L.n_tiles * 4 <= 0x7fffffffLL && 4 * L.n_tiles * (long long)L.max_steps <= kItemsMax &&
+           L.n_entries <= kItemsMaxEntries;
+}
+
 // Device scratch each call needs (besides caller buffers).
 // 64-bit accumulator words of one assessment
 long long acc_words(const Layout &L) {
@@ -279,7 +286,10 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
     s.acc_words = acc_words(L);
     s.acc = align_up(8 * (size_t)s.acc_words);
-    s.total = s.desc + s.weights + s.bounds + s.prob + s.acc;
+    s.items = items_eligible(L) ? kAlign + align_up(8 * (size_t)(4 * L.n_tiles * (long long)L.max_steps)) +
+                                      align_up(4 * (size_t)L.n_entries) + align_up(16 * (size_t)L.n_tiles)
+                                : 0;
+    s.total = s.desc + s.weights + s.bounds + s.prob + s.acc + s.items;
     return s;
 }
 
@@ -527,11 +537,12 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     if (coll_in) {
         int variant = 1, cull = 1;
         pick_collide_config(ctx, L, fused, variant, cull);
+        if (variant == 6 && !items_eligible(L)) variant = 5;
         float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_bounds));
         if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
         // small tables: the quarter-tile layout writes the -1s of its own blocks (one launch less); large ones
         // are filled by the HBM-rate fill kernel (in-kernel 2-byte row stores cost issue slots there)
-        const bool fill_in_collide = variant == 5 && L.n_entries <= kFillInCollideMax;
+        const bool fill_in_collide = (variant == 5 && L.n_entries <= kFillInCollideMax) || variant == 6;
         {
             TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_in_collide ? 0 : 1));
             cudaError_t e = fill_in_collide ? cudaSuccess : launch_fill_table(table, L.n_entries, st);
@@ -555,11 +566,22 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
             c.probf = r.probf;
             c.acc = r.acc;
         }
-        TimedScope ts(ctx, st, MHC_K_COLLIDE, 1);
+        if (variant == 6) {   // the item list and its length (zeroed here)
+            c.max_items = 4 * L.n_tiles * (long long)L.max_steps;
+            c.item_count = static_cast<unsigned long long *>(bump.take(kAlign));
+            c.items = static_cast<int2 *>(bump.take(sizeof(int2) * (size_t)c.max_items));
+            c.active_count = c.item_count + 1;
+            c.first32 = static_cast<int *>(bump.take(sizeof(int) * (size_t)L.n_entries));
+            c.active = static_cast<int *>(bump.take(sizeof(int) * (size_t)(4 * L.n_tiles)));
+            if (!c.items || !c.item_count || !c.first32 || !c.active)
+                return fail(MHC_E_NOMEM, "arena too small for the step items");
+            MHC_CUDA(cudaMemsetAsync(c.item_count, 0, 2 * sizeof(unsigned long long), st));
+        }
+        TimedScope ts(ctx, st, MHC_K_COLLIDE, variant == 6 ? 3 : 1);
         cudaError_t e = launch_collide(c, st);
         if (e != cudaSuccess) return cuda_fail(e, "collision kernel launch");
     }
-    if (risk) {
+    if (risk) {   // fused collision: the walk only; else preparation, table scan and walk
         TimedScope ts(ctx, st, MHC_K_RISK, (fused ? 0 : 2) + risk_tail_launches(r));
         cudaError_t e = fused ? launch_risk_tail(r, st) : launch_risk(r, st);
         if (e != cudaSuccess) return cuda_fail(e, "risk kernel launch");
@@ -651,7 +673,7 @@ int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
         return MHC_OK;
     }
     if (option == MHC_OPT_COLLIDE_VARIANT) {
-        if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 5");
+        if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 6");
         ctx->variant = (int)value;
         return MHC_OK;
     }
@@ -870,7 +892,9 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
                 if ((rc = mhc_profile_read(ctx, ms, n, rep == 0))) break;
             }
             if (rc != MHC_OK) break;
-            const float t = (float)ms[MHC_K_COLLIDE];
+            // the collision stage as the path runs it: fill / bounds, collision, and (fused) the risk kernels,
+            // which carry the table scan when a layout does not fuse it
+            const float t = (float)(ms[MHC_K_BOUNDS] + ms[MHC_K_COLLIDE] + (fused ? ms[MHC_K_RISK] : 0.0));
             mhc_profile_read(ctx, nullptr, nullptr, 1);
             if (t < best) { best = t; bv = v; bc = cull; }
             if (v == v_default && cull == 1) t_default = t;

@@ -930,6 +930,277 @@ __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) coll
                               s_new[warp]);
 }
 
+// ---- step-item layout (variant 6): the active (block, step) pairs of a small scene in parallel ----------
+//
+// The warp-per-block layouts walk a block's steps in order, so a block whose objects stay close for many
+// steps is one long chain, and on small scenes the launch waits for it.  Here a first kernel lists every
+// active step of every 32 x 32 block as an item; then persistent warps test one item each, all steps at
+// once, keeping a pair's earliest overlapping step in a 32-bit scratch array with a fire-and-forget
+// atomicMin (INT_MAX: none); a third kernel writes the int16 table from it and adds the risk terms of the
+// first hits.  Pairs that already hit are retested at later steps (there is no in-order mask).
+
+// the pair of global 32 x 32 block gw (4 per 64 x 64 tile) and the block's origin and extent
+struct BlockAt {
+    int pair, i0, j0, rows, cols;
+};
+
+__device__ __forceinline__ BlockAt block_at(const CollideArgs &a, long long gw) {
+    const long long g = gw >> 2;
+    const int quarter = (int)(gw & 3);
+    int lo = 0, hi = a.n_pairs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
+    }
+    const PairDesc &P = a.pairs[lo];
+    const long long t = g - P.tile_start;
+    const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
+    BlockAt r;
+    r.pair = lo;
+    r.i0 = (ta * 2 + (quarter >> 1)) * 32;
+    r.j0 = (tb * 2 + (quarter & 1)) * 32;
+    r.rows = min(32, a.objs[P.a].h - r.i0);
+    r.cols = min(32, a.objs[P.b].h - r.j0);
+    return r;
+}
+
+// One warp per block (grid-stride): its active steps appended to the item list (one ballot per 32 steps,
+// one atomic per ballot); then a block without any writes its table entries (-1) at once, and an active
+// block sets its first-step entries to INT_MAX and joins the list of active blocks.
+__global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long long total = a.n_tiles * 4;
+    for (long long gw = (long long)blockIdx.x * 4 + (threadIdx.x >> 5); gw < total; gw += (long long)gridDim.x * 4) {
+        const BlockAt blk = block_at(a, gw);
+        if (blk.rows <= 0 || blk.cols <= 0) continue;            // a quarter past a ragged edge
+        const PairDesc &P = a.pairs[blk.pair];
+        const ObjDesc &A = a.objs[P.a];
+        const ObjDesc &B = a.objs[P.b];
+        const int N = P.n_steps;
+        int n_active = 0;
+        const float4 *bA0 = a.bounds + A.bounds_base + (long long)(blk.i0 / kBoundTile) * N;
+        const float4 *bB0 = a.bounds + B.bounds_base + (long long)(blk.j0 / kBoundTile) * N;
+        const float rc = P.r_cull;
+        for (int k0 = 0; k0 < N; k0 += 32) {
+            const int k = k0 + lane;
+            bool act = k < N;
+            if (act && a.cull) {
+                const float4 ba = bA0[k], bb = bB0[k];
+                act = (ba.x - rc <= bb.z) && (bb.x - rc <= ba.z) && (ba.y - rc <= bb.w) && (bb.y - rc <= ba.w);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, act);
+            if (!m) continue;
+            n_active += __popc(m);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.item_count, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (act) {
+                const unsigned long long at = base + __popc(m & ((1u << lane) - 1u));
+                if (at < (unsigned long long)a.max_items) a.items[at] = make_int2((int)gw, k);
+            }
+        }
+        const long long base = P.off + (long long)blk.i0 * B.h + blk.j0 + lane;
+        if (n_active == 0) {                    // never close: the table entries are final now
+            if (lane < blk.cols)
+                for (int r = 0; r < blk.rows; ++r) a.table[base + (long long)r * B.h] = (int16_t)-1;
+            continue;
+        }
+        if (lane < blk.cols)
+            for (int r = 0; r < blk.rows; ++r) a.first32[base + (long long)r * B.h] = 0x7fffffff;
+        if (lane == 0) {
+            const unsigned long long at = atomicAdd(a.active_count, 1ull);
+            if (at < (unsigned long long)(a.n_tiles * 4)) a.active[at] = (int)gw;
+        }
+    }
+}
+
+// Persistent one-warp CTAs take items it = blockIdx.x, + gridDim.x, ...: stage the block's 32 + 32 poses
+// of the item's step, broad phase on a 4 x 8 micro-block per lane, candidates compacted and tested one per
+// lane, hits kept with atomicMin on the first-step array (no return value: nothing waits on it).
+__global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
+    constexpr int MI = 4, MJ = 8;
+    __shared__ float4 pa_s[32], pb_s[32];   // x, y, h
+    __shared__ float2 ra_s[32], rb_s[32];   // c, s
+    __shared__ unsigned short queue[256];
+    const int lane = threadIdx.x, lr = lane >> 2, lc = lane & 3;
+    const float ka = 0.5f * (1.0f - kEps);
+    const unsigned long long listed = *a.item_count;
+    const long long count = listed < (unsigned long long)a.max_items ? (long long)listed : a.max_items;
+    unsigned long long narrow = 0, executed = 0;
+    for (long long it = blockIdx.x; it < count; it += gridDim.x) {
+        const int2 item = a.items[it];
+        const int k = item.y;
+        const BlockAt blk = block_at(a, item.x);
+        const PairDesc &P = a.pairs[blk.pair];
+        const ObjDesc &A = a.objs[P.a];
+        const ObjDesc &B = a.objs[P.b];
+        const float rc2 = P.rc2 + kEps0;
+        const bool oka = lane < blk.rows, okb = lane < blk.cols;
+        const long long ia = A.pose_base + (long long)k * A.h + blk.i0 + lane;
+        const long long ib = B.pose_base + (long long)k * B.h + blk.j0 + lane;
+        const float xa = oka ? __ldg(a.x + ia) : kFar, ya = oka ? __ldg(a.y + ia) : 0.0f;
+        const float ca = oka ? __ldg(a.c + ia) : 1.0f, sa = oka ? __ldg(a.s + ia) : 0.0f;
+        const float xb = okb ? __ldg(a.x + ib) : -kFar, yb = okb ? __ldg(a.y + ib) : 0.0f;
+        const float cb = okb ? __ldg(a.c + ib) : 1.0f, sb = okb ? __ldg(a.s + ib) : 0.0f;
+        __syncwarp();                           // the previous item's slot is no longer read
+        pa_s[lane] = make_float4(xa, ya, ka * fmaf(xa, xa, ya * ya), 0.0f);
+        ra_s[lane] = make_float2(ca, sa);
+        pb_s[lane] = make_float4(xb, yb, 0.5f * fmaf(1.0f - kEps, fmaf(xb, xb, yb * yb), -rc2), 0.0f);
+        rb_s[lane] = make_float2(cb, sb);
+        __syncwarp();
+        executed += 32 * 32;
+        float ax[MI], ay[MI], ah[MI];
+#pragma unroll
+        for (int m = 0; m < MI; ++m) {
+            const float4 q = pa_s[lr + 8 * m];
+            ax[m] = q.x; ay[m] = q.y; ah[m] = q.z;
+        }
+        unsigned cand = 0u;                     // bit MJ m + n
+#pragma unroll
+        for (int n = 0; n < MJ; ++n) {
+            const float4 qb = pb_s[lc + 4 * n];
+#pragma unroll
+            for (int m = 0; m < MI; ++m)
+                if (fmaf(ax[m], qb.x, fmaf(ay[m], qb.y, -qb.z)) >= ah[m]) cand |= 1u << (MJ * m + n);
+        }
+        if (!__ballot_sync(0xffffffffu, cand != 0u)) continue;
+        const float la = A.hl, wa = A.hw, ra = A.rad, lb = B.hl, wb = B.hw, rb = B.rad;
+        for (;;) {                              // rounds of at most 8 candidates per lane
+            const int cnt = min(__popc(cand), 8);
+            if (!__ballot_sync(0xffffffffu, cnt != 0)) break;
+            int off = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, off, d);
+                if (lane >= d) off += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, off, 31);
+            off -= cnt;
+            for (int q = 0; q < cnt; ++q) {
+                const int bit = __ffs(cand) - 1;
+                cand &= cand - 1u;
+                queue[off + q] = (unsigned short)((lane << 7) | bit);
+            }
+            __syncwarp();
+            narrow += total;
+            for (int e = lane; e < total; e += 32) {
+                const int ent = queue[e];
+                const int owner = ent >> 7, bit = ent & 127;
+                const int i = (owner >> 2) + 8 * (bit / MJ), j = (owner & 3) + 4 * (bit % MJ);
+                const float4 qa4 = pa_s[i], qb4 = pb_s[j];
+                const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
+                const float2 qa = ra_s[i], qb = rb_s[j];
+                bool hit;
+                switch (P.combo) {
+                    case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
+                    case 1: hit = rect_disc(dx, dy, qa.x, qa.y, la, wa, rb); break;
+                    case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
+                    default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
+                }
+                if (hit) atomicMin(a.first32 + P.off + (long long)(blk.i0 + i) * B.h + blk.j0 + j, k);
+            }
+            __syncwarp();
+        }
+    }
+    if (a.counters && lane == 0) {
+        if (narrow) atomicAdd(a.counters + 1, narrow);
+        if (executed) atomicAdd(a.counters, executed);
+    }
+}
+
+// The table of the step-item layout from the first-step array, and (probf set) the risk terms of its first
+// hits: one warp per block (grid-stride, lane = column) takes the block's rows 8 at a time (the 8 loads in
+// flight together), writes the int16 entries and adds each first hit's terms with the fixed-point atomics
+// of the fused layouts (the same sums, in any order).
+__global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
+    const int lane = threadIdx.x & 31;
+    const bool risk = a.probf != nullptr;
+    const unsigned long long listed = *a.active_count;
+    const long long total = listed < (unsigned long long)(a.n_tiles * 4) ? (long long)listed : a.n_tiles * 4;
+    for (long long q = (long long)blockIdx.x * 4 + (threadIdx.x >> 5); q < total; q += (long long)gridDim.x * 4) {
+        const BlockAt blk = block_at(a, a.active[q]);
+        if (blk.rows <= 0 || blk.cols <= 0) continue;
+        const PairDesc &P = a.pairs[blk.pair];
+        const ObjDesc &A = a.objs[P.a];
+        const ObjDesc &B = a.objs[P.b];
+        const int N = P.n_steps;
+        const bool col_ok = lane < blk.cols;
+        const float pb = risk && col_ok ? a.probf[B.traj_off + blk.j0 + lane] : 0.0f;
+        const long long base = P.off + (long long)blk.i0 * B.h + blk.j0 + lane;
+        unsigned long long cnt = 0, mass = 0, col_mass = 0;
+        unsigned col_hits = 0;
+        for (int r0 = 0; r0 < blk.rows; r0 += 8) {
+            int v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = col_ok && r0 + u < blk.rows ? a.first32[base + (long long)(r0 + u) * B.h] : 0x7fffffff;
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) any |= v[u] != 0x7fffffff;
+            if (!__ballot_sync(0xffffffffu, any)) {          // no hit in these 8 rows
+                if (col_ok)
+                    for (int u = 0; u < 8 && r0 + u < blk.rows; ++u) a.table[base + (long long)(r0 + u) * B.h] = -1;
+                continue;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int r = r0 + u;
+                if (r >= blk.rows) break;                     // uniform over the warp
+                const int k = v[u] == 0x7fffffff ? -1 : v[u];
+                if (col_ok) a.table[base + (long long)r * B.h] = (int16_t)k;
+                const bool hit = k >= 0;
+                if (!risk || !__ballot_sync(0xffffffffu, hit)) continue;
+                const float pa = a.probf[A.traj_off + blk.i0 + r];
+                unsigned long long row_mass = 0;
+                if (hit) {
+                    const unsigned long long w = to_fixed(pa * pb, kFixProb);
+                    ++cnt;
+                    mass += w;
+                    atomicAdd(a.acc.count_k + P.kofs + k, 1ull);
+                    atomicAdd(a.acc.H + P.kofs + k, w);
+                    if (P.ego_side >= 0) {
+                        const long long e = P.ego_side == 0 ? blk.i0 + r : blk.j0 + lane;   // the EGO hypothesis
+                        const float pco = P.ego_side == 0 ? pb : pa;                        // the CO hypothesis
+                        atomicAdd(a.acc.lsum + P.lsum_base + (e * N + k) * P.n_obj_s + P.co_local,
+                                  to_fixed(neg_log_survival(pco), kFixLog));
+                        if (P.ego_side == 0) {
+                            row_mass = to_fixed(pco, kFixProb);
+                        } else {
+                            col_mass += to_fixed(pco, kFixProb);
+                            ++col_hits;
+                        }
+                    }
+                }
+                if (P.ego_side == 0) {   // the row's EGO hypothesis: its CO mass and hit count over the row
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) row_mass += __shfl_xor_sync(0xffffffffu, row_mass, d);
+                    const unsigned hits = __popc(__ballot_sync(0xffffffffu, hit));
+                    if (lane == 0) {
+                        const long long e = blk.i0 + r;
+                        atomicAdd(a.acc.mass + P.mass_base + e * P.n_obj_s + P.co_local, row_mass);
+                        atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)hits);
+                    }
+                }
+            }
+        }
+        if (!risk) continue;
+        if (P.ego_side == 1 && col_hits) {
+            const long long e = blk.j0 + lane;
+            atomicAdd(a.acc.mass + P.mass_base + e * P.n_obj_s + P.co_local, col_mass);
+            atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)col_hits);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+            mass += __shfl_xor_sync(0xffffffffu, mass, d);
+        }
+        if (lane == 0 && cnt) {
+            atomicAdd(a.acc.count + P.index, cnt);
+            atomicAdd(a.acc.P + P.index, mass);
+        }
+    }
+}
+
 // table[0, n) = -1 (no collision), 16-byte stores on the aligned body
 __global__ void __launch_bounds__(256) fill_kernel(int16_t *table, long long n) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -999,6 +1270,21 @@ cudaError_t launch_tile_variant(const CollideArgs &a, cudaStream_t st) {
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (a.variant == 6) {   // the caller zeroed *item_count and sized items and first32
+        if (!a.items || !a.item_count || !a.first32 || !a.active || !a.active_count || a.n_tiles * 4 > 0x7fffffffLL)
+            return cudaErrorInvalidValue;
+        long long blocks = (a.n_tiles * 4 + 3) / 4;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        items_list_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        int n_sm = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        items_kernel<<<(unsigned)(32 * n_sm), 32, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        items_table_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);   // over the active blocks only
+        return cudaGetLastError();
+    }
     if (a.variant == 4)
         return a.probf ? launch_tile_variant<4, 64, true>(a, st) : launch_tile_variant<4, 64, false>(a, st);
     if (a.variant == 5)   // one warp per CTA: a finished warp frees its slot at once (small, uneven grids)

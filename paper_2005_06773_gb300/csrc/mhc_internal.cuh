@@ -21,7 +21,7 @@ constexpr float kVMin = 2.0f;      // below this speed the one-track model gives
 constexpr double kVMinD = 2.0;
 
 constexpr int kTile = 64;           // collision tile edge (hypotheses per side)
-constexpr int kCollideVariants = 5; // thread layouts of the collision kernel (MHC_OPT_COLLIDE_VARIANT 1..5)
+constexpr int kCollideVariants = 6; // thread layouts of the collision kernel (MHC_OPT_COLLIDE_VARIANT 1..6)
 constexpr int kBoundTile = 32;     // hypotheses per bounding-box tile (one warp)
 constexpr int16_t kNoHit = 0x7fff; // in-kernel sentinel, stored as -1
 
@@ -156,6 +156,13 @@ struct CollideArgs {
     int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
     int fill_blocks;          // 1: each warp writes -1 to its own block first (variant 5; no fill launch)
     int max_ctas;             // > 0: at most this many CTAs for variants 4, 5 (the warps loop over the blocks)
+    // variant 6: the item list (active (block, step) pairs) and its length, zeroed by the caller
+    int2 *items;
+    unsigned long long *item_count;
+    int *first32;             // [n_entries] first overlapping step per table entry (INT_MAX: none)
+    int *active;              // [4 n_tiles] blocks with at least one active step, and their number (zeroed)
+    unsigned long long *active_count;
+    long long max_items;      // capacity: 4 n_tiles x max_steps
     int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile, 5: warp per quarter tile
     const float *x, *y, *c, *s;
     const float4 *bounds;
@@ -217,6 +224,6 @@ cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);              
 cudaError_t launch_risk_prepare(const RiskArgs &a, cudaStream_t st);             // zero + normalise
 int risk_tail_launches(const RiskArgs &a);   // kernels launch_risk_tail launches
 cudaError_t launch_risk_tail(const RiskArgs &a, cudaStream_t st);                // ego walk + finish
-cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st);
+cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st, bool with_prepare = true);
 
 }  // namespace mhc

@@ -363,8 +363,8 @@ cudaError_t launch_risk_tail(const RiskArgs &args, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st) {
-    cudaError_t e = launch_risk_prepare(a, st);
+cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st, bool with_prepare) {
+    cudaError_t e = with_prepare ? launch_risk_prepare(a, st) : cudaSuccess;
     if (e != cudaSuccess) return e;
     if (a.n_tiles > 0) {
         if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;

@@ -24,6 +24,8 @@ constexpr size_t kAlign = 256;
 constexpr size_t kReserved = 4096;    // persistent words at the start of the arena (counters)
 constexpr int kSlots = 4;
 constexpr long long kFillInCollideMax = 1LL << 25;   // table entries up to which the collision kernel fills
+constexpr long long kItemsMax = 1LL << 22;             // step items (8 B each) up to which variant 6 applies
+constexpr long long kItemsMaxEntries = 1LL << 26;      // and table entries (4 B of first-step scratch each)
 constexpr long long kGenScanMaxTraj = 4096;           // a scenario's hypotheses up to which generation is parallel in time
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
@@ -55,10 +57,11 @@ int build_layout(const mhc_scenario *sc, int n_scen, Layout &L);
 int build_layout(const mhc_scenario *sc, Layout &L);
 void plan_generation(Layout &L, int n_sm, int mode);   // mode: MHC_OPT_GEN_SCAN
 long long acc_words(const Layout &L);
+bool items_eligible(const Layout &L);
 
 // Device scratch each call needs (besides caller buffers).
 struct Scratch {
-    size_t desc = 0, bounds = 0, prob = 0, acc = 0, weights = 0, total = 0;
+    size_t desc = 0, bounds = 0, prob = 0, acc = 0, weights = 0, items = 0, total = 0;
     long long acc_words = 0;
 };
 

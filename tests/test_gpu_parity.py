@@ -199,7 +199,7 @@ def test_collision_variants_agree(mhc, ctx, name):
     p = mhc.generate(ctx, sc)
     ref_t, ref_r = None, None
     try:
-        for variant in (1, 2, 3, 4, 5):
+        for variant in (1, 2, 3, 4, 5, 6):
             for cull in (1, 0):
                 ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, variant)
                 ctx.set_option(mhc.MHC_OPT_CULL, cull)
@@ -227,7 +227,7 @@ def test_autotune_picks_a_layout_and_keeps_results(mhc):
         p = mhc.generate(c, sc)
         before = mhc.detect(c, sc, p).clone()
         v, cull = mhc.autotune(c, sc, p)
-        assert v in (1, 2, 3, 4, 5) and cull in (0, 1)
+        assert v in (1, 2, 3, 4, 5, 6) and cull in (0, 1)
         after = mhc.detect(c, sc, p)
         torch.cuda.synchronize()
         assert torch.equal(before, after)
