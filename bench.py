@@ -582,15 +582,17 @@ def run_mhc(args):
 
     # end to end through mhc_run: host scenario in, host (pinned) risk out, copies inside the timed region
     host_out = mhc.alloc_risk(cs, device="cpu", pin=True)
+    host_struct = mhc.risk_struct(host_out)
     e2e_ctx = mhc.Context(local, max(lay["run_bytes"] + (64 << 20), 256 << 20))
+    raw_stream = stream.cuda_stream
     for _ in range(3):
-        mhc.run(e2e_ctx, cs, out=host_out, stream=stream)
+        mhc.run(e2e_ctx, cs, out=host_out, stream=raw_stream, out_struct=host_struct)
     e2e_ms = []
     for _ in range(args.e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        mhc.run(e2e_ctx, cs, out=host_out, stream=stream)
+        mhc.run(e2e_ctx, cs, out=host_out, stream=raw_stream, out_struct=host_struct)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     h2d, d2h = e2e_ctx.transfer_bytes()
     e2e_ctx.close()

@@ -202,7 +202,7 @@ enum { MHC_K_GENERATE = 0, MHC_K_BOUNDS = 1, MHC_K_COLLIDE = 2, MHC_K_RISK = 3, 
 int mhc_profile_read(mhc_ctx *ctx, double ms[4], int64_t launches[4], int reset);
 
 /* Bytes the most recent call on this context copied host->device (descriptors, weights) and
-   device->host (mhc_run outputs). */
+   device->host (mhc_run: its whole output block, one copy). */
 int mhc_transfer_bytes(mhc_ctx *ctx, int64_t *h2d, int64_t *d2h);
 
 /*

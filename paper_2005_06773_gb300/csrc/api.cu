@@ -656,6 +656,7 @@ void mhc_destroy(mhc_ctx *c) {
         if (c->stage_ev[s]) cudaEventDestroy(c->stage_ev[s]);
         if (c->stage[s]) cudaFreeHost(c->stage[s]);
     }
+    if (c->out_stage) cudaFreeHost(c->out_stage);
     if (c->done_ev) cudaEventDestroy(c->done_ev);
     for (auto &t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -960,19 +961,30 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     DevDesc D;
     if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
     if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st, true)) return r;
+    // the outputs are contiguous in the arena: one copy into pinned staging, then to the caller's arrays
+    const size_t out_bytes = risk_output_bytes(L);
+    if (ctx->out_stage_cap < out_bytes) {
+        if (ctx->out_stage) MHC_CUDA(cudaFreeHost(ctx->out_stage));
+        ctx->out_stage = nullptr;
+        ctx->out_stage_cap = 0;
+        const size_t cap = out_bytes < (1u << 20) ? (1u << 20) : 2 * out_bytes;
+        MHC_CUDA(cudaHostAlloc(&ctx->out_stage, cap, cudaHostAllocDefault));
+        ctx->out_stage_cap = cap;
+    }
+    MHC_CUDA(cudaMemcpyAsync(ctx->out_stage, R.count, out_bytes, cudaMemcpyDeviceToHost, st));
+    ctx->d2h = (long long)out_bytes;
+    if (int r = end_call(ctx, st)) return r;
+    MHC_CUDA(cudaStreamSynchronize(st));
+    const char *h = static_cast<const char *>(ctx->out_stage);
+    auto at = [&](const void *dev_field) { return h + (static_cast<const char *>(dev_field) - reinterpret_cast<const char *>(R.count)); };
     struct Cp { void *dst; const void *src; size_t n; } cps[] = {
         {out->count, R.count, 8 * np}, {out->count_k, R.count_k, 8 * nk}, {out->P, R.P, 8 * np},
         {out->H, R.H, 8 * nk}, {out->naive, R.naive, 8 * he}, {out->cond, R.cond, 8 * he},
         {out->indep, R.indep, 8 * he}, {out->hits, R.hits, 4 * he}, {out->attr_obj, R.attr_obj, 8 * no},
         {out->attr_step, R.attr_step, 8 * (size_t)L.n_steps_total}, {out->scalars, R.scalars, 8 * 4 * ns},
         {out->escape, R.escape, 4 * he}, {out->n_escape, R.n_escape, 4 * ns}};
-    for (const Cp &c : cps) {
-        if (!c.dst) continue;
-        MHC_CUDA(cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, st));
-        ctx->d2h += (long long)c.n;
-    }
-    if (int r = end_call(ctx, st)) return r;
-    MHC_CUDA(cudaStreamSynchronize(st));
+    for (const Cp &c : cps)
+        if (c.dst && c.n) std::memcpy(c.dst, at(c.src), c.n);
     return MHC_OK;
 }
 

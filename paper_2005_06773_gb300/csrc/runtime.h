@@ -127,6 +127,8 @@ struct mhc_ctx {
     long long prof_n[MHC_K_COUNT] = {};
     long long h2d = 0, d2h = 0;
     void *server = nullptr;          // the serving loop (serve.cu), if started
+    void *out_stage = nullptr;       // pinned staging of mhc_run's outputs
+    size_t out_stage_cap = 0;
 };
 
 namespace mhc {

@@ -373,14 +373,20 @@ def evaluate(ctx: Context, sc, poses=None, table=None, weights=None, out=None, s
     return poses, table, out
 
 
-def run(ctx: Context, sc, weights=None, out=None, stream=None) -> Dict[str, torch.Tensor]:
-    """Host inputs -> host risk outputs through mhc_run (synchronises the stream)."""
+def run(ctx: Context, sc, weights=None, out=None, stream=None, out_struct=None) -> Dict[str, torch.Tensor]:
+    """Host inputs -> host risk outputs through mhc_run (synchronises the stream).  `out_struct` may carry
+    the prebuilt MhcRisk of `out` (risk_struct(out)) to skip rebuilding it on every call."""
     cs = as_c(sc)
     out = alloc_risk(cs, device="cpu", pin=True) if out is None else out
-    rs = _risk_struct(out)
-    w = weights if isinstance(weights, CWeights) else CWeights(weights)
-    _check(lib.mhc_run(ctx.h, cs.ref, w.ptr, ctypes.byref(rs), _stream(stream)), "mhc_run")
+    rs = out_struct if out_struct is not None else _risk_struct(out)
+    wptr = None if weights is None else (weights if isinstance(weights, CWeights) else CWeights(weights)).ptr
+    _check(lib.mhc_run(ctx.h, cs.ref, wptr, ctypes.byref(rs), _stream(stream)), "mhc_run")
     return out
+
+
+def risk_struct(out: Dict[str, torch.Tensor]) -> MhcRisk:
+    """The C struct of a dict of risk output buffers (for repeated calls)."""
+    return _risk_struct(out)
 
 
 def poses_by_trajectory(sc, plane: torch.Tensor) -> np.ndarray:
