@@ -74,12 +74,20 @@ def _scenes():
     sc = S.intersection11(8, n_steps=1, n_acc=4, n_str=4, n_ped_v=3, n_ped_h=3)
     sc.name = "one_step"
     out[sc.name] = sc
+    # long horizons: more than 160 steps (the fused per-CTA survival cells give way to global atomics) and
+    # more than 1024 (so do the per-CTA step histograms); many 32-step activity words in every layout
+    sc = S.intersection11(12, n_steps=1200, n_acc=3, n_str=3, n_ped_v=2, n_ped_h=3)
+    sc.tau, sc.substeps, sc.name = S.F32(0.01), 1, "long_n1200"
+    out[sc.name] = sc
+    sc = S.intersection11(13, n_steps=300, n_acc=4, n_str=5, n_ped_v=3, n_ped_h=3)
+    sc.pair_mode, sc.ego, sc.tau, sc.substeps, sc.name = S.EGO_ONLY, 1, S.F32(0.02), 2, "ego_only_n300"
+    out[sc.name] = sc
     return out
 
 
 _CACHE = {}
 SCENE_NAMES = ["tiny", "tiny_near", "mixed_small", "ragged", "ped_accel", "paper_s1", "ego_only_ego2_n70",
-               "kinematic", "one_step"]
+               "kinematic", "one_step", "long_n1200", "ego_only_n300"]
 
 
 def scene(name):
@@ -191,7 +199,8 @@ def test_fused_evaluate_equals_separate_calls(mhc, ctx, name):
             np.testing.assert_array_equal(a, b, err_msg=k)
 
 
-@pytest.mark.parametrize("name", ["mixed_small", "ragged", "ego_only_ego2_n70", "paper_s1", "kinematic"])
+@pytest.mark.parametrize("name", ["mixed_small", "ragged", "ego_only_ego2_n70", "paper_s1", "kinematic", "long_n1200",
+                                  "ego_only_n300"])
 def test_collision_variants_agree(mhc, ctx, name):
     """Every thread layout of the collision kernel (and culling on / off) gives the same table and, fused,
     the same risk outputs."""
