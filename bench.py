@@ -191,6 +191,78 @@ def cpu_baseline(sc, budget_s: float):
             "seconds": dt}
 
 
+_ORACLE_STATE = {}
+
+
+def _oracle_pool_init(root, sc, poses):
+    sys.path.insert(0, root)
+    from oracle import oracle
+    _ORACLE_STATE.update(oracle=oracle, sc=sc, poses=poses)
+
+
+def _oracle_pool_task(chunk):
+    o = _ORACLE_STATE["oracle"]
+    return int((o.first_steps(_ORACLE_STATE["sc"], _ORACLE_STATE["poses"], *chunk) >= 0).sum())
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_oracle_cores(sc, n_pairs: int, seed: int = 7):
+    """The oracle's first-collision steps (its functions unchanged) on n_pairs random trajectory pairs of the
+    scene (or all of them), on one host thread and on every core (a spawn-started process pool over slices
+    of the pairs): pose tests per second each way."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import oracle
+    oracle.build()
+    poses = oracle.generate(sc)
+    off = oracle.traj_offsets(sc)
+    pairs = oracle.pair_list(sc)
+    h = np.diff(off)
+    sizes = np.array([h[a] * h[b] for a, b in pairs], dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    if n_pairs >= sizes.sum():           # every trajectory pair of the scene
+        oa, ta, ob, tb = [], [], [], []
+        for a, b in pairs:
+            i, j = np.meshgrid(np.arange(h[a]), np.arange(h[b]), indexing="ij")
+            oa.append(np.full(i.size, a)); ob.append(np.full(i.size, b))
+            ta.append(off[a] + i.ravel()); tb.append(off[b] + j.ravel())
+        oa, ta, ob, tb = (np.concatenate(v) for v in (oa, ta, ob, tb))
+        what = f"all {oa.size} trajectory pairs"
+    else:
+        q = rng.choice(len(pairs), size=n_pairs, p=sizes / sizes.sum())
+        oa = np.array([pairs[x][0] for x in q]); ob = np.array([pairs[x][1] for x in q])
+        ta = off[oa] + (rng.random(n_pairs) * h[oa]).astype(np.int64)
+        tb = off[ob] + (rng.random(n_pairs) * h[ob]).astype(np.int64)
+        what = f"{n_pairs} random trajectory pairs"
+    tests = oa.size * sc.n_steps
+    t0 = time.perf_counter()
+    oracle.first_steps(sc, poses, oa, ta, ob, tb)
+    t1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    chunks = [(oa[s], ta[s], ob[s], tb[s]) for s in np.array_split(np.arange(oa.size), 4 * cores)]
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"),
+                                initializer=_oracle_pool_init, initargs=(ROOT, sc, poses)) as ex:
+        list(ex.map(_oracle_pool_task, chunks[:cores]))          # workers started and warm
+        t0 = time.perf_counter()
+        list(ex.map(_oracle_pool_task, chunks))
+        tn = time.perf_counter() - t0
+    return {"tests": tests, "sample": what + f" x {sc.n_steps} steps (first-collision steps only)",
+            "one_thread_tests_per_s": tests / t1, "all_cores_tests_per_s": tests / tn, "cores": cores,
+            "cpu": cpu_model()}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, each step a bounded random sample of the
     scene's trajectory pairs (plus the full trajectory generation)."""
@@ -647,6 +719,11 @@ def run_mhc(args):
         line["serving"] = measure_serving(mhc, torch, dev, args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD == "intersection11":
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+        # the oracle on every host core as well (the whole table of the scene), and on a sample of the
+        # 32-vehicle stress scene
+        line["cpu_oracle_cores"] = {"intersection11": cpu_oracle_cores(sc, 1 << 40),
+                                    "stress32": cpu_oracle_cores(__import__("paper_2005_06773_gb300.scenarios",
+                                                                            fromlist=["x"]).stress32(4), 2_000_000)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
