@@ -190,10 +190,17 @@ int orc_generate(int n_obj, const int *kind, const double *x0, const double *y0,
  * ------------------------------------------------------------------------------------------------ */
 
 typedef struct {
-    int kind;            /* 0 rectangle, 1 disc */
+    int kind;            /* 0 rectangle, 1 disc, 2 convex polygon */
     double hl, hw, rad;  /* half length, half width, radius */
     double x, y, c, s;   /* centre, body axis (c, s) */
+    int nv;              /* polygon: vertex count and body-frame vertices (x along the body axis) */
+    const double *pv;
 } shape;
+
+#define MAX_VERTICES 16
+
+/* World vertices of a rectangle (its four corners) or polygon; returns their number. */
+static int world_vertices(const shape *p, double *wx, double *wy);
 
 static double dot2(double ax, double ay, double bx, double by) { return ax * bx + ay * by; }
 
@@ -275,8 +282,88 @@ static double disc_disc_margin(const shape *a, const shape *b) {
     return sqrt(dx * dx + dy * dy) - a->rad - b->rad;
 }
 
+static int world_vertices(const shape *p, double *wx, double *wy) {
+    if (p->kind == 0) {
+        corners(p, wx, wy);
+        return 4;
+    }
+    for (int q = 0; q < p->nv; ++q) {
+        double vx = p->pv[2 * q], vy = p->pv[2 * q + 1];
+        wx[q] = p->x + p->c * vx - p->s * vy;
+        wy[q] = p->y + p->s * vx + p->c * vy;
+    }
+    return p->nv;
+}
+
+/* Separating-axis gap of two convex polygons (or rectangles): the largest separation between their
+   projections over all edge normals of both.  <= 0 iff the closed polygons intersect. */
+static double poly_poly_gap(const shape *a, const shape *b) {
+    double ax[MAX_VERTICES], ay[MAX_VERTICES], bx[MAX_VERTICES], by[MAX_VERTICES];
+    int na = world_vertices(a, ax, ay), nb = world_vertices(b, bx, by);
+    double best = -INFINITY;
+    for (int side = 0; side < 2; ++side) {
+        const double *px = side ? bx : ax, *py = side ? by : ay;
+        int n = side ? nb : na;
+        for (int e = 0; e < n; ++e) {
+            int f = (e + 1) % n;
+            double nx = -(py[f] - py[e]), ny = px[f] - px[e];
+            double len = sqrt(nx * nx + ny * ny);
+            nx /= len; ny /= len;
+            double amin = INFINITY, amax = -INFINITY, bmin = INFINITY, bmax = -INFINITY;
+            for (int q = 0; q < na; ++q) { double t = dot2(ax[q], ay[q], nx, ny); amin = fmin(amin, t); amax = fmax(amax, t); }
+            for (int q = 0; q < nb; ++q) { double t = dot2(bx[q], by[q], nx, ny); bmin = fmin(bmin, t); bmax = fmax(bmax, t); }
+            double gap = fmax(bmin - amax, amin - bmax);
+            if (gap > best) best = gap;
+        }
+    }
+    return best;
+}
+
+/* Euclidean distance of two disjoint convex polygons: the smallest vertex-to-edge distance, both ways. */
+static double poly_poly_distance(const shape *a, const shape *b) {
+    double ax[MAX_VERTICES], ay[MAX_VERTICES], bx[MAX_VERTICES], by[MAX_VERTICES];
+    int na = world_vertices(a, ax, ay), nb = world_vertices(b, bx, by);
+    double best = INFINITY;
+    for (int i = 0; i < na; ++i)
+        for (int e = 0; e < nb; ++e) {
+            double d = point_segment_dist(ax[i], ay[i], bx[e], by[e], bx[(e + 1) % nb], by[(e + 1) % nb]);
+            if (d < best) best = d;
+        }
+    for (int i = 0; i < nb; ++i)
+        for (int e = 0; e < na; ++e) {
+            double d = point_segment_dist(bx[i], by[i], ax[e], ay[e], ax[(e + 1) % na], ay[(e + 1) % na]);
+            if (d < best) best = d;
+        }
+    return best;
+}
+
+/* Signed margin of convex polygon a and disc b: the centre's distance to the outline minus the radius,
+   the distance counted negative when the centre lies inside. */
+static double poly_disc_margin(const shape *a, const shape *b) {
+    double ax[MAX_VERTICES], ay[MAX_VERTICES];
+    int n = world_vertices(a, ax, ay);
+    double dmin = INFINITY;
+    int pos = 0, neg = 0;
+    for (int e = 0; e < n; ++e) {
+        int f = (e + 1) % n;
+        double cr = (ax[f] - ax[e]) * (b->y - ay[e]) - (ay[f] - ay[e]) * (b->x - ax[e]);
+        if (cr > 0.0) ++pos;
+        if (cr < 0.0) ++neg;
+        double d = point_segment_dist(b->x, b->y, ax[e], ay[e], ax[f], ay[f]);
+        if (d < dmin) dmin = d;
+    }
+    int inside = pos == 0 || neg == 0;      /* on one side of every edge (or on the outline) */
+    return (inside ? -dmin : dmin) - b->rad;
+}
+
 /* Exact signed separation margin: > 0 disjoint (Euclidean distance), <= 0 overlapping. */
 static double shape_margin(const shape *a, const shape *b) {
+    if (a->kind == 2 || b->kind == 2) {
+        if (a->kind == 1) return poly_disc_margin(b, a);
+        if (b->kind == 1) return poly_disc_margin(a, b);
+        double g = poly_poly_gap(a, b);
+        return g <= 0.0 ? g : poly_poly_distance(a, b);
+    }
     if (a->kind == 0 && b->kind == 0) {
         double g = rect_rect_gap(a, b);
         return g <= 0.0 ? g : rect_rect_distance(a, b);
@@ -289,6 +376,7 @@ static double shape_margin(const shape *a, const shape *b) {
 /* Overlap flag (margin <= 0) without computing the full distance of disjoint rectangles. */
 static int shape_overlap(const shape *a, const shape *b) {
     if (a->kind == 0 && b->kind == 0) return rect_rect_gap(a, b) <= 0.0;
+    if ((a->kind == 2 && b->kind != 1) || (b->kind == 2 && a->kind != 1)) return poly_poly_gap(a, b) <= 0.0;
     return shape_margin(a, b) <= 0.0;
 }
 
@@ -312,6 +400,31 @@ static shape make_shape(int kind, double length, double width, double radius,
     shape p;
     p.kind = kind; p.hl = length / 2.0; p.hw = width / 2.0; p.rad = radius;
     p.x = x; p.y = y; p.c = c; p.s = s;
+    p.nv = 0; p.pv = 0;
+    return p;
+}
+
+/* Polygon outlines of the objects (set by orc_set_polygons; none by default): object o with nv[o] > 0 has
+   the convex outline verts[2 * off[o] ..] (body frame) and shape kind 2. */
+static int g_poly_n = 0;
+static const int *g_poly_nv = 0;
+static const long *g_poly_off = 0;
+static const double *g_poly_v = 0;
+
+int orc_set_polygons(int n_obj, const int *nv, const long *off, const double *verts) {
+    g_poly_n = n_obj; g_poly_nv = nv; g_poly_off = off; g_poly_v = verts;
+    return 0;
+}
+
+/* The shape of object o (its polygon outline when one is set). */
+static shape object_shape(int o, int kind, double length, double width, double radius,
+                          double x, double y, double c, double s) {
+    shape p = make_shape(kind, length, width, radius, x, y, c, s);
+    if (g_poly_nv && o < g_poly_n && g_poly_nv[o] > 0) {
+        p.kind = 2;
+        p.nv = g_poly_nv[o];
+        p.pv = g_poly_v + 2 * g_poly_off[o];
+    }
     return p;
 }
 
@@ -319,6 +432,20 @@ double orc_margin(int kind_a, double len_a, double wid_a, double rad_a, double x
                   int kind_b, double len_b, double wid_b, double rad_b, double xb, double yb, double cb, double sb) {
     shape a = make_shape(kind_a, len_a, wid_a, rad_a, xa, ya, ca, sa);
     shape b = make_shape(kind_b, len_b, wid_b, rad_b, xb, yb, cb, sb);
+    return shape_margin(&a, &b);
+}
+
+/* Signed margin (and, *overlap, the closed overlap flag) of two shapes given directly: kind 0 rectangle
+   (len, wid), 1 disc (rad), 2 convex polygon (nv body-frame vertices v[2 nv]). */
+double orc_margin_shapes(int kind_a, double len_a, double wid_a, double rad_a, int nv_a, const double *va,
+                         double xa, double ya, double ca, double sa,
+                         int kind_b, double len_b, double wid_b, double rad_b, int nv_b, const double *vb,
+                         double xb, double yb, double cb, double sb, int *overlap) {
+    shape a = make_shape(kind_a, len_a, wid_a, rad_a, xa, ya, ca, sa);
+    shape b = make_shape(kind_b, len_b, wid_b, rad_b, xb, yb, cb, sb);
+    a.nv = nv_a; a.pv = va;
+    b.nv = nv_b; b.pv = vb;
+    if (overlap) *overlap = shape_overlap(&a, &b);
     return shape_margin(&a, &b);
 }
 
@@ -349,8 +476,8 @@ int orc_table(int n_obj, const int *kind, const double *length, const double *wi
                 int first = -1;
                 for (int k = 0; k < n_steps; ++k) {
                     long ia = ta * n_steps + k, ib = tb * n_steps + k;
-                    shape sa = make_shape(kind[a], length[a], width[a], radius[a], px[ia], py[ia], pc[ia], ps[ia]);
-                    shape sb = make_shape(kind[b], length[b], width[b], radius[b], px[ib], py[ib], pc[ib], ps[ib]);
+                    shape sa = object_shape(a, kind[a], length[a], width[a], radius[a], px[ia], py[ia], pc[ia], ps[ia]);
+                    shape sb = object_shape(b, kind[b], length[b], width[b], radius[b], px[ib], py[ib], pc[ib], ps[ib]);
                     if (shape_overlap(&sa, &sb)) { first = k; break; }
                 }
                 out[pair_off[p] + i * hb + j] = (int16_t)first;
@@ -369,8 +496,8 @@ int orc_first(const int *kind, const double *length, const double *width, const 
         int a = oa[q], b = ob[q], first = -1;
         for (int k = 0; k < n_steps; ++k) {
             long ia = ta[q] * n_steps + k, ib = tb[q] * n_steps + k;
-            shape sa = make_shape(kind[a], length[a], width[a], radius[a], px[ia], py[ia], pc[ia], ps[ia]);
-            shape sb = make_shape(kind[b], length[b], width[b], radius[b], px[ib], py[ib], pc[ib], ps[ib]);
+            shape sa = object_shape(a, kind[a], length[a], width[a], radius[a], px[ia], py[ia], pc[ia], ps[ia]);
+            shape sb = object_shape(b, kind[b], length[b], width[b], radius[b], px[ib], py[ib], pc[ib], ps[ib]);
             if (shape_overlap(&sa, &sb)) { first = k; break; }
         }
         out[q] = (int16_t)first;
@@ -387,8 +514,8 @@ int orc_margins(const int *kind, const double *length, const double *width, cons
         int a = oa[q], b = ob[q];
         for (int k = 0; k < n_steps; ++k) {
             long ia = ta[q] * n_steps + k, ib = tb[q] * n_steps + k;
-            shape sa = make_shape(kind[a], length[a], width[a], radius[a], px[ia], py[ia], pc[ia], ps[ia]);
-            shape sb = make_shape(kind[b], length[b], width[b], radius[b], px[ib], py[ib], pc[ib], ps[ib]);
+            shape sa = object_shape(a, kind[a], length[a], width[a], radius[a], px[ia], py[ia], pc[ia], ps[ia]);
+            shape sb = object_shape(b, kind[b], length[b], width[b], radius[b], px[ib], py[ib], pc[ib], ps[ib]);
             margins[q * n_steps + k] = shape_margin(&sa, &sb);
         }
     }

@@ -53,6 +53,7 @@ def lib():
             _lib = ctypes.CDLL(build())
             _lib.orc_margin.restype = ctypes.c_double
             _lib.orc_margin.argtypes = [ctypes.c_int] + [ctypes.c_double] * 7 + [ctypes.c_int] + [ctypes.c_double] * 7
+            _lib.orc_margin_shapes.restype = ctypes.c_double
             _lib.orc_overlap_pip.restype = ctypes.c_int
             _lib.orc_overlap_pip.argtypes = [ctypes.c_double] * 12
     return _lib
@@ -128,6 +129,21 @@ def generate(sc) -> Dict[str, np.ndarray]:
     return dict(x=x, y=y, psi=psi, c=np.cos(psi), s=np.sin(psi), traj_off=off)
 
 
+def _set_polygons(sc):
+    """Registers the objects' convex outlines with the C oracle for the next call (none: cleared).
+    Returns the arrays, which must stay alive during that call."""
+    L = lib()
+    nv = _i32([0 if getattr(o, "outline", None) is None else len(o.outline) for o in sc.objects])
+    if not nv.any():
+        L.orc_set_polygons(ctypes.c_int(0), None, None, None)
+        return None
+    off = _i64(np.concatenate([[0], np.cumsum(nv.astype(np.int64))])[:-1])
+    verts = _f64(np.concatenate([np.asarray(o.outline, D).reshape(-1) for o in sc.objects
+                                 if getattr(o, "outline", None) is not None]))
+    L.orc_set_polygons(ctypes.c_int(len(sc.objects)), _p(nv, _ip), _p(off, _lp), _p(verts, _dp))
+    return nv, off, verts
+
+
 def table(sc, poses: Dict[str, np.ndarray], pairs=None) -> Tuple[np.ndarray, np.ndarray, list]:
     """First-collision step of every trajectory combination of every listed object pair (Section IV-C);
     -1 where the closed shapes never overlap within the horizon.  Returns (table, pair_off, pairs)."""
@@ -139,6 +155,7 @@ def table(sc, poses: Dict[str, np.ndarray], pairs=None) -> Tuple[np.ndarray, np.
     out = np.empty(int(poff[-1]), np.int16)
     pa = _i32([p[0] for p in pairs]); pb = _i32([p[1] for p in pairs])
     px, py, pc, ps = (_f64(poses[k]) for k in ("x", "y", "c", "s"))
+    keep = _set_polygons(sc)  # noqa: F841 (alive during the call)
     L.orc_table(ctypes.c_int(len(sc.objects)), _p(ob["kind"], _ip), _p(ob["length"], _dp), _p(ob["width"], _dp),
                 _p(ob["radius"], _dp), _p(off, _lp), ctypes.c_int(int(sc.n_steps)),
                 _p(px, _dp), _p(py, _dp), _p(pc, _dp), _p(ps, _dp), ctypes.c_int(len(pairs)),
@@ -156,6 +173,7 @@ def margins(sc, poses, oa, ta, ob_, tb) -> np.ndarray:
     N = int(sc.n_steps)
     out = np.empty((oa.size, N), D)
     px, py, pc, ps = (_f64(poses[k]) for k in ("x", "y", "c", "s"))
+    keep = _set_polygons(sc)  # noqa: F841 (alive during the call)
     L.orc_margins(_p(ob["kind"], _ip), _p(ob["length"], _dp), _p(ob["width"], _dp), _p(ob["radius"], _dp),
                   ctypes.c_int(N), _p(px, _dp), _p(py, _dp), _p(pc, _dp), _p(ps, _dp),
                   ctypes.c_long(oa.size), _p(oa, _ip), _p(ta, _lp), _p(ob_, _ip), _p(tb, _lp), _p(out, _dp))
@@ -170,6 +188,7 @@ def first_steps(sc, poses, oa, ta, ob_, tb) -> np.ndarray:
     ta, tb = _i64(ta), _i64(tb)
     out = np.empty(oa.size, np.int16)
     px, py, pc, ps = (_f64(poses[k]) for k in ("x", "y", "c", "s"))
+    keep = _set_polygons(sc)  # noqa: F841 (alive during the call)
     L.orc_first(_p(ob["kind"], _ip), _p(ob["length"], _dp), _p(ob["width"], _dp), _p(ob["radius"], _dp),
                 ctypes.c_int(int(sc.n_steps)), _p(px, _dp), _p(py, _dp), _p(pc, _dp), _p(ps, _dp),
                 ctypes.c_long(oa.size), _p(oa, _ip), _p(ta, _lp), _p(ob_, _ip), _p(tb, _lp), _p(out, _sp))
@@ -180,6 +199,23 @@ def margin(kind_a, len_a, wid_a, rad_a, xa, ya, psi_a, kind_b, len_b, wid_b, rad
     """Signed margin of two shapes (rectangle: kind 0, disc: kind 1) given centre and heading."""
     return lib().orc_margin(kind_a, len_a, wid_a, rad_a, xa, ya, np.cos(psi_a), np.sin(psi_a),
                             kind_b, len_b, wid_b, rad_b, xb, yb, np.cos(psi_b), np.sin(psi_b))
+
+
+def margin_shapes(a: dict, b: dict):
+    """Signed margin and closed overlap flag of two shapes given directly as dicts with kind (0 rectangle,
+    1 disc, 2 convex polygon), length, width, radius, outline ([n, 2] body frame), x, y, psi."""
+    L = lib()
+    args, keep = [], []
+    for d in (a, b):
+        v = _f64(np.asarray(d.get("outline", np.zeros((0, 2))), D).reshape(-1))
+        keep.append(v)
+        args += [ctypes.c_int(int(d["kind"])), ctypes.c_double(d.get("length", 0.0)), ctypes.c_double(d.get("width", 0.0)),
+                 ctypes.c_double(d.get("radius", 0.0)), ctypes.c_int(v.size // 2), _p(v, _dp),
+                 ctypes.c_double(d["x"]), ctypes.c_double(d["y"]), ctypes.c_double(np.cos(d["psi"])),
+                 ctypes.c_double(np.sin(d["psi"]))]
+    flag = ctypes.c_int(0)
+    m = L.orc_margin_shapes(*args, ctypes.byref(flag))
+    return float(m), bool(flag.value)
 
 
 def overlap_pip(len_a, wid_a, xa, ya, psi_a, len_b, wid_b, xb, yb, psi_b) -> bool:

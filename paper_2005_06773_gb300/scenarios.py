@@ -72,8 +72,9 @@ class SplitMix64:
 class Obj:
     """One traffic object and the control grid its hypotheses are sampled from.
 
-    Vehicles (rectangles centred on the pose point, body axis along psi): hypothesis h = i_a * n_b + i_b
-    uses acceleration grid_a[i_a] (m/s^2) and constant front steering angle grid_b[i_b] (rad).
+    Vehicles (rectangles centred on the pose point, body axis along psi, or the convex `outline` given in
+    the body frame): hypothesis h = i_a * n_b + i_b uses acceleration grid_a[i_a] (m/s^2) and constant
+    front steering angle grid_b[i_b] (rad).
     Pedestrians (discs): grid_a holds initial speeds (m/s) or, with PED_ACCEL_GRID, accelerations;
     grid_b holds heading offsets (rad) added to psi0.
     """
@@ -90,6 +91,7 @@ class Obj:
     params: Optional[np.ndarray] = None
     v_max: float = 0.0
     flags: int = 0
+    outline: Optional[np.ndarray] = None   # vehicles: convex outline, [n, 2] body-frame vertices (x ahead)
 
     def __post_init__(self):
         for f in ("length", "width", "radius", "x0", "y0", "psi0", "v0", "v_max"):
@@ -98,6 +100,8 @@ class Obj:
         self.grid_b = np.ascontiguousarray(self.grid_b, dtype=F32)
         if self.params is not None:
             self.params = np.ascontiguousarray(self.params, dtype=F32)
+        if self.outline is not None:
+            self.outline = np.ascontiguousarray(np.asarray(self.outline).reshape(-1, 2), dtype=F32)
 
     @property
     def n_hyp(self) -> int:
@@ -317,6 +321,26 @@ def paper_s1s2(n_co: int = 10, n_profiles: int = 6, seed: int = 6) -> Scenario:
 
 def uniform_weights(sc: Scenario) -> List[np.ndarray]:
     return [np.ones(o.n_hyp, dtype=F32) for o in sc.objects]
+
+
+def chamfered_outline(length: float, width: float, cut: float) -> np.ndarray:
+    """Octagon outline of a length x width body with every corner cut `cut` metres along both sides
+    (counter-clockwise, body frame, x ahead); cut = 0 gives the rectangle's corners."""
+    hl, hw = length / 2.0, width / 2.0
+    if cut <= 0.0:
+        return np.array([[hl, hw], [-hl, hw], [-hl, -hw], [hl, -hw]], dtype=F32)
+    return np.array([[hl, hw - cut], [hl - cut, hw], [-hl + cut, hw], [-hl, hw - cut],
+                     [-hl, -hw + cut], [-hl + cut, -hw], [hl - cut, -hw], [hl, -hw + cut]], dtype=F32)
+
+
+def with_outlines(sc: Scenario, cut: float = 0.35, every: int = 1) -> Scenario:
+    """The scenario with every `every`-th vehicle drawn as its chamfered outline instead of a rectangle."""
+    objs = []
+    for i, o in enumerate(sc.objects):
+        if o.kind == VEHICLE and i % every == 0:
+            o = dataclasses.replace(o, outline=chamfered_outline(o.length, o.width, cut))
+        objs.append(o)
+    return dataclasses.replace(sc, objects=objs, name=f"{sc.name}_outline{cut:g}")
 
 
 def random_weights(sc: Scenario, seed: int) -> List[np.ndarray]:
