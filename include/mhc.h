@@ -46,6 +46,7 @@ enum { MHC_MODEL_OT = 0, MHC_MODEL_KIN = 1 };     /* vehicle motion model */
 #define MHC_MAX_STEPS 32767                        /* first-collision steps are stored as int16 */
 #define MHC_MAX_OBJECTS 4096                       /* per scenario */
 #define MHC_MAX_SCENARIOS 65536                    /* per batch */
+#define MHC_MAX_VERTICES 16                        /* vertices of a vehicle's convex outline */
 
 /*
  * One traffic object and the control grid of its hypotheses (Section IV-B; a hypothesis is one
@@ -59,6 +60,14 @@ enum { MHC_MODEL_OT = 0, MHC_MODEL_KIN = 1 };     /* vehicle motion model */
  *       accelerations from initial speed v0, the speed then limited to [0, v_max] (v_max <= 0: no cap).
  *   veh_params: host pointer to {m, I_z, l_f, l_r, c_af, c_ar} (kg, kg m^2, m, m, N/rad, N/rad), or NULL
  *       for {1500, 2500, 1.2, 1.5, 80000, 80000}.  grid_a / grid_b are host pointers.
+ *   n_vertices / vertices (vehicles only; Section IV-C.1 lets an outline be as detailed as needed):
+ *       0 draws the vehicle as its length x width rectangle.  3..MHC_MAX_VERTICES draws it as the convex
+ *       polygon vertices[2 q], vertices[2 q + 1] (host, metres, body frame: x along the body axis, y to
+ *       the left, origin at the pose point), listed in either orientation; length and width stay
+ *       required but are not used for collisions.  The polygon must be strictly convex and simple (every
+ *       turn in the same direction, one turn in total): anything else, repeated vertices, non-finite
+ *       coordinates or an outline on a pedestrian returns MHC_E_INVALID.  The static entry point
+ *       (mhc_detect_collisions_static) takes rectangles only.
  */
 typedef struct {
     int32_t kind;
@@ -70,6 +79,8 @@ typedef struct {
     const float *grid_a;
     const float *grid_b;
     const float *veh_params;
+    int32_t n_vertices;
+    const float *vertices;
 } mhc_object;
 
 /*

@@ -59,6 +59,52 @@ Regime speed_regime(float v0f, float acc, int model, int NK, double tau_i_d) {
     return g;
 }
 
+// Validates the convex outline of a vehicle (Section IV-C.1: any outline detail) and appends it to `out`
+// counter-clockwise with the outward unit normal of each edge; `circ` receives its circumradius about the
+// pose point.  Returns an empty string, or the reason it is rejected.
+std::string append_outline(const float *v, int n, std::vector<PolyVertex> &out, float &circ) {
+    if (n < 3 || n > MHC_MAX_VERTICES) return "n_vertices must be 0 or in [3, 16]";
+    if (!v) return "vertices is NULL";
+    double x[MHC_MAX_VERTICES], y[MHC_MAX_VERTICES];
+    for (int q = 0; q < n; ++q) {
+        if (!finite(v[2 * q]) || !finite(v[2 * q + 1])) return "outline vertices must be finite";
+        x[q] = v[2 * q];
+        y[q] = v[2 * q + 1];
+    }
+    double area2 = 0.0;
+    for (int q = 0; q < n; ++q) area2 += x[q] * y[(q + 1) % n] - x[(q + 1) % n] * y[q];
+    if (!(std::fabs(area2) > 0.0)) return "outline has no area";
+    if (area2 < 0.0)   // clockwise: reverse
+        for (int q = 0; q < n / 2; ++q) { std::swap(x[q], x[n - 1 - q]); std::swap(y[q], y[n - 1 - q]); }
+    double turn = 0.0, r2 = 0.0;
+    for (int q = 0; q < n; ++q) {
+        const int q1 = (q + 1) % n, q2 = (q + 2) % n;
+        const double ex = x[q1] - x[q], ey = y[q1] - y[q], fx = x[q2] - x[q1], fy = y[q2] - y[q1];
+        const double le = std::hypot(ex, ey), lf = std::hypot(fx, fy);
+        if (!(le > 1e-6) || !(lf > 1e-6)) return "outline has repeated vertices";
+        const double cr = ex * fy - ey * fx;
+        if (!(cr > 1e-9 * le * lf)) return "outline is not strictly convex";
+        turn += std::atan2(cr, ex * fx + ey * fy);
+        r2 = std::max(r2, x[q] * x[q] + y[q] * y[q]);
+    }
+    if (std::fabs(turn - 6.283185307179586) > 1e-6) return "outline is not simple (it winds more than once)";
+    for (int q = 0; q < n; ++q) {
+        const int q1 = (q + 1) % n;
+        const double ex = x[q1] - x[q], ey = y[q1] - y[q], le = std::hypot(ex, ey);
+        out.push_back(make_float4((float)x[q], (float)y[q], (float)(ey / le), (float)(-ex / le)));
+    }
+    circ = (float)std::sqrt(r2);
+    return std::string();
+}
+
+// The rectangle of half extents hl x hw as a counter-clockwise 4-gon (for pairs with an outline).
+void append_rectangle(float hl, float hw, std::vector<PolyVertex> &out) {
+    out.push_back(make_float4(hl, -hw, 1.f, 0.f));
+    out.push_back(make_float4(hl, hw, 0.f, 1.f));
+    out.push_back(make_float4(-hl, hw, -1.f, 0.f));
+    out.push_back(make_float4(-hl, -hw, 0.f, -1.f));
+}
+
 // Validates scenario `si` and appends it to the layout.
 int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
     char sw[48] = "";
@@ -78,6 +124,10 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
     if (L.n_obj + n_obj_s > (1 << 24)) return fail(MHC_E_INVALID, "too many objects in the batch");
     if (N > L.max_steps) L.max_steps = N;
     static const float kDefault[6] = {1500.f, 2500.f, 1.2f, 1.5f, 80000.f, 80000.f};
+    // a scenario with any convex outline lists every vehicle's outline (rectangles as 4-gons)
+    bool any_outline = false;
+    for (int o = 0; o < n_obj_s; ++o) any_outline |= sc->objects[o].n_vertices != 0;
+    std::vector<char> outline(n_obj_s, 0);
     for (int o = 0; o < n_obj_s; ++o) {
         const mhc_object &src = sc->objects[o];
         ObjDesc d;
@@ -124,7 +174,19 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
             d.m = pp[0]; d.Iz = pp[1]; d.lf = pp[2]; d.lr = pp[3]; d.caf = pp[4]; d.car = pp[5];
             d.hl = 0.5f * src.length; d.hw = 0.5f * src.width; d.rad = 0.f;
             d.circ = (float)std::sqrt((double)d.hl * d.hl + (double)d.hw * d.hw);
+            if (any_outline) {
+                d.poly_off = (int)L.polys.size();
+                if (src.n_vertices != 0) {
+                    const std::string why = append_outline(src.vertices, src.n_vertices, L.polys, d.circ);
+                    if (!why.empty()) return fail(MHC_E_INVALID, std::string(where) + why);
+                    outline[o] = 1;
+                } else {
+                    append_rectangle(d.hl, d.hw, L.polys);
+                }
+                d.n_poly = (int)L.polys.size() - d.poly_off;
+            }
         } else {
+            if (src.n_vertices != 0) return fail(MHC_E_INVALID, std::string(where) + "pedestrians take no outline");
             if (!(src.radius > 0.f) || !finite(src.radius)) return fail(MHC_E_INVALID, std::string(where) + "pedestrian needs a positive radius");
             d.rad = src.radius; d.circ = src.radius;
         }
@@ -169,6 +231,9 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
         p.rc2 = (float)(R * R * (1.0 + 1e-6));
         p.r_cull = (float)(R * (1.0 + 1e-6) + 1e-3);
         p.combo = (A.kind == MHC_VEHICLE ? 0 : 2) + (B.kind == MHC_VEHICLE ? 0 : 1);
+        if (outline[la] || outline[lb]) p.combo = p.combo == 0 ? 4 : (p.combo == 1 ? 5 : 6);
+        p.poly_a = A.poly_off; p.nv_a = A.n_poly;
+        p.poly_b = B.poly_off; p.nv_b = B.n_poly;
         p.ego_side = la == sc->ego ? 0 : (lb == sc->ego ? 1 : -1);
         p.n_steps = N;
         p.scen = si;
@@ -280,7 +345,7 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
     s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + 2 * align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
              align_up(sizeof(ScenDesc) * L.scens.size()) + align_up(sizeof(float) * L.grids.size()) +
              2 * align_up(sizeof(int) * L.warp_obj.size()) + 2 * align_up(sizeof(int) * gen_tasks) +
-             align_up(sizeof(Regime) * L.regimes.size());
+             align_up(sizeof(Regime) * L.regimes.size()) + align_up(sizeof(PolyVertex) * L.polys.size());
     s.bounds = align_up(sizeof(float4) * (size_t)L.n_bounds);
     s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj);
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
@@ -319,7 +384,7 @@ int end_call(mhc_ctx *ctx, cudaStream_t st) {
 }
 
 size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char *host, char *dev, DevDesc &out) {
-    constexpr int kParts = 10;
+    constexpr int kParts = 11;
     const std::pair<const void *, size_t> parts[kParts] = {
         {L.objs.data(), sizeof(ObjDesc) * L.objs.size()},
         {L.pairs.data(), sizeof(PairDesc) * L.pairs.size()},
@@ -331,6 +396,7 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
         {L.gen_obj.data(), sizeof(int) * L.gen_obj.size()},
         {L.gen_first.data(), sizeof(int) * L.gen_first.size()},
         {L.regimes.data(), sizeof(Regime) * L.regimes.size()},
+        {L.polys.data(), sizeof(PolyVertex) * L.polys.size()},
     };
     size_t caps[kParts];
     for (int q = 0; q < kParts; ++q) caps[q] = align_up(parts[q].second);
@@ -358,6 +424,7 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
     out.gen_obj = reinterpret_cast<int *>(ptrs[7]);
     out.gen_first = reinterpret_cast<int *>(ptrs[8]);
     out.regimes = reinterpret_cast<Regime *>(ptrs[9]);
+    out.polys = L.polys.empty() ? nullptr : reinterpret_cast<PolyVertex *>(ptrs[10]);
     out.weights = weights ? reinterpret_cast<float *>(ptrs[kParts]) : nullptr;
     return off;
 }
@@ -561,7 +628,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         c.max_steps = L.max_steps; c.cull = cull; c.variant = variant; c.fill_blocks = fill_in_collide;
         c.max_ctas = ctx->collide_max_ctas;
         c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
-        c.bounds = bounds; c.table = table; c.counters = ctx->counters;
+        c.bounds = bounds; c.polys = D.polys; c.table = table; c.counters = ctx->counters;
         if (fused) {
             c.probf = r.probf;
             c.acc = r.acc;

@@ -48,6 +48,94 @@ __device__ __forceinline__ bool rect_disc(float dx, float dy, float c, float s, 
     return fmaf(ex, ex, ey * ey) <= r * r;
 }
 
+// Convex outlines (Section IV-C.1 lets an outline be as detailed as needed); in a pair with an outline a
+// plain rectangle comes as a 4-gon.  Two convex polygons are disjoint iff the supporting line of some edge
+// of one has the whole other polygon strictly on its outer side (the edges of their Minkowski difference
+// are the edges of the two), so each edge is one test: edge e of A (body-frame vertex v_e, outward unit
+// normal n_e, support h_e = n_e . v_e) separates iff min over B's vertices w of
+// (R_a n_e) . (d + R_b w) > h_e, d = p_b - p_a.  The normal is turned into B's frame once per edge and B's
+// vertices are read as stored.  Only the kernels instantiated for batches with outlines contain it.
+__device__ __forceinline__ bool outline_outline(float dx, float dy, float ca, float sa, float cb, float sb,
+                                               const PolyVertex *A, int na, const PolyVertex *B, int nb) {
+    const float cr = fmaf(ca, cb, sa * sb), sr = fmaf(sa, cb, -ca * sb);   // R_b^T R_a = R(psi_a - psi_b)
+    for (int e = 0; e < na; ++e) {
+        const float4 v = A[e];
+        const float h = fmaf(v.z, v.x, v.w * v.y);
+        const float nwx = fmaf(ca, v.z, -sa * v.w), nwy = fmaf(sa, v.z, ca * v.w);
+        const float o = fmaf(nwx, dx, nwy * dy);
+        const float mx = fmaf(cr, v.z, -sr * v.w), my = fmaf(sr, v.z, cr * v.w);
+        float lo = INFINITY;
+        for (int q = 0; q < nb; ++q) {
+            const float4 w = B[q];
+            lo = fminf(lo, fmaf(mx, w.x, my * w.y));
+        }
+        if (o + lo > h) return false;
+    }
+    for (int e = 0; e < nb; ++e) {   // B's edges: A's vertices relative to p_b are -d + R_a w
+        const float4 v = B[e];
+        const float h = fmaf(v.z, v.x, v.w * v.y);
+        const float nwx = fmaf(cb, v.z, -sb * v.w), nwy = fmaf(sb, v.z, cb * v.w);
+        const float o = -fmaf(nwx, dx, nwy * dy);
+        const float mx = fmaf(cr, v.z, sr * v.w), my = fmaf(-sr, v.z, cr * v.w);   // R_a^T R_b = R(psi_b - psi_a)
+        float lo = INFINITY;
+        for (int q = 0; q < na; ++q) {
+            const float4 w = A[q];
+            lo = fminf(lo, fmaf(mx, w.x, my * w.y));
+        }
+        if (o + lo > h) return false;
+    }
+    return true;
+}
+
+// Outline A at the origin of d (axis (c, s)) against a disc of radius r at offset d: the disc's centre in
+// A's frame lies inside A, or within r of one of its edges (segment distance).
+__device__ __forceinline__ bool outline_disc(float dx, float dy, float c, float s, const PolyVertex *A, int n,
+                                            float r) {
+    const float qx = fmaf(dx, c, dy * s), qy = fmaf(dy, c, -dx * s);
+    float smax = -INFINITY;
+    for (int e = 0; e < n; ++e) {
+        const float4 v = A[e];
+        smax = fmaxf(smax, fmaf(v.z, qx - v.x, v.w * (qy - v.y)));
+    }
+    if (smax > r) return false;   // beyond some edge's line by more than r
+    if (smax <= 0.0f) return true; // centre inside
+    float d2 = INFINITY;
+    for (int e = 0; e < n; ++e) {
+        const float4 v = A[e], w = A[e + 1 == n ? 0 : e + 1];
+        const float ex = w.x - v.x, ey = w.y - v.y, px = qx - v.x, py = qy - v.y;
+        const float t = fminf(fmaxf(fmaf(px, ex, py * ey) / fmaf(ex, ex, ey * ey), 0.0f), 1.0f);
+        const float rx = fmaf(-t, ex, px), ry = fmaf(-t, ey, py);
+        d2 = fminf(d2, fmaf(rx, rx, ry * ry));
+    }
+    return d2 <= r * r;
+}
+
+// The exact test of one broad-phase candidate: d = p_b - p_a, (ca, sa) / (cb, sb) the body axes, la / wa
+// and lb / wb the half extents of rectangles, ra / rb the radii of discs.  OUTL: the batch has outlines
+// (combos 4..6); the kernels without them keep the short rectangle and disc tests alone.
+template <bool OUTL>
+__device__ __forceinline__ bool narrow_hit(const PairDesc &P, const PolyVertex *polys, float dx, float dy,
+                                           float2 qa, float2 qb, float la, float wa, float lb, float wb,
+                                           float ra, float rb) {
+    if (!OUTL) {
+        switch (P.combo) {
+            case 0: return rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb);
+            case 1: return rect_disc(dx, dy, qa.x, qa.y, la, wa, rb);
+            case 2: return rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra);
+            default: return fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb);
+        }
+    }
+    switch (P.combo) {
+        case 0: return rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb);
+        case 1: return rect_disc(dx, dy, qa.x, qa.y, la, wa, rb);
+        case 2: return rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra);
+        case 3: return fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb);
+        case 4: return outline_outline(dx, dy, qa.x, qa.y, qb.x, qb.y, polys + P.poly_a, P.nv_a, polys + P.poly_b, P.nv_b);
+        case 5: return outline_disc(dx, dy, qa.x, qa.y, polys + P.poly_a, P.nv_a, rb);
+        default: return outline_disc(-dx, -dy, qb.x, qb.y, polys + P.poly_b, P.nv_b, ra);
+    }
+}
+
 constexpr int kMaxChunks = (32767 + 31) / 32;   // 32-step activity words for the longest horizon
 constexpr int kFusedHistSteps = 1024;            // per-CTA step histograms in shared memory up to this N
 constexpr int kFusedCellSteps = 160;             // per-CTA EGO survival cells (64 x N x 8 B) up to this N
@@ -67,7 +155,7 @@ __device__ __forceinline__ int next_active(const unsigned *mask, int n_chunks, i
 // THREADS threads per 64 x 64 tile, each testing an MI x MJ micro-tile (rows ti + TI m, columns tj + TJ n).
 // The tile's active steps are taken CH at a time: all their poses are staged into shared memory with
 // every load in flight at once, then each warp runs through the CH steps without further barriers.
-template <int THREADS, int MI, int MJ, int CH, bool FUSED>
+template <int THREADS, int MI, int MJ, int CH, bool FUSED, bool OUTL>
 __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
     constexpr int TI = kTile / MI, TJ = kTile / MJ;
     static_assert(TI * TJ == THREADS, "micro-tiles must cover the tile");
@@ -266,13 +354,7 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
                 const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                 const float2 qa = s_ra[c * kTile + i], qb = s_rb[c * kTile + j];
-                bool hit;
-                switch (P.combo) {
-                    case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
-                    case 1: hit = rect_disc(dx, dy, qa.x, qa.y, la, wa, rb); break;
-                    case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
-                    default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
-                }
+                const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                 if (!hit) continue;
                 atomicOr(s_found + owner, 1ull << bit);
                 a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
@@ -398,7 +480,7 @@ __device__ __forceinline__ void add_hit(const CollideArgs &a, const PairDesc &P,
 // per 4096 tests.  Candidates are tested one per lane; the earliest overlapping step of each pair is
 // kept with a shared-memory atomicMin, and the first hits are stored (and their risk terms added) once,
 // when the tile is done.
-template <int WARPS, int CH, bool FUSED>
+template <int WARPS, int CH, bool FUSED, bool OUTL>
 __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideArgs a) {
     constexpr int THREADS = WARPS * 32;
     constexpr int QCAP = 256;            // candidates compacted per warp per round
@@ -571,13 +653,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
                     const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                     const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                     const float2 qa = s_ra[c * kTile + i], qb = s_rb[c * kTile + j];
-                    bool hit;
-                    switch (P.combo) {
-                        case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
-                        case 1: hit = rect_disc(dx, dy, qa.x, qa.y, la, wa, rb); break;
-                        case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
-                        default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
-                    }
+                    const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                     if (hit) atomicMin(s_first + i * kTile + j, k);
                 }
                 __syncwarp();
@@ -679,7 +755,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
 // bounding boxes) is decided 32 steps at a time with one ballot.  Fused risk terms are added per hit with
 // global atomics; the per-step histogram terms of one step's hits are summed over the warp first.
 // One TE x TE block (warp task gw) walked by the calling warp; pa_s .. s_new are the warp's own slots.
-template <int TE, bool FUSED>
+template <int TE, bool FUSED, bool OUTL>
 __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, int lane, float4 *pa_s, float4 *pb_s,
                                            float2 *ra_s, float2 *rb_s, unsigned short *queue,
                                            unsigned long long (*s_new)[2]) {
@@ -849,13 +925,7 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
                     const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                     const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                     const float2 qa = ra_s[i], qb = rb_s[j];
-                    bool hit;
-                    switch (P.combo) {
-                        case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
-                        case 1: hit = rect_disc(dx, dy, qa.x, qa.y, la, wa, rb); break;
-                        case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
-                        default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
-                    }
+                    const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                     if (hit) {
                         any_hit = true;
                         atomicOr(s_new[owner] + (bit >> 6), 1ull << (bit & 63));
@@ -913,7 +983,7 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
 
 // The warp-per-block layouts: each warp takes blocks gw = blockIdx.x * WARPS + warp, then every
 // gridDim.x * WARPS further (a grid smaller than the work, max_ctas, leaves SM room to other streams).
-template <int WARPS, int TE, bool FUSED>
+template <int WARPS, int TE, bool FUSED, bool OUTL>
 __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) collide_tile_kernel(const CollideArgs a) {
     constexpr int SUB = kTile / TE;
     constexpr int QCAP = 256;
@@ -926,7 +996,7 @@ __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) coll
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long total = a.n_tiles * (SUB * SUB);
     for (long long gw = (long long)blockIdx.x * WARPS + warp; gw < total; gw += (long long)gridDim.x * WARPS)
-        tile_block<TE, FUSED>(a, gw, lane, s_pa[warp], s_pb[warp], s_ra[warp], s_rb[warp], s_queue[warp],
+        tile_block<TE, FUSED, OUTL>(a, gw, lane, s_pa[warp], s_pb[warp], s_ra[warp], s_rb[warp], s_queue[warp],
                               s_new[warp]);
 }
 
@@ -1017,6 +1087,7 @@ __global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
 // Persistent one-warp CTAs take items it = blockIdx.x, + gridDim.x, ...: stage the block's 32 + 32 poses
 // of the item's step, broad phase on a 4 x 8 micro-block per lane, candidates compacted and tested one per
 // lane, hits kept with atomicMin on the first-step array (no return value: nothing waits on it).
+template <bool OUTL>
 __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
     constexpr int MI = 4, MJ = 8;
     __shared__ float4 pa_s[32], pb_s[32];   // x, y, h
@@ -1090,13 +1161,7 @@ __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
                 const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                 const float2 qa = ra_s[i], qb = rb_s[j];
-                bool hit;
-                switch (P.combo) {
-                    case 0: hit = rect_rect(dx, dy, qa.x, qa.y, la, wa, qb.x, qb.y, lb, wb); break;
-                    case 1: hit = rect_disc(dx, dy, qa.x, qa.y, la, wa, rb); break;
-                    case 2: hit = rect_disc(-dx, -dy, qb.x, qb.y, lb, wb, ra); break;
-                    default: hit = fmaf(dx, dx, dy * dy) <= (ra + rb) * (ra + rb); break;
-                }
+                const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                 if (hit) atomicMin(a.first32 + P.off + (long long)(blk.i0 + i) * B.h + blk.j0 + j, k);
             }
             __syncwarp();
@@ -1224,7 +1289,7 @@ cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int THREADS, int MI, int MJ, int CH, bool FUSED>
+template <int THREADS, int MI, int MJ, int CH, bool FUSED, bool OUTL>
 cudaError_t launch_variant(const CollideArgs &a, cudaStream_t st) {
     size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2));
     if (FUSED) {
@@ -1232,15 +1297,15 @@ cudaError_t launch_variant(const CollideArgs &a, cudaStream_t st) {
         if (a.max_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.max_steps;
     }
     if (smem > 32 * 1024) {   // dynamic + static (about 5 KiB) above the default 48 KiB needs the opt-in
-        cudaError_t e = cudaFuncSetAttribute(collide_kernel<THREADS, MI, MJ, CH, FUSED>,
+        cudaError_t e = cudaFuncSetAttribute(collide_kernel<THREADS, MI, MJ, CH, FUSED, OUTL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    collide_kernel<THREADS, MI, MJ, CH, FUSED><<<(unsigned)a.n_tiles, THREADS, smem, st>>>(a);
+    collide_kernel<THREADS, MI, MJ, CH, FUSED, OUTL><<<(unsigned)a.n_tiles, THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int WARPS, int CH, bool FUSED>
+template <int WARPS, int CH, bool FUSED, bool OUTL>
 cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
     size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2)) + sizeof(int) * kTile * kTile;
     if (FUSED) {
@@ -1248,26 +1313,27 @@ cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
         if (a.max_steps <= kFusedCellSteps) smem += 8 * (size_t)kTile * a.max_steps;
     }
     if (smem > 32 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(collide_warp_kernel<WARPS, CH, FUSED>,
+        cudaError_t e = cudaFuncSetAttribute(collide_warp_kernel<WARPS, CH, FUSED, OUTL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    collide_warp_kernel<WARPS, CH, FUSED><<<(unsigned)a.n_tiles, WARPS * 32, smem, st>>>(a);
+    collide_warp_kernel<WARPS, CH, FUSED, OUTL><<<(unsigned)a.n_tiles, WARPS * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int WARPS, int TE, bool FUSED>
+template <int WARPS, int TE, bool FUSED, bool OUTL>
 cudaError_t launch_tile_variant(const CollideArgs &a, cudaStream_t st) {
     constexpr int SUB = kTile / TE;
     const long long warps = a.n_tiles * SUB * SUB;
     long long blocks = (warps + WARPS - 1) / WARPS;
     if (a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    collide_tile_kernel<WARPS, TE, FUSED><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
+    collide_tile_kernel<WARPS, TE, FUSED, OUTL><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
+template <bool OUTL>
+cudaError_t launch_collide_t(const CollideArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a.variant == 6) {   // the caller zeroed *item_count and sized items and first32
@@ -1280,22 +1346,27 @@ cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         int n_sm = 152, dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        items_kernel<<<(unsigned)(32 * n_sm), 32, 0, st>>>(a);
+        items_kernel<OUTL><<<(unsigned)(32 * n_sm), 32, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         items_table_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);   // over the active blocks only
         return cudaGetLastError();
     }
     if (a.variant == 4)
-        return a.probf ? launch_tile_variant<4, 64, true>(a, st) : launch_tile_variant<4, 64, false>(a, st);
+        return a.probf ? launch_tile_variant<4, 64, true, OUTL>(a, st) : launch_tile_variant<4, 64, false, OUTL>(a, st);
     if (a.variant == 5)   // one warp per CTA: a finished warp frees its slot at once (small, uneven grids)
-        return a.probf ? launch_tile_variant<1, 32, true>(a, st) : launch_tile_variant<1, 32, false>(a, st);
+        return a.probf ? launch_tile_variant<1, 32, true, OUTL>(a, st) : launch_tile_variant<1, 32, false, OUTL>(a, st);
     // variant 1: 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests); variant 2: 8 x 8 with
     // 64 threads; variant 3: one warp per step (8 x 16 lanes).  The caller picks one (autotuned per size).
     const bool many = a.variant == 2;
     if (a.variant == 3)
-        return a.probf ? launch_warp_variant<4, 8, true>(a, st) : launch_warp_variant<4, 8, false>(a, st);
-    if (a.probf) return many ? launch_variant<64, 8, 8, 8, true>(a, st) : launch_variant<256, 4, 4, 16, true>(a, st);
-    return many ? launch_variant<64, 8, 8, 8, false>(a, st) : launch_variant<256, 4, 4, 16, false>(a, st);
+        return a.probf ? launch_warp_variant<4, 8, true, OUTL>(a, st) : launch_warp_variant<4, 8, false, OUTL>(a, st);
+    if (a.probf)
+        return many ? launch_variant<64, 8, 8, 8, true, OUTL>(a, st) : launch_variant<256, 4, 4, 16, true, OUTL>(a, st);
+    return many ? launch_variant<64, 8, 8, 8, false, OUTL>(a, st) : launch_variant<256, 4, 4, 16, false, OUTL>(a, st);
+}
+
+cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
+    return a.polys ? launch_collide_t<true>(a, st) : launch_collide_t<false>(a, st);
 }
 
 }  // namespace mhc

@@ -45,7 +45,13 @@ struct ObjDesc {
     float tau;
     int regime_off;     // vehicles: the speed regimes of grid_a[0..n_a) at regimes[regime_off ..]
     double tau_i_d;     // (double)tau / substeps, the sub-step of the speed recurrence
+    int poly_off;       // vehicles of scenarios with convex outlines: the outline's vertices at
+    int n_poly;         // polys[poly_off .. + n_poly) (a rectangle as its 4 corners); n_poly = 0 otherwise
 };
+
+// One vertex of a convex outline in the body frame with the outward unit normal of the edge to the next
+// vertex (counter-clockwise order): {x, y, n_x, n_y}.
+using PolyVertex = float4;
 
 // Per-object-pair descriptor (device).
 struct PairDesc {
@@ -55,7 +61,8 @@ struct PairDesc {
     long long tile_start;     // first global collision tile of this pair
     float rc2;                // (R_a + R_b)^2, R = circumradius about the pose point
     float r_cull;             // R_a + R_b plus a margin, for bounding-box culling
-    int combo;                // 0 rect-rect, 1 rect(a)-disc(b), 2 disc(a)-rect(b), 3 disc-disc
+    int combo;                // 0 rect-rect, 1 rect(a)-disc(b), 2 disc(a)-rect(b), 3 disc-disc,
+                              // 4 outline-outline, 5 outline(a)-disc(b), 6 disc(a)-outline(b)
     int ego_side;             // 0: a is its scenario's EGO object, 1: b is, -1: neither
     int n_steps;              // steps of the pair's scenario
     int scen;
@@ -67,6 +74,8 @@ struct PairDesc {
     int n_obj_s;              // objects in the scenario
     int co_local;             // the CO object's index in its scenario
     int index;                // the pair's position in table order (per-pair outputs count, P)
+    int poly_a, nv_a;         // combos 4..6: the outlines' vertices (ObjDesc::poly_off, n_poly)
+    int poly_b, nv_b;
     int pad_;
 };
 
@@ -163,9 +172,11 @@ struct CollideArgs {
     int *active;              // [4 n_tiles] blocks with at least one active step, and their number (zeroed)
     unsigned long long *active_count;
     long long max_items;      // capacity: 4 n_tiles x max_steps
-    int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile, 5: warp per quarter tile
+    int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile,
+                              // 5: warp per quarter tile, 6: step items
     const float *x, *y, *c, *s;
     const float4 *bounds;
+    const PolyVertex *polys;       // convex outlines (pairs of combo 4..6), or null when there are none
     int16_t *table;
     unsigned long long *counters;  // optional: [0] broad-phase tests executed, [1] narrow-phase tests
     // fused risk accumulation at first-hit time (probf null: table only)

@@ -42,6 +42,7 @@ struct Layout {
     std::vector<ScenDesc> scens;
     std::vector<float> grids;
     std::vector<Regime> regimes;                     // per vehicle and acceleration value
+    std::vector<PolyVertex> polys;                   // vehicles' outlines in scenarios that have convex outlines
     std::vector<int> warp_obj, warp_first;          // 32-hypothesis bound tiles
     std::vector<int> gen_obj, gen_first;            // generation warp tasks of gen_lanes hypotheses
     std::vector<int> pair0;                         // first pair of each scenario (n_scen + 1 entries)
@@ -90,6 +91,7 @@ struct DevDesc {
     int *warp_obj, *warp_first;
     int *gen_obj, *gen_first;
     Regime *regimes;
+    PolyVertex *polys;       // null when the batch has no outlines
     float *weights;
 };
 

@@ -104,6 +104,8 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
         ObjDesc &d = objs[o];
         std::memset(&d, 0, sizeof d);
         if (src.kind != MHC_VEHICLE && src.kind != MHC_PEDESTRIAN) return fail(MHC_E_INVALID, "bad object kind");
+        if (src.n_vertices != 0)
+            return fail(MHC_E_INVALID, "the static entry point takes rectangles only (n_vertices must be 0)");
         if (src.n_a < 1 || src.n_b < 1 || (long long)src.n_a * src.n_b > (1LL << 30))
             return fail(MHC_E_INVALID, "hypothesis grid sizes out of range");
         d.kind = src.kind;

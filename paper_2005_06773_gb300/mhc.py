@@ -38,7 +38,8 @@ class MhcObject(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("flags", c_int32), ("length", c_float), ("width", c_float),
                 ("radius", c_float), ("x0", c_float), ("y0", c_float), ("psi0", c_float), ("v0", c_float),
                 ("v_max", c_float), ("n_a", c_int32), ("n_b", c_int32), ("grid_a", POINTER(c_float)),
-                ("grid_b", POINTER(c_float)), ("veh_params", POINTER(c_float))]
+                ("grid_b", POINTER(c_float)), ("veh_params", POINTER(c_float)), ("n_vertices", c_int32),
+                ("vertices", POINTER(c_float))]
 
 
 class MhcScenario(ctypes.Structure):
@@ -186,6 +187,12 @@ class CScenario:
                 pp = np.ascontiguousarray(o.params, np.float32)
                 self._keep.append(pp)
                 d.veh_params = pp.ctypes.data_as(POINTER(c_float))
+            outline = getattr(o, "outline", None)
+            if outline is not None:
+                vv = np.ascontiguousarray(np.asarray(outline, np.float32).reshape(-1))
+                self._keep.append(vv)
+                d.n_vertices = vv.size // 2
+                d.vertices = vv.ctypes.data_as(POINTER(c_float))
         self._objs = objs
         self.c = MhcScenario(len(sc.objects), objs, sc.tau, int(sc.n_steps), int(sc.substeps), int(sc.pair_mode),
                              int(sc.ego), int(sc.model))

@@ -343,6 +343,21 @@ def with_outlines(sc: Scenario, cut: float = 0.35, every: int = 1) -> Scenario:
     return dataclasses.replace(sc, objects=objs, name=f"{sc.name}_outline{cut:g}")
 
 
+def paper_pedestrians(sc: Scenario, n_acc: int = 9, n_head: int = 12, seed: int = 15) -> Scenario:
+    """The scenario with its pedestrians sampled as in Section IV-B.3: accelerations evenly over
+    [-12, 12] m/s^2 from an initial walking speed U[0.5, 1.5] m/s, the speed held within [0, 2.7] m/s, and
+    headings evenly over the full circle (psi0 + 2 pi q / n_head)."""
+    rng = SplitMix64(seed)
+    objs = []
+    for o in sc.objects:
+        if o.kind == PEDESTRIAN:
+            o = dataclasses.replace(o, flags=o.flags | PED_ACCEL_GRID, v0=rng.uniform(0.5, 1.5), v_max=2.7,
+                                    grid_a=linspace(-12.0, 12.0, n_acc),
+                                    grid_b=np.array([2.0 * math.pi * q / n_head for q in range(n_head)], dtype=F32))
+        objs.append(o)
+    return dataclasses.replace(sc, objects=objs, name=f"{sc.name}_paperped")
+
+
 def random_weights(sc: Scenario, seed: int) -> List[np.ndarray]:
     rng = SplitMix64(seed)
     return [np.array([rng.uniform(0.05, 1.0) for _ in range(o.n_hyp)], dtype=F32) for o in sc.objects]

@@ -108,3 +108,46 @@ def test_invalid_pedestrian_and_pairing(mhc):
     # a single object with all pairs is valid: no pairs, an empty table
     lay = mhc.layout(S.Scenario([car]))
     assert lay["n_pairs"] == 0 and lay["n_entries"] == 0
+
+
+def _with_outline(outline, obj=0):
+    sc = S.tiny_crossing(1)
+    sc.objects[obj].outline = np.asarray(outline, np.float32).reshape(-1, 2)
+    return sc
+
+
+def _regular(n, r=1.0, turns=1):
+    return [[r * math.cos(2 * math.pi * turns * q / n), r * math.sin(2 * math.pi * turns * q / n)] for q in range(n)]
+
+
+BAD_OUTLINES = {
+    "two_vertices": [[1, 0], [-1, 0]],
+    "seventeen_vertices": _regular(17),
+    "dart": [[2, 0], [-1, 1], [0, 0], [-1, -1]],                 # reflex vertex at the origin
+    "pentagram": _regular(5, turns=2),                           # every turn the same way, but twice round
+    "repeated_vertex": [[1, 1], [-1, 1], [-1, 1], [-1, -1], [1, -1]],
+    "collinear_vertex": [[1, 1], [0, 1], [-1, 1], [-1, -1], [1, -1]],
+    "no_area": [[1, 0], [0, 0], [-1, 0]],
+    "nan_vertex": [[1, 1], [-1, 1], [float("nan"), -1], [1, -1]],
+}
+
+
+@pytest.mark.parametrize("case", list(BAD_OUTLINES))
+def test_invalid_outlines_rejected(mhc, case):
+    with pytest.raises(mhc.MhcError) as e:
+        mhc.layout(_with_outline(BAD_OUTLINES[case]))
+    assert e.value.code == -1
+
+
+def test_outlines_accepted_in_either_orientation(mhc):
+    plain = mhc.layout(S.tiny_crossing(1))
+    ccw = S.chamfered_outline(4.5, 1.8, 0.3)
+    for outline in (ccw, ccw[::-1], _regular(16, 2.0), _regular(3, 2.0)):
+        lay = mhc.layout(_with_outline(outline))
+        sizes = [k for k in plain if k not in ("scratch", "run_bytes")]
+        assert {k: lay[k] for k in sizes} == {k: plain[k] for k in sizes}   # no output array changes size
+        assert lay["scratch"] > plain["scratch"]                             # the vertices travel with the descriptors
+    ped = S.Obj(S.PEDESTRIAN, 0, 0, 0.4, 0, 0, 0, 0, np.array([1.0]), np.array([0.0]),
+                outline=np.array([[1, 0], [0, 1], [-1, 0]], np.float32))
+    with pytest.raises(mhc.MhcError):
+        mhc.layout(S.Scenario([S.tiny_crossing(1).objects[0], ped]))

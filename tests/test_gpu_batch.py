@@ -106,6 +106,26 @@ def test_batch_matches_oracle(mhc, ctx, orc):
         check_risk(mhc.scenario_view(out, sl), orc.risk(sc, t_g, pairs, ws), sl["h_ego"])
 
 
+def test_batch_with_outlines(mhc, ctx, orc):
+    """Scenarios with convex outlines batched with plain ones: the batch runs the outline kernels, and each
+    scenario still gets exactly what it gets alone (the plain ones alone run the kernels without outline
+    tests); the outline scenarios' tables match the oracle."""
+    from test_gpu_parity import scene
+    batch = [S.tiny_crossing(1), copy.deepcopy(scene("outline_shapes")), copy.deepcopy(scene("ragged")),
+             copy.deepcopy(scene("outline_ragged"))]
+    w = _weights(batch, 60)
+    info, sls = mhc.batch_slices(batch)
+    poses, table, out = mhc.evaluate_batch(ctx, batch, weights=w)
+    torch.cuda.synchronize()
+    _compare_single(mhc, ctx, batch, poses, table, out, sls, weights=w)
+    for q in (1, 3):
+        sc, sl = batch[q], sls[q]
+        ref = orc.generate(sc)
+        tab_o, poff, pairs = orc.table(sc, ref)
+        t_g = table[sl["entry0"]: sl["entry0"] + tab_o.size].cpu().numpy()
+        check_table(orc, sc, t_g, tab_o, ref, pairs, poff)
+
+
 def test_batch_pair_table_is_the_concatenation(mhc):
     batch = mixed_batch()
     pa, pb, poff = mhc.batch_pair_table(batch)

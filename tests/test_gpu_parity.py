@@ -56,8 +56,39 @@ def _ped_accel():
     return sc
 
 
+# convex outlines (body frame, metres): a pointed nose, a hexagon, an ellipse as a 16-gon, a triangle and a
+# body whose pose point sits at its rear end
+OUTLINES = [
+    [[2.25, 0.0], [1.5, 0.9], [-2.25, 0.9], [-2.25, -0.9], [1.5, -0.9]],
+    [[2.25, 0.0], [1.2, 0.9], [-1.2, 0.9], [-2.25, 0.0], [-1.2, -0.9], [1.2, -0.9]],
+    [[2.25 * math.cos(2 * math.pi * q / 16), 0.9 * math.sin(2 * math.pi * q / 16)] for q in range(16)],
+    [[2.5, 0.0], [-2.0, 1.0], [-2.0, -1.0]],
+    [[3.6, -0.9], [3.6, 0.9], [-0.9, 0.9], [-0.9, -0.9]],
+]
+
+
+def _outline_shapes():
+    """Vehicles drawn with the assorted outlines above, one in six left a rectangle; pedestrians as discs:
+    every pairing of rectangle, outline and disc."""
+    sc = S.intersection11(14, n_steps=30, n_acc=5, n_str=7, n_ped_v=3, n_ped_h=5)
+    k = 0
+    for o in sc.objects:
+        if o.kind == S.VEHICLE:
+            if k % 6 < 5:
+                o.outline = np.asarray(OUTLINES[k % 6], np.float32)
+            k += 1
+    sc.name = "outline_shapes"
+    return sc
+
+
 def _scenes():
     out = {
+        "outline_shapes": _outline_shapes(),
+        "outline_ragged": S.with_outlines(_ragged(), cut=0.4),
+        "outline_half": S.with_outlines(S.intersection11(5, n_steps=40, n_acc=9, n_str=7, n_ped_v=5, n_ped_h=9),
+                                        cut=0.35, every=2),
+        "outline_paper_peds": S.paper_pedestrians(
+            S.with_outlines(S.intersection11(16, n_steps=50, n_acc=7, n_str=7), cut=0.3), n_acc=9, n_head=12),
         "tiny": S.tiny_crossing(1),
         "tiny_near": S.tiny_crossing(1, 15.0),
         "mixed_small": S.intersection11(5, n_steps=40, n_acc=9, n_str=7, n_ped_v=5, n_ped_h=9),
@@ -87,7 +118,8 @@ def _scenes():
 
 _CACHE = {}
 SCENE_NAMES = ["tiny", "tiny_near", "mixed_small", "ragged", "ped_accel", "paper_s1", "ego_only_ego2_n70",
-               "kinematic", "one_step", "long_n1200", "ego_only_n300"]
+               "kinematic", "one_step", "long_n1200", "ego_only_n300", "outline_shapes", "outline_ragged",
+               "outline_half", "outline_paper_peds"]
 
 
 def scene(name):
@@ -177,7 +209,8 @@ def test_run_equals_separate_calls(mhc, ctx, orc):
             np.testing.assert_array_equal(a, b, err_msg=k)
 
 
-@pytest.mark.parametrize("name", ["mixed_small", "ragged", "ego_only_ego2_n70", "paper_s1", "ped_accel"])
+@pytest.mark.parametrize("name", ["mixed_small", "ragged", "ego_only_ego2_n70", "paper_s1", "ped_accel",
+                                  "outline_shapes"])
 def test_fused_evaluate_equals_separate_calls(mhc, ctx, name):
     """mhc_evaluate accumulates the risk terms inside the collision kernel; the result must equal generate +
     detect + assess: tables and every fixed-point sum bit for bit, the FP64 scalar totals to 1e-12."""
@@ -200,7 +233,7 @@ def test_fused_evaluate_equals_separate_calls(mhc, ctx, name):
 
 
 @pytest.mark.parametrize("name", ["mixed_small", "ragged", "ego_only_ego2_n70", "paper_s1", "kinematic", "long_n1200",
-                                  "ego_only_n300"])
+                                  "ego_only_n300", "outline_shapes", "outline_ragged"])
 def test_collision_variants_agree(mhc, ctx, name):
     """Every thread layout of the collision kernel (and culling on / off) gives the same table and, fused,
     the same risk outputs."""

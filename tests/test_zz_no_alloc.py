@@ -64,3 +64,13 @@ def test_static_entry_rejects_scenarios_beyond_its_scratch(mhc):
     rc = _static_detect(mhc, cs, dummy, table)
     assert rc == -1
     assert b"static scratch" in mhc.lib.mhc_last_error()
+
+
+def test_static_entry_rejects_outlines(mhc):
+    sc = S.with_outlines(S.tiny_crossing(1), cut=0.3)
+    cs = mhc.as_c(sc)
+    dummy = {k: torch.zeros(1, dtype=torch.float32, device="cuda") for k in "xycs"}
+    table = torch.zeros(1, dtype=torch.int16, device="cuda")
+    rc = _static_detect(mhc, cs, dummy, table)
+    assert rc == -1
+    assert b"rectangles only" in mhc.lib.mhc_last_error()
