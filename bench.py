@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "pose-pair tests/s"
 UNIT = "tests/s"
 PROFILE_NOTE = os.path.join(ROOT, "profiles", "collide_tile_kernel_intersection11.md")
-COLLIDE_SRC = os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", "collide.cu")
+COLLIDE_SRC = [os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", f) for f in ("collide.cu", "mhc_internal.cuh")]
 # algorithmic FP32-pipe lane instructions per unit of collision work (roofline section)
 OPS_PER_BROAD_TEST = 3.0      # 2 FFMA (expanded squared distance) + 1 compare
 OPS_PER_NARROW_TEST = 30.0    # separating-axis test of two rectangles, worst shape combination
@@ -69,6 +69,7 @@ WORKLOADS = {
     "stress32": "stress32: 32 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps of 0.1 s, 496 object pairs",
     "stress12": "stress12: 12 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps of 0.1 s, 66 object pairs",
     "paper_s2": "paper_s2: EGO 2058 (6 x 343) + 10 COs x 42 (6 x 7), 100 steps of 20 ms, EGO-only pairs",
+    "outline11": "outline11: intersection11 with every car drawn as a convex octagon (4.5x1.8 m, corners cut 0.35 m)",
 }
 WORKLOAD = "intersection11"
 
@@ -81,6 +82,8 @@ def workload(rank: int = 0):
         return S.stress32(4 + rank, n_cars=12)
     if WORKLOAD == "paper_s2":
         return S.paper_s1s2(10, 6, seed=6 + rank)
+    if WORKLOAD == "outline11":
+        return S.with_outlines(S.intersection11(replica_seed(rank)), cut=0.35)
     return S.intersection11(replica_seed(rank))
 
 
@@ -103,15 +106,27 @@ def load_peaks():
         return {}
 
 
+def collide_code_sha256() -> str:
+    """Hash of the collision kernels' code: collide.cu and the descriptor header with `//` comments and
+    blank lines removed (neither file has `//` inside a string), so that a comment edit keeps a profile."""
+    h = hashlib.sha256()
+    for path in COLLIDE_SRC:
+        for line in open(path, encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
 def traffic_from_profile(variant: int):
-    """DRAM bytes per collide launch from the committed ncu summary, if it was taken on this source and
+    """DRAM bytes per collide launch from the committed ncu summary, if it was taken on this code and
     this collision layout."""
     try:
         text = open(PROFILE_NOTE).read()
-        sha = hashlib.sha256(open(COLLIDE_SRC, "rb").read()).hexdigest()
+        sha = collide_code_sha256()
     except OSError:
         return None
-    m_sha = re.search(r"collide_source_sha256:\s*([0-9a-f]{64})", text)
+    m_sha = re.search(r"collide_code_sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     m_v = re.search(r"collide_variant:\s*([0-9]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != sha or not m_v or int(m_v.group(1)) != variant:
@@ -714,6 +729,11 @@ def run_mhc(args):
                              workload="32 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps, 496 pairs"),
             "paper_s2": dict(measure_workload(mhc, torch, S.paper_s1s2(10, 6), dev, 50, flush, peak),
                              workload="paper Table I S2 shape: EGO 2058 x 10 CO 42, 100 steps of 20 ms, EGO-only"),
+            "outline11": dict(measure_workload(mhc, torch, S.with_outlines(S.intersection11(2), cut=0.35), dev, 50,
+                                               flush, peak),
+                              workload="the benchmark scene with every car drawn as a convex octagon (corners cut "
+                                       "0.35 m); roofline fraction counts each narrow test at the rectangle cost, "
+                                       "so it is a lower bound"),
         }
         line["batch"] = measure_batch(mhc, torch, dev, 10, flush)
         line["serving"] = measure_serving(mhc, torch, dev, args.serve_seconds)

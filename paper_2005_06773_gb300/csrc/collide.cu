@@ -1,12 +1,20 @@
 // collide.cu -- collision recognition (Section IV-C): first overlapping step of every hypothesis pair.
 //
-// Work decomposition: the table is first filled with -1 (HBM-bound); then one CTA per 64 x 64 tile of
-// hypothesis pairs of one object pair walks the active steps in order: per step it stages the 64 + 64
-// poses of its tile in shared memory (double buffered, one barrier per step, the next step's poses
-// already loading) and every thread tests a register micro-tile (8 x 8 with 64 threads when the launch
-// has many tiles, 4 x 4 with 256 threads when it has few and the slowest tile sets the time).  A 64-bit
-// register mask remembers which of the thread's pairs have had their first hit; only first hits are
-// stored.
+// Work decomposition: the hypothesis pairs of each object pair form 64 x 64 tiles, listed pair after pair
+// in collision-grid order (closest pairs first).  Six thread layouts share one result:
+//   1, 2  one CTA per tile (256 threads with 4 x 4 register micro-tiles, or 64 threads with 8 x 8); the
+//         tile's active steps are staged into shared memory a chunk at a time and tested in any order, the
+//         earliest hit kept with a shared atomicMin;
+//   3     a CTA of 4 warps per tile, each warp testing whole steps;
+//   4, 5  one warp per 64 x 64 tile (4 warps per CTA) or per 32 x 32 quarter (1-warp CTAs) walking the
+//         active steps in ascending order: a register mask remembers the pairs that already hit, so only
+//         first hits are stored and later candidates of those pairs cost nothing; the warp stages its own
+//         poses with the next step's loads in flight, and loops over blocks when the grid is capped;
+//   6     step items: (32 x 32 block, active step) pairs listed by one kernel and taken in any order by a
+//         persistent kernel that keeps each pair's earliest step with a global atomicMin; a third kernel
+//         writes the int16 table (and the fused risk terms) for the blocks with active steps.
+// The table is -1 outside first hits: a fill kernel writes it first, or variant 5 writes its own blocks
+// (small tables) and variant 6 its active blocks.
 //
 // Broad phase (per test, 3 FP32 instructions): with h_a = (1 - eps)|p_a|^2 / 2 and
 // h_b = ((1 - eps)|p_b|^2 - R^2 - eps0) / 2 precomputed at staging, the pair is a candidate iff
@@ -15,9 +23,10 @@
 // relative to |p|^2) by more than 10x, so no true candidate is ever rejected; the narrow phase then
 // decides exactly on direct coordinate differences.
 // Narrow phase: separating-axis test on the four edge normals (rectangle-rectangle), clamped distance in
-// the rectangle frame (rectangle-disc), centre distance (disc-disc).  Closed sets: touching overlaps.
-// Culling: steps at which the two tiles' bounding boxes, inflated by R, do not meet are skipped whole
-// (result-preserving).  The first hit of a pair is kept (steps are visited in ascending order).
+// the rectangle frame (rectangle-disc), centre distance (disc-disc), separating edges of convex outlines
+// (outline kernels only).  Closed sets: touching overlaps.
+// Culling: steps at which two blocks' pose-centre bounding boxes, inflated by R, do not meet are skipped
+// whole (result-preserving).
 #include <cstdint>
 
 #include "mhc_internal.cuh"
