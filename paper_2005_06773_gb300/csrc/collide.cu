@@ -145,6 +145,19 @@ __device__ __forceinline__ bool narrow_hit(const PairDesc &P, const PolyVertex *
     }
 }
 
+// Queue slots of one compaction round: each lane brings cnt (0..8) candidates; off = the candidates of the
+// lanes below it, total = all of them (one ballot per bit of cnt instead of a shuffle scan: four
+// independent instructions, not a chain of five).  Returns false when no lane has any (uniform).
+__device__ __forceinline__ bool queue_offsets(int cnt, int lane, int &off, int &total) {
+    const unsigned b0 = __ballot_sync(0xffffffffu, cnt & 1), b1 = __ballot_sync(0xffffffffu, cnt & 2);
+    const unsigned b2 = __ballot_sync(0xffffffffu, cnt & 4), b3 = __ballot_sync(0xffffffffu, cnt & 8);
+    if (!(b0 | b1 | b2 | b3)) return false;
+    const unsigned lt = (1u << lane) - 1u;
+    off = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
+    total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
+    return true;
+}
+
 constexpr int kMaxChunks = (32767 + 31) / 32;   // 32-step activity words for the longest horizon
 constexpr int kFusedHistSteps = 1024;            // per-CTA step histograms in shared memory up to this N
 constexpr int kFusedCellSteps = 160;             // per-CTA EGO survival cells (64 x N x 8 B) up to this N
@@ -767,7 +780,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
 template <int TE, bool FUSED, bool OUTL>
 __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, int lane, float4 *pa_s, float4 *pb_s,
                                            float2 *ra_s, float2 *rb_s, unsigned short *queue,
-                                           unsigned long long (*s_new)[2]) {
+                                           unsigned long long (*s_new)[2], float *prob_s) {
     static_assert(TE == 64 || TE == 32, "block edge");
     constexpr int MI = TE / 8, MJ = TE / 4;       // micro-block of a lane
     constexpr int SUB = kTile / TE;               // blocks per tile edge
@@ -804,6 +817,14 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
         for (int r = 0; r < rows; ++r, row += B.h)
             for (int c = lane; c < cols; c += 32) row[c] = (int16_t)-1;
         __syncwarp();      // the fill is ordered before this warp's first-hit stores
+    }
+    if (FUSED) {   // the block's probabilities, read at every first hit (kept off the hit path's latency)
+#pragma unroll
+        for (int u = 0; u < TE / 32; ++u) {
+            const int r = lane + 32 * u;
+            prob_s[r] = r < rows ? a.probf[A.traj_off + i0 + r] : 0.0f;
+            prob_s[TE + r] = r < cols ? a.probf[B.traj_off + j0 + r] : 0.0f;
+        }
     }
 
     // activity of the 32 steps from k0 (one ballot)
@@ -909,15 +930,8 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
             // compact and test one candidate per lane, in rounds of at most 8 per lane
             for (;;) {
                 const int cnt = min(__popcll(c_lo) + __popcll(c_hi), 8);
-                if (!__ballot_sync(0xffffffffu, cnt != 0)) break;
-                int off = cnt;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, off, d);
-                    if (lane >= d) off += v;
-                }
-                const int total = __shfl_sync(0xffffffffu, off, 31);
-                off -= cnt;
+                int off, total;
+                if (!queue_offsets(cnt, lane, off, total)) break;
                 for (int q = 0; q < cnt; ++q) {
                     int bit;
                     if (c_lo) { bit = __ffsll((long long)c_lo) - 1; c_lo &= c_lo - 1ull; }
@@ -940,7 +954,7 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
                         atomicOr(s_new[owner] + (bit >> 6), 1ull << (bit & 63));
                         a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
                         if (FUSED) {
-                            const float pa_ = a.probf[A.traj_off + i0 + i], pb_ = a.probf[B.traj_off + j0 + j];
+                            const float pa_ = prob_s[i], pb_ = prob_s[TE + j];
                             const unsigned long long w = to_fixed(pa_ * pb_, kFixProb);
                             ++step_cnt;
                             step_mass += w;
@@ -1002,11 +1016,12 @@ __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) coll
     __shared__ float2 s_rb[WARPS][TE];
     __shared__ unsigned short s_queue[WARPS][QCAP];       // candidates: owner lane << 7 | bit
     __shared__ unsigned long long s_new[WARPS][32][2];     // pairs found in this step, in owner-lane layout
+    __shared__ float s_prob[WARPS][FUSED ? 2 * TE : 1];    // fused: the block's row and column probabilities
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long total = a.n_tiles * (SUB * SUB);
     for (long long gw = (long long)blockIdx.x * WARPS + warp; gw < total; gw += (long long)gridDim.x * WARPS)
         tile_block<TE, FUSED, OUTL>(a, gw, lane, s_pa[warp], s_pb[warp], s_ra[warp], s_rb[warp], s_queue[warp],
-                              s_new[warp]);
+                              s_new[warp], s_prob[warp]);
 }
 
 // ---- step-item layout (variant 6): the active (block, step) pairs of a small scene in parallel ----------
@@ -1147,15 +1162,8 @@ __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
         const float la = A.hl, wa = A.hw, ra = A.rad, lb = B.hl, wb = B.hw, rb = B.rad;
         for (;;) {                              // rounds of at most 8 candidates per lane
             const int cnt = min(__popc(cand), 8);
-            if (!__ballot_sync(0xffffffffu, cnt != 0)) break;
-            int off = cnt;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, off, d);
-                if (lane >= d) off += v;
-            }
-            const int total = __shfl_sync(0xffffffffu, off, 31);
-            off -= cnt;
+            int off, total;
+            if (!queue_offsets(cnt, lane, off, total)) break;
             for (int q = 0; q < cnt; ++q) {
                 const int bit = __ffs(cand) - 1;
                 cand &= cand - 1u;

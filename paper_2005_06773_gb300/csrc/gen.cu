@@ -415,6 +415,10 @@ __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Reg
     }
 }
 
+// LAYOUTS: 1 every task is a warp per hypothesis, 2 every task is a thread per hypothesis, 3 both (a kernel
+// holding one layout only has a smaller instruction footprint: the integration is latency-bound and
+// instruction fetch was its largest stall).
+template <int LAYOUTS>
 __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
     if ((int)blockIdx.x >= a.gen_blocks) {               // the risk preparation, independent of generation
         prepare_block(a.prep, blockIdx.x - a.gen_blocks, a.prep_blocks);
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
     }
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= a.n_warps) return;                          // whole warps leave
-    if (w < a.n_scan) {                                  // one hypothesis by the whole warp
+    if ((LAYOUTS & 1) && (LAYOUTS == 1 || w < a.n_scan)) {   // one hypothesis by the whole warp
         const int lane = threadIdx.x & 31;
         const ObjDesc &o = a.objs[a.warp_obj[w]];
         const int i = a.warp_first[w];
@@ -436,6 +440,7 @@ __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
             pedestrian(o, ga, gb, o.n_steps, o.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s, lane, 32);
         return;
     }
+    if (!(LAYOUTS & 2)) return;
     if ((threadIdx.x & 31) >= a.lanes) return;
     const ObjDesc &o = a.objs[a.warp_obj[w]];
     const int i = a.warp_first[w] + (threadIdx.x & 31);
@@ -488,7 +493,12 @@ cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
     a.gen_blocks = (a.n_warps + warps_per_block - 1) / warps_per_block;
     const long long blocks = (long long)a.gen_blocks + (a.prep_blocks > 0 ? a.prep_blocks : 0);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    gen_kernel<<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
+    if (a.n_scan >= a.n_warps)
+        gen_kernel<1><<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
+    else if (a.n_scan <= 0)
+        gen_kernel<2><<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
+    else
+        gen_kernel<3><<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
