@@ -351,8 +351,9 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
     s.acc_words = acc_words(L);
     s.acc = align_up(8 * (size_t)s.acc_words);
-    s.items = items_eligible(L) ? kAlign + align_up(8 * (size_t)(4 * L.n_tiles * (long long)L.max_steps)) +
-                                      align_up(4 * (size_t)L.n_entries) + align_up(16 * (size_t)L.n_tiles)
+    s.items = items_eligible(L) ? kAlign + align_up(sizeof(StepItem) * (size_t)(4 * L.n_tiles * (long long)L.max_steps)) +
+                                      align_up(4 * (size_t)L.n_entries) + align_up(16 * (size_t)L.n_tiles) +
+                                      align_up(4 * sizeof(ItemBlock) * (size_t)L.n_tiles)
                                 : 0;
     s.total = s.desc + s.weights + s.bounds + s.prob + s.acc + s.items;
     return s;
@@ -579,10 +580,15 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     if (risk) {
         if (int rc = make_risk_args(L, D, bump, table, rout, r)) return rc;
     }
+    // after_kernel: the last operation put on the stream here is one of this sequence's kernels, so the
+    // next may be a programmatic dependent launch (not while profiling: event records sit in between)
+    bool after_kernel = false;
+    auto pdl = [&]() { return after_kernel && !ctx->profile; };
     if (fused && !gen_out) {   // else the preparation runs inside the generation launch
         TimedScope ts(ctx, st, MHC_K_RISK, 1);
         cudaError_t e = launch_risk_prepare(r, st);
         if (e != cudaSuccess) return cuda_fail(e, "risk prepare launch");
+        after_kernel = true;
     }
     if (gen_out) {
         GenArgs g;
@@ -600,6 +606,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
         cudaError_t e = launch_generate(g, st);
         if (e != cudaSuccess) return cuda_fail(e, "generation kernel launch");
+        after_kernel = true;
     }
     if (coll_in) {
         int variant = 1, cull = 1;
@@ -612,15 +619,17 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         const bool fill_in_collide = (variant == 5 && L.n_entries <= kFillInCollideMax) || variant == 6;
         {
             TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_in_collide ? 0 : 1));
-            cudaError_t e = fill_in_collide ? cudaSuccess : launch_fill_table(table, L.n_entries, st);
+            cudaError_t e = fill_in_collide ? cudaSuccess : launch_fill_table(table, L.n_entries, st, pdl());
             if (e != cudaSuccess) return cuda_fail(e, "table fill launch");
+            if (!fill_in_collide && L.n_entries > 0) after_kernel = true;
             if (cull) {
                 BoundsArgs b;
                 b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
                 b.n_warps = (int)L.warp_obj.size(); b.max_steps = L.max_steps; b.x = coll_in->x; b.y = coll_in->y;
                 b.bounds = bounds;
-                e = launch_bounds(b, st);
+                e = launch_bounds(b, st, pdl());
                 if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
+                if ((long long)b.n_warps * b.max_steps > 0) after_kernel = true;
             }
         }
         CollideArgs c{};
@@ -636,21 +645,24 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         if (variant == 6) {   // the item list and its length (zeroed here)
             c.max_items = 4 * L.n_tiles * (long long)L.max_steps;
             c.item_count = static_cast<unsigned long long *>(bump.take(kAlign));
-            c.items = static_cast<int2 *>(bump.take(sizeof(int2) * (size_t)c.max_items));
+            c.items = static_cast<StepItem *>(bump.take(sizeof(StepItem) * (size_t)c.max_items));
             c.active_count = c.item_count + 1;
             c.first32 = static_cast<int *>(bump.take(sizeof(int) * (size_t)L.n_entries));
             c.active = static_cast<int *>(bump.take(sizeof(int) * (size_t)(4 * L.n_tiles)));
-            if (!c.items || !c.item_count || !c.first32 || !c.active)
+            c.blocks = static_cast<ItemBlock *>(bump.take(sizeof(ItemBlock) * (size_t)(4 * L.n_tiles)));
+            if (!c.items || !c.item_count || !c.first32 || !c.active || !c.blocks)
                 return fail(MHC_E_NOMEM, "arena too small for the step items");
             MHC_CUDA(cudaMemsetAsync(c.item_count, 0, 2 * sizeof(unsigned long long), st));
+            after_kernel = false;
         }
         TimedScope ts(ctx, st, MHC_K_COLLIDE, variant == 6 ? 3 : 1);
-        cudaError_t e = launch_collide(c, st);
+        cudaError_t e = launch_collide(c, st, pdl());
         if (e != cudaSuccess) return cuda_fail(e, "collision kernel launch");
+        if (L.n_tiles > 0) after_kernel = true;
     }
     if (risk) {   // fused collision: the walk only; else preparation, table scan and walk
         TimedScope ts(ctx, st, MHC_K_RISK, (fused ? 0 : 2) + risk_tail_launches(r));
-        cudaError_t e = fused ? launch_risk_tail(r, st) : launch_risk(r, st);
+        cudaError_t e = fused ? launch_risk_tail(r, st, pdl()) : launch_risk(r, st, true, pdl());
         if (e != cudaSuccess) return cuda_fail(e, "risk kernel launch");
     }
     return MHC_OK;

@@ -158,6 +158,25 @@ __device__ __forceinline__ bool queue_offsets(int cnt, int lane, int &off, int &
     return true;
 }
 
+// The pair of collision tile g: the last pair (in collision-grid order) whose first tile is <= g.  A 32-way
+// search by the whole warp (every lane must call it with the same g): each round the lanes probe 32
+// evenly spaced pairs at once and keep the span between the last probe <= g and the next, so 55 pairs take
+// one round of loads and 32,768 take three (a binary search is a chain of log2 n dependent loads).
+__device__ __forceinline__ int pair_of_tile(const CollideArgs &a, long long g) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = a.n_pairs - 1;
+    while (lo < hi) {
+        const long long span = hi - lo + 1;
+        const bool le = a.pairs[lo + (int)(span * lane / 32)].tile_start <= g;
+        const unsigned m = __ballot_sync(0xffffffffu, le);           // lane 0 always: pairs[lo] <= g
+        const int L = 31 - __clz(m);
+        const int nlo = lo + (int)(span * L / 32);
+        hi = L == 31 ? hi : lo + (int)(span * (L + 1) / 32) - 1;
+        lo = nlo;
+    }
+    return lo;
+}
+
 constexpr int kMaxChunks = (32767 + 31) / 32;   // 32-step activity words for the longest horizon
 constexpr int kFusedHistSteps = 1024;            // per-CTA step histograms in shared memory up to this N
 constexpr int kFusedCellSteps = 160;             // per-CTA EGO survival cells (64 x N x 8 B) up to this N
@@ -179,6 +198,7 @@ __device__ __forceinline__ int next_active(const unsigned *mask, int n_chunks, i
 // every load in flight at once, then each warp runs through the CH steps without further barriers.
 template <int THREADS, int MI, int MJ, int CH, bool FUSED, bool OUTL>
 __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
+    pdl_start();
     constexpr int TI = kTile / MI, TJ = kTile / MJ;
     static_assert(TI * TJ == THREADS, "micro-tiles must cover the tile");
     static_assert(MI * MJ <= 64, "first-hit mask is 64 bits");
@@ -198,11 +218,7 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
 
     const long long g = blockIdx.x;
     if (g >= a.n_tiles) return;
-    int lo = 0, hi = a.n_pairs - 1;      // last pair whose first tile is <= g
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
-    }
+    const int lo = pair_of_tile(a, g);
     const PairDesc P = a.pairs[lo];
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
@@ -504,6 +520,7 @@ __device__ __forceinline__ void add_hit(const CollideArgs &a, const PairDesc &P,
 // when the tile is done.
 template <int WARPS, int CH, bool FUSED, bool OUTL>
 __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideArgs a) {
+    pdl_start();
     constexpr int THREADS = WARPS * 32;
     constexpr int QCAP = 256;            // candidates compacted per warp per round
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -520,11 +537,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
 
     const long long g = blockIdx.x;
     if (g >= a.n_tiles) return;
-    int lo = 0, hi = a.n_pairs - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
-    }
+    const int lo = pair_of_tile(a, g);
     const PairDesc P = a.pairs[lo];
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
@@ -787,11 +800,7 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
     const long long g = gw / (SUB * SUB);                 // the 64 x 64 tile
     if (g >= a.n_tiles) return;
     const int quarter = (int)(gw - g * (SUB * SUB));
-    int lo = 0, hi = a.n_pairs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
-    }
+    const int lo = pair_of_tile(a, g);
     const PairDesc &P = a.pairs[lo];   // fields read where used (fewer live registers)
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
@@ -1008,6 +1017,7 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
 // gridDim.x * WARPS further (a grid smaller than the work, max_ctas, leaves SM room to other streams).
 template <int WARPS, int TE, bool FUSED, bool OUTL>
 __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) collide_tile_kernel(const CollideArgs a) {
+    pdl_start();
     constexpr int SUB = kTile / TE;
     constexpr int QCAP = 256;
     __shared__ float4 s_pa[WARPS][TE];            // x, y, h_a
@@ -1041,11 +1051,7 @@ struct BlockAt {
 __device__ __forceinline__ BlockAt block_at(const CollideArgs &a, long long gw) {
     const long long g = gw >> 2;
     const int quarter = (int)(gw & 3);
-    int lo = 0, hi = a.n_pairs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.pairs[mid].tile_start <= g) lo = mid; else hi = mid - 1;
-    }
+    const int lo = pair_of_tile(a, g);
     const PairDesc &P = a.pairs[lo];
     const long long t = g - P.tile_start;
     const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
@@ -1062,6 +1068,7 @@ __device__ __forceinline__ BlockAt block_at(const CollideArgs &a, long long gw) 
 // one atomic per ballot); then a block without any writes its table entries (-1) at once, and an active
 // block sets its first-step entries to INT_MAX and joins the list of active blocks.
 __global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
+    pdl_start();
     const int lane = threadIdx.x & 31;
     const long long total = a.n_tiles * 4;
     for (long long gw = (long long)blockIdx.x * 4 + (threadIdx.x >> 5); gw < total; gw += (long long)gridDim.x * 4) {
@@ -1090,7 +1097,14 @@ __global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
             base = __shfl_sync(0xffffffffu, base, 0);
             if (act) {
                 const unsigned long long at = base + __popc(m & ((1u << lane) - 1u));
-                if (at < (unsigned long long)a.max_items) a.items[at] = make_int2((int)gw, k);
+                if (at < (unsigned long long)a.max_items) {
+                    StepItem itm;
+                    itm.pa = A.pose_base + (long long)k * A.h + blk.i0;
+                    itm.pb = B.pose_base + (long long)k * B.h + blk.j0;
+                    itm.gw = (int)gw;
+                    itm.k = k;
+                    a.items[at] = itm;
+                }
             }
         }
         const long long base = P.off + (long long)blk.i0 * B.h + blk.j0 + lane;
@@ -1104,6 +1118,11 @@ __global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
         if (lane == 0) {
             const unsigned long long at = atomicAdd(a.active_count, 1ull);
             if (at < (unsigned long long)(a.n_tiles * 4)) a.active[at] = (int)gw;
+            ItemBlock rec;
+            rec.entry0 = P.off + (long long)blk.i0 * B.h + blk.j0;
+            rec.h_b = B.h; rec.pair = blk.pair; rec.rows = blk.rows; rec.cols = blk.cols;
+            rec.rc2 = P.rc2; rec.la = A.hl; rec.wa = A.hw; rec.ra = A.rad; rec.lb = B.hl; rec.wb = B.hw; rec.rb = B.rad;
+            a.blocks[gw] = rec;
         }
     }
 }
@@ -1113,6 +1132,7 @@ __global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
 // lane, hits kept with atomicMin on the first-step array (no return value: nothing waits on it).
 template <bool OUTL>
 __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
+    pdl_start();
     constexpr int MI = 4, MJ = 8;
     __shared__ float4 pa_s[32], pb_s[32];   // x, y, h
     __shared__ float2 ra_s[32], rb_s[32];   // c, s
@@ -1122,17 +1142,17 @@ __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
     const unsigned long long listed = *a.item_count;
     const long long count = listed < (unsigned long long)a.max_items ? (long long)listed : a.max_items;
     unsigned long long narrow = 0, executed = 0;
+    StepItem next;                                                   // one item ahead
+    if (blockIdx.x < count) next = a.items[blockIdx.x];
     for (long long it = blockIdx.x; it < count; it += gridDim.x) {
-        const int2 item = a.items[it];
-        const int k = item.y;
-        const BlockAt blk = block_at(a, item.x);
-        const PairDesc &P = a.pairs[blk.pair];
-        const ObjDesc &A = a.objs[P.a];
-        const ObjDesc &B = a.objs[P.b];
-        const float rc2 = P.rc2 + kEps0;
-        const bool oka = lane < blk.rows, okb = lane < blk.cols;
-        const long long ia = A.pose_base + (long long)k * A.h + blk.i0 + lane;
-        const long long ib = B.pose_base + (long long)k * B.h + blk.j0 + lane;
+        const StepItem item = next;
+        if (it + gridDim.x < count) next = a.items[it + gridDim.x];
+        const int k = item.k;
+        const ItemBlock bk = a.blocks[item.gw];                      // loaded beside the poses
+        const float rc2 = bk.rc2 + kEps0;
+        const bool oka = lane < bk.rows, okb = lane < bk.cols;
+        const long long ia = item.pa + lane;
+        const long long ib = item.pb + lane;
         const float xa = oka ? __ldg(a.x + ia) : kFar, ya = oka ? __ldg(a.y + ia) : 0.0f;
         const float ca = oka ? __ldg(a.c + ia) : 1.0f, sa = oka ? __ldg(a.s + ia) : 0.0f;
         const float xb = okb ? __ldg(a.x + ib) : -kFar, yb = okb ? __ldg(a.y + ib) : 0.0f;
@@ -1159,7 +1179,8 @@ __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
                 if (fmaf(ax[m], qb.x, fmaf(ay[m], qb.y, -qb.z)) >= ah[m]) cand |= 1u << (MJ * m + n);
         }
         if (!__ballot_sync(0xffffffffu, cand != 0u)) continue;
-        const float la = A.hl, wa = A.hw, ra = A.rad, lb = B.hl, wb = B.hw, rb = B.rad;
+        const PairDesc &P = a.pairs[bk.pair];
+        const float la = bk.la, wa = bk.wa, ra = bk.ra, lb = bk.lb, wb = bk.wb, rb = bk.rb;
         for (;;) {                              // rounds of at most 8 candidates per lane
             const int cnt = min(__popc(cand), 8);
             int off, total;
@@ -1179,7 +1200,7 @@ __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                 const float2 qa = ra_s[i], qb = rb_s[j];
                 const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
-                if (hit) atomicMin(a.first32 + P.off + (long long)(blk.i0 + i) * B.h + blk.j0 + j, k);
+                if (hit) atomicMin(a.first32 + bk.entry0 + (long long)i * bk.h_b + j, k);
             }
             __syncwarp();
         }
@@ -1195,80 +1216,100 @@ __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
 // flight together), writes the int16 entries and adds each first hit's terms with the fixed-point atomics
 // of the fused layouts (the same sums, in any order).
 __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
-    const int lane = threadIdx.x & 31;
+    pdl_start();
+    __shared__ float s_pa[4][32];                    // the block's row probabilities
+    __shared__ unsigned long long s_sub[4][8][16];   // EGO rows: sums of the CO masses of any subset of
+                                                     // columns 4q .. 4q + 3 (bit b of m: column 4q + b)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const bool risk = a.probf != nullptr;
     const unsigned long long listed = *a.active_count;
     const long long total = listed < (unsigned long long)(a.n_tiles * 4) ? (long long)listed : a.n_tiles * 4;
-    for (long long q = (long long)blockIdx.x * 4 + (threadIdx.x >> 5); q < total; q += (long long)gridDim.x * 4) {
+    for (long long q = (long long)blockIdx.x * 4 + w; q < total; q += (long long)gridDim.x * 4) {
         const BlockAt blk = block_at(a, a.active[q]);
         if (blk.rows <= 0 || blk.cols <= 0) continue;
         const PairDesc &P = a.pairs[blk.pair];
         const ObjDesc &A = a.objs[P.a];
         const ObjDesc &B = a.objs[P.b];
-        const int N = P.n_steps;
+        const int N = P.n_steps, ego_side = P.ego_side, n_obj_s = P.n_obj_s, co_local = P.co_local;
+        const long long kofs = P.kofs, lsum_base = P.lsum_base, hb = B.h;
         const bool col_ok = lane < blk.cols;
         const float pb = risk && col_ok ? a.probf[B.traj_off + blk.j0 + lane] : 0.0f;
-        const long long base = P.off + (long long)blk.i0 * B.h + blk.j0 + lane;
+        __syncwarp();                                // the previous block's slots are no longer read
+        s_pa[w][lane] = risk && lane < blk.rows ? a.probf[A.traj_off + blk.i0 + lane] : 0.0f;
+        if (risk && ego_side == 0) {                 // a row's CO mass = the sum over its colliding columns
+            const unsigned long long c = to_fixed(pb, kFixProb);   // zero past the block's columns
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = lane + 32 * u, g = e >> 4, m = e & 15;
+                unsigned long long sum = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const unsigned long long cb = __shfl_sync(0xffffffffu, c, 4 * g + b);
+                    if (m >> b & 1) sum += cb;
+                }
+                s_sub[w][g][m] = sum;
+            }
+        }
+        __syncwarp();
+        const long long base = P.off + (long long)blk.i0 * hb + blk.j0 + lane;
         unsigned long long cnt = 0, mass = 0, col_mass = 0;
         unsigned col_hits = 0;
         for (int r0 = 0; r0 < blk.rows; r0 += 8) {
             int v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                v[u] = col_ok && r0 + u < blk.rows ? a.first32[base + (long long)(r0 + u) * B.h] : 0x7fffffff;
+                v[u] = col_ok && r0 + u < blk.rows ? a.first32[base + (long long)(r0 + u) * hb] : 0x7fffffff;
             bool any = false;
 #pragma unroll
             for (int u = 0; u < 8; ++u) any |= v[u] != 0x7fffffff;
             if (!__ballot_sync(0xffffffffu, any)) {          // no hit in these 8 rows
                 if (col_ok)
-                    for (int u = 0; u < 8 && r0 + u < blk.rows; ++u) a.table[base + (long long)(r0 + u) * B.h] = -1;
+                    for (int u = 0; u < 8 && r0 + u < blk.rows; ++u) a.table[base + (long long)(r0 + u) * hb] = -1;
                 continue;
             }
+            // each lane adds its own first hits' terms; an EGO row's totals come from one ballot
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int r = r0 + u;
                 if (r >= blk.rows) break;                     // uniform over the warp
                 const int k = v[u] == 0x7fffffff ? -1 : v[u];
-                if (col_ok) a.table[base + (long long)r * B.h] = (int16_t)k;
-                const bool hit = k >= 0;
-                if (!risk || !__ballot_sync(0xffffffffu, hit)) continue;
-                const float pa = a.probf[A.traj_off + blk.i0 + r];
-                unsigned long long row_mass = 0;
-                if (hit) {
-                    const unsigned long long w = to_fixed(pa * pb, kFixProb);
+                if (col_ok) a.table[base + (long long)r * hb] = (int16_t)k;
+                if (!risk) continue;
+                if (k >= 0) {
+                    const float pa = s_pa[w][r];
+                    const unsigned long long wt = to_fixed(pa * pb, kFixProb);
                     ++cnt;
-                    mass += w;
-                    atomicAdd(a.acc.count_k + P.kofs + k, 1ull);
-                    atomicAdd(a.acc.H + P.kofs + k, w);
-                    if (P.ego_side >= 0) {
-                        const long long e = P.ego_side == 0 ? blk.i0 + r : blk.j0 + lane;   // the EGO hypothesis
-                        const float pco = P.ego_side == 0 ? pb : pa;                        // the CO hypothesis
-                        atomicAdd(a.acc.lsum + P.lsum_base + (e * N + k) * P.n_obj_s + P.co_local,
+                    mass += wt;
+                    atomicAdd(a.acc.count_k + kofs + k, 1ull);
+                    atomicAdd(a.acc.H + kofs + k, wt);
+                    if (ego_side >= 0) {
+                        const long long e = ego_side == 0 ? blk.i0 + r : blk.j0 + lane;   // the EGO hypothesis
+                        const float pco = ego_side == 0 ? pb : pa;                        // the CO hypothesis
+                        atomicAdd(a.acc.lsum + lsum_base + (e * N + k) * n_obj_s + co_local,
                                   to_fixed(neg_log_survival(pco), kFixLog));
-                        if (P.ego_side == 0) {
-                            row_mass = to_fixed(pco, kFixProb);
-                        } else {
+                        if (ego_side == 1) {
                             col_mass += to_fixed(pco, kFixProb);
                             ++col_hits;
                         }
                     }
                 }
-                if (P.ego_side == 0) {   // the row's EGO hypothesis: its CO mass and hit count over the row
+                if (ego_side == 0) {                     // the row's EGO hypothesis: CO mass and hits
+                    const unsigned hm = __ballot_sync(0xffffffffu, k >= 0);
+                    if (hm && lane == 0) {
+                        unsigned long long rm = 0;
 #pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) row_mass += __shfl_xor_sync(0xffffffffu, row_mass, d);
-                    const unsigned hits = __popc(__ballot_sync(0xffffffffu, hit));
-                    if (lane == 0) {
+                        for (int g = 0; g < 8; ++g) rm += s_sub[w][g][(hm >> (4 * g)) & 15];
                         const long long e = blk.i0 + r;
-                        atomicAdd(a.acc.mass + P.mass_base + e * P.n_obj_s + P.co_local, row_mass);
-                        atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)hits);
+                        atomicAdd(a.acc.mass + P.mass_base + e * n_obj_s + co_local, rm);
+                        atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)__popc(hm));
                     }
                 }
             }
         }
         if (!risk) continue;
-        if (P.ego_side == 1 && col_hits) {
+        if (ego_side == 1 && col_hits) {                                // the block's EGO columns
             const long long e = blk.j0 + lane;
-            atomicAdd(a.acc.mass + P.mass_base + e * P.n_obj_s + P.co_local, col_mass);
+            atomicAdd(a.acc.mass + P.mass_base + e * n_obj_s + co_local, col_mass);
             atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)col_hits);
         }
 #pragma unroll
@@ -1285,6 +1326,7 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
 
 // table[0, n) = -1 (no collision), 16-byte stores on the aligned body
 __global__ void __launch_bounds__(256) fill_kernel(int16_t *table, long long n) {
+    pdl_start();
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long head = min(n, (long long)((16 - ((uintptr_t)table & 15)) & 15) / 2);
@@ -1298,16 +1340,15 @@ __global__ void __launch_bounds__(256) fill_kernel(int16_t *table, long long n) 
 
 }  // namespace
 
-cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st) {
+cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st, bool pdl) {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n / 8 + 255) / 256 + 1;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(table, n);
-    return cudaGetLastError();
+    return launch_kernel(fill_kernel, dim3((unsigned)blocks), dim3(256), 0, st, pdl, table, n);
 }
 
 template <int THREADS, int MI, int MJ, int CH, bool FUSED, bool OUTL>
-cudaError_t launch_variant(const CollideArgs &a, cudaStream_t st) {
+cudaError_t launch_variant(const CollideArgs &a, cudaStream_t st, bool pdl) {
     size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2));
     if (FUSED) {
         if (a.max_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.max_steps + (a.max_steps + 1) / 2);
@@ -1318,12 +1359,12 @@ cudaError_t launch_variant(const CollideArgs &a, cudaStream_t st) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    collide_kernel<THREADS, MI, MJ, CH, FUSED, OUTL><<<(unsigned)a.n_tiles, THREADS, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(collide_kernel<THREADS, MI, MJ, CH, FUSED, OUTL>, dim3((unsigned)a.n_tiles), dim3(THREADS),
+                         smem, st, pdl, a);
 }
 
 template <int WARPS, int CH, bool FUSED, bool OUTL>
-cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
+cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st, bool pdl) {
     size_t smem = (size_t)CH * kTile * (2 * sizeof(float4) + 2 * sizeof(float2)) + sizeof(int) * kTile * kTile;
     if (FUSED) {
         if (a.max_steps <= kFusedHistSteps) smem += 8 * ((size_t)a.max_steps + (a.max_steps + 1) / 2);
@@ -1334,56 +1375,57 @@ cudaError_t launch_warp_variant(const CollideArgs &a, cudaStream_t st) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    collide_warp_kernel<WARPS, CH, FUSED, OUTL><<<(unsigned)a.n_tiles, WARPS * 32, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(collide_warp_kernel<WARPS, CH, FUSED, OUTL>, dim3((unsigned)a.n_tiles), dim3(WARPS * 32),
+                         smem, st, pdl, a);
 }
 
 template <int WARPS, int TE, bool FUSED, bool OUTL>
-cudaError_t launch_tile_variant(const CollideArgs &a, cudaStream_t st) {
+cudaError_t launch_tile_variant(const CollideArgs &a, cudaStream_t st, bool pdl) {
     constexpr int SUB = kTile / TE;
     const long long warps = a.n_tiles * SUB * SUB;
     long long blocks = (warps + WARPS - 1) / WARPS;
     if (a.max_ctas > 0 && blocks > a.max_ctas) blocks = a.max_ctas;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    collide_tile_kernel<WARPS, TE, FUSED, OUTL><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(collide_tile_kernel<WARPS, TE, FUSED, OUTL>, dim3((unsigned)blocks), dim3(WARPS * 32), 0,
+                         st, pdl, a);
 }
 
 template <bool OUTL>
-cudaError_t launch_collide_t(const CollideArgs &a, cudaStream_t st) {
+cudaError_t launch_collide_t(const CollideArgs &a, cudaStream_t st, bool pdl) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a.variant == 6) {   // the caller zeroed *item_count and sized items and first32
-        if (!a.items || !a.item_count || !a.first32 || !a.active || !a.active_count || a.n_tiles * 4 > 0x7fffffffLL)
+        if (!a.items || !a.item_count || !a.first32 || !a.active || !a.active_count || !a.blocks ||
+            a.n_tiles * 4 > 0x7fffffffLL)
             return cudaErrorInvalidValue;
         long long blocks = (a.n_tiles * 4 + 3) / 4;
         if (blocks > 152 * 16) blocks = 152 * 16;
-        items_list_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_kernel(items_list_kernel, dim3((unsigned)blocks), dim3(128), 0, st, pdl, a);
         if (e != cudaSuccess) return e;
         int n_sm = 152, dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        items_kernel<OUTL><<<(unsigned)(32 * n_sm), 32, 0, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        items_table_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);   // over the active blocks only
-        return cudaGetLastError();
+        e = launch_kernel(items_kernel<OUTL>, dim3((unsigned)(32 * n_sm)), dim3(32), 0, st, true, a);
+        if (e != cudaSuccess) return e;
+        return launch_kernel(items_table_kernel, dim3((unsigned)blocks), dim3(128), 0, st, true, a);   // active blocks only
     }
     if (a.variant == 4)
-        return a.probf ? launch_tile_variant<4, 64, true, OUTL>(a, st) : launch_tile_variant<4, 64, false, OUTL>(a, st);
+        return a.probf ? launch_tile_variant<4, 64, true, OUTL>(a, st, pdl) : launch_tile_variant<4, 64, false, OUTL>(a, st, pdl);
     if (a.variant == 5)   // one warp per CTA: a finished warp frees its slot at once (small, uneven grids)
-        return a.probf ? launch_tile_variant<1, 32, true, OUTL>(a, st) : launch_tile_variant<1, 32, false, OUTL>(a, st);
+        return a.probf ? launch_tile_variant<1, 32, true, OUTL>(a, st, pdl) : launch_tile_variant<1, 32, false, OUTL>(a, st, pdl);
     // variant 1: 4 x 4 micro-tiles with 256 threads (8 warps share each tile's tests); variant 2: 8 x 8 with
     // 64 threads; variant 3: one warp per step (8 x 16 lanes).  The caller picks one (autotuned per size).
     const bool many = a.variant == 2;
     if (a.variant == 3)
-        return a.probf ? launch_warp_variant<4, 8, true, OUTL>(a, st) : launch_warp_variant<4, 8, false, OUTL>(a, st);
+        return a.probf ? launch_warp_variant<4, 8, true, OUTL>(a, st, pdl) : launch_warp_variant<4, 8, false, OUTL>(a, st, pdl);
     if (a.probf)
-        return many ? launch_variant<64, 8, 8, 8, true, OUTL>(a, st) : launch_variant<256, 4, 4, 16, true, OUTL>(a, st);
-    return many ? launch_variant<64, 8, 8, 8, false, OUTL>(a, st) : launch_variant<256, 4, 4, 16, false, OUTL>(a, st);
+        return many ? launch_variant<64, 8, 8, 8, true, OUTL>(a, st, pdl)
+                    : launch_variant<256, 4, 4, 16, true, OUTL>(a, st, pdl);
+    return many ? launch_variant<64, 8, 8, 8, false, OUTL>(a, st, pdl)
+                : launch_variant<256, 4, 4, 16, false, OUTL>(a, st, pdl);
 }
 
-cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st) {
-    return a.polys ? launch_collide_t<true>(a, st) : launch_collide_t<false>(a, st);
+cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st, bool pdl) {
+    return a.polys ? launch_collide_t<true>(a, st, pdl) : launch_collide_t<false>(a, st, pdl);
 }
 
 }  // namespace mhc

@@ -420,6 +420,7 @@ __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Reg
 // instruction fetch was its largest stall).
 template <int LAYOUTS>
 __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
+    pdl_start();
     if ((int)blockIdx.x >= a.gen_blocks) {               // the risk preparation, independent of generation
         prepare_block(a.prep, blockIdx.x - a.gen_blocks, a.prep_blocks);
         return;
@@ -457,6 +458,7 @@ __global__ void __launch_bounds__(128) gen_kernel(const GenArgs a) {
 
 // Bounding box of the 32 pose centres of each bound tile at each step (warp min/max reduction).
 __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
+    pdl_start();
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long total = (long long)a.n_warps * a.max_steps;
     if (g >= total) return;
@@ -502,12 +504,11 @@ cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st) {
+cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st, bool pdl) {
     const long long total = (long long)a.n_warps * a.max_steps;
     if (total <= 0) return cudaSuccess;
     const long long blocks = (total + 7) / 8;
-    bounds_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(bounds_kernel, dim3((unsigned)blocks), dim3(256), 0, st, pdl, a);
 }
 
 }  // namespace mhc

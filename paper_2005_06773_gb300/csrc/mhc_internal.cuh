@@ -137,6 +137,34 @@ struct BoundsArgs {
 // Risk accumulators: one contiguous block of 64-bit words, zeroed before every assessment.  Masses and
 // log-survival sums are unsigned fixed point (kFixProb / kFixLog fractional bits): every term is an FP32
 // value converted exactly, and integer atomics add them exactly and in any order.
+// Programmatic dependent launch.  Every kernel of the library starts with pdl_start(): it lets the next
+// kernel of the stream be scheduled as soon as every block of this one is running, then waits until the
+// previous kernel of the stream has completed and its writes are visible (a no-op for a kernel launched
+// without the attribute).  A dependent's blocks thus sit resident, waiting, while its predecessor's tail
+// runs, instead of being launched after it ends.  Because every block waits first, a kernel completes only
+// after its predecessor did, so the ordering stays transitive along the chain.
+__device__ __forceinline__ void pdl_start() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// kernel<<<grid, block, smem, st>>>(args...), with programmatic stream serialization when pdl is set.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 constexpr int kFixProb = 62;   // probability masses: every accumulated sum is at most 1
 constexpr int kFixLog = 40;    // sums of -log(1 - p): each term capped at 2^22
 
@@ -156,6 +184,23 @@ struct RiskScratch {
     long long n_words;             // words to zero
 };
 
+// A 32 x 32 block of the step-item layout (variant 6) with active steps, recorded by the listing kernel so
+// that an item needs no descriptor search: table entry (i, j) of the block at entry0 + i h_b + j, the
+// pair's squared circumradius sum and the two shapes' half extents and radii.
+struct __align__(16) ItemBlock {
+    long long entry0;
+    int h_b, pair, rows, cols;
+    float rc2, la, wa, ra, lb, wb, rb;
+};
+
+// One item of the step-item layout: an active step k of block gw, with the pose indices of the step's first
+// row of A and first column of B (pa = pose_a + k h_a, pb = pose_b + k h_b), so that its poses are one
+// load away from the item.
+struct StepItem {
+    long long pa, pb;
+    int gw, k;
+};
+
 struct CollideArgs {
     const ObjDesc *objs;
     const PairDesc *pairs;    // in collision-grid order (tile_start over that order; index = table order)
@@ -166,10 +211,11 @@ struct CollideArgs {
     int fill_blocks;          // 1: each warp writes -1 to its own block first (variant 5; no fill launch)
     int max_ctas;             // > 0: at most this many CTAs for variants 4, 5 (the warps loop over the blocks)
     // variant 6: the item list (active (block, step) pairs) and its length, zeroed by the caller
-    int2 *items;
+    StepItem *items;
     unsigned long long *item_count;
     int *first32;             // [n_entries] first overlapping step per table entry (INT_MAX: none)
     int *active;              // [4 n_tiles] blocks with at least one active step, and their number (zeroed)
+    ItemBlock *blocks;        // [4 n_tiles] the records of the active blocks (indexed by block)
     unsigned long long *active_count;
     long long max_items;      // capacity: 4 n_tiles x max_steps
     int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile,
@@ -228,13 +274,15 @@ __device__ __forceinline__ float neg_log_survival(float p) {
     return p >= 1.0f ? kMaxLogTerm : fminf(-log1pf(-p), kMaxLogTerm);
 }
 
+// pdl: the launch follows another kernel of the library on the same stream with nothing in between, so
+// it may use programmatic dependent launch (see launch_kernel).
 cudaError_t launch_generate(const GenArgs &a, cudaStream_t st);
-cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st);
-cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st);   // table[0, n) = -1
-cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);               // stores first hits only
+cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st, bool pdl = false);
+cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st, bool pdl = false);   // table[0, n) = -1
+cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st, bool pdl = false);  // stores first hits only
 cudaError_t launch_risk_prepare(const RiskArgs &a, cudaStream_t st);             // zero + normalise
 int risk_tail_launches(const RiskArgs &a);   // kernels launch_risk_tail launches
-cudaError_t launch_risk_tail(const RiskArgs &a, cudaStream_t st);                // ego walk + finish
-cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st, bool with_prepare = true);
+cudaError_t launch_risk_tail(const RiskArgs &a, cudaStream_t st, bool pdl = false);   // ego walk + finish
+cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st, bool with_prepare = true, bool pdl = false);
 
 }  // namespace mhc

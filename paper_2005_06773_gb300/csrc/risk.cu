@@ -41,9 +41,13 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // blocks [0, n_obj) normalise one object each; every block zeroes a slice of the accumulators
-__global__ void __launch_bounds__(256) prepare_kernel(const PrepArgs a) { prepare_block(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256) prepare_kernel(const PrepArgs a) {
+    pdl_start();
+    prepare_block(a, blockIdx.x, gridDim.x);
+}
 
 __global__ void __launch_bounds__(64) scan_kernel(const RiskArgs a) {
+    pdl_start();
     // dynamic: [N] u64 masses | [N] u32 counts | [64][N] u64 log-survival cells of the tile's EGO hypotheses
     extern __shared__ unsigned long long s_dyn64[];
     __shared__ unsigned long long s_row_mass[kTile];
@@ -208,6 +212,7 @@ __device__ void convert_walk_totals(const RiskArgs &a, long long t, long long nt
 // Every CTA first converts a slice of the pair totals; the last CTA to finish converts the walk's own
 // totals (or a separate grid-wide kernel does, for large batches).
 __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
+    pdl_start();
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31;
     convert_pair_totals(a, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
@@ -325,6 +330,7 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
 // The walk's totals of a large batch, grid-wide after the walk (and the pair totals too when there is no
 // EGO hypothesis to walk, which a valid scenario never has).
 __global__ void __launch_bounds__(256) totals_kernel(const RiskArgs a) {
+    pdl_start();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
     if (a.h_e == 0) convert_pair_totals(a, t, nt);
     convert_walk_totals(a, t, nt);
@@ -350,22 +356,27 @@ int risk_tail_launches(const RiskArgs &a) {
     return (a.h_e > 0 ? 1 : 0) + (a.h_e > 0 && convert_elements(a) <= kConvertInWalk ? 0 : 1);
 }
 
-cudaError_t launch_risk_tail(const RiskArgs &args, cudaStream_t st) {
+cudaError_t launch_risk_tail(const RiskArgs &args, cudaStream_t st, bool pdl) {
     RiskArgs a = args;
     const long long conv = convert_elements(a);
     a.convert_in_walk = a.h_e > 0 && conv <= kConvertInWalk;
-    if (a.h_e > 0) ego_kernel<<<(unsigned)((a.h_e + 1) / 2), 64, 0, st>>>(a);
+    if (a.h_e > 0) {
+        cudaError_t e = launch_kernel(ego_kernel, dim3((unsigned)((a.h_e + 1) / 2)), dim3(64), 0, st, pdl, a);
+        if (e != cudaSuccess) return e;
+        pdl = true;
+    }
     if (!a.convert_in_walk) {
         long long blocks = (conv + 255) / 256;
         if (blocks > 152 * 8) blocks = 152 * 8;
-        totals_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+        return launch_kernel(totals_kernel, dim3((unsigned)blocks), dim3(256), 0, st, pdl, a);
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
-cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st, bool with_prepare) {
+cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st, bool with_prepare, bool pdl) {
     cudaError_t e = with_prepare ? launch_risk_prepare(a, st) : cudaSuccess;
     if (e != cudaSuccess) return e;
+    pdl = pdl || with_prepare;
     if (a.n_tiles > 0) {
         if (a.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
         size_t smem = 0;
@@ -375,10 +386,11 @@ cudaError_t launch_risk(const RiskArgs &a, cudaStream_t st, bool with_prepare) {
             e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        scan_kernel<<<(unsigned)a.n_tiles, 64, smem, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = launch_kernel(scan_kernel, dim3((unsigned)a.n_tiles), dim3(64), smem, st, pdl, a);
+        if (e != cudaSuccess) return e;
+        pdl = true;
     }
-    return launch_risk_tail(a, st);
+    return launch_risk_tail(a, st, pdl);
 }
 
 }  // namespace mhc
