@@ -33,7 +33,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pose-pair tests/s"
 UNIT = "tests/s"
-PROFILE_NOTE = os.path.join(ROOT, "profiles", "collide_tile_kernel_intersection11.md")
+# committed ncu summaries of the collision stage on the benchmark scene, per collision layout
+PROFILE_NOTES = {5: os.path.join(ROOT, "profiles", "collide_tile_kernel_intersection11.md"),
+                 6: os.path.join(ROOT, "profiles", "items_kernels_intersection11.md")}
 COLLIDE_SRC = [os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", f) for f in ("collide.cu", "mhc_internal.cuh")]
 # algorithmic FP32-pipe lane instructions per unit of collision work (roofline section)
 OPS_PER_BROAD_TEST = 3.0      # 2 FFMA (expanded squared distance) + 1 compare
@@ -41,7 +43,8 @@ OPS_PER_NARROW_TEST = 30.0    # separating-axis test of two rectangles, worst sh
 FP32_LANES_PER_SM = 128
 # the kernel behind each collision layout (MHC_OPT_COLLIDE_VARIANT)
 COLLIDE_KERNELS = {1: "collide_kernel<256, 4, 4, 16>", 2: "collide_kernel<64, 8, 8, 8>", 3: "collide_warp_kernel<4, 8>",
-                   4: "collide_tile_kernel<4, 64>", 5: "collide_tile_kernel<1, 32>", 6: "items_kernel"}
+                   4: "collide_tile_kernel<4, 64>", 5: "collide_tile_kernel<1, 32>",
+                   6: "items_list_kernel + items_kernel + items_table_kernel (per-launch figures average the three)"}
 
 
 def parse():
@@ -121,8 +124,10 @@ def collide_code_sha256() -> str:
 def traffic_from_profile(variant: int):
     """DRAM bytes per collide launch from the committed ncu summary, if it was taken on this code and
     this collision layout."""
+    if variant not in PROFILE_NOTES:
+        return None
     try:
-        text = open(PROFILE_NOTE).read()
+        text = open(PROFILE_NOTES[variant]).read()
         sha = collide_code_sha256()
     except OSError:
         return None
@@ -711,7 +716,8 @@ def run_mhc(args):
                        "note": "the same step replayed from a plan: layout once, descriptor upload + kernels as one CUDA graph"},
         "collision_work": {"nominal_tests_per_launch": sc.n_tests(), "executed_tests_per_launch": executed / max(coll_n, 1),
                            "narrow_tests_per_launch": narrow / max(coll_n, 1),
-                           "nominal_tests_per_s_collide_only": sc.n_tests() / avg_coll_s},
+                           "collide_launches_per_step": coll_n / max(prof_steps, 1),
+                           "nominal_tests_per_s_collide_only": sc.n_tests() * prof_steps / (coll_ms / 1e3)},
         "roofline": {"bound": "alu", "kernel": COLLIDE_KERNELS.get(tuned[0], "collide"), "achieved": achieved, "peak": peak,
                      "unit": "T FP32-lane-instr/s", "frac": achieved / peak, "traffic": traffic,
                      "avg_launch_ms": 1e3 * avg_coll_s, "ops_per_launch": ops_per_launch,
