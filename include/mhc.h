@@ -184,7 +184,7 @@ void mhc_destroy(mhc_ctx *ctx);
  *                    pair's first step by atomicMin in scratch, the table and the risk terms written after);
  *                    for small scenes (at most 2^22 items and 2^26 table entries; larger ones use 5);
  *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 4 for at
- *                 least 32 tiles per SM and 5 below. */
+ *                 least 32 tiles per SM, and below that 6 where it applies, else 5. */
 #define MHC_OPT_COLLIDE_VARIANT 3
 /*   MHC_OPT_GEN_SCAN  trajectory generation: 1 one warp per hypothesis, its sub-steps in parallel (warp
  *                 scans of the state maps and of the heading / position increments); 0 one thread per

@@ -529,6 +529,13 @@ int log2_floor(long long v) {
 
 // Collision configuration for a scenario: the forced variant, else the tuned one of its size class, else
 // the default (a warp per tile for at least 32 tiles per SM, else a warp per quarter tile).
+// The collision layout without tuning.  Large scenes: a warp per tile in step order; small ones, whose
+// time is the closest pairs' long step chains: every active step in parallel where the item list fits,
+// else a warp per quarter tile.
+int default_variant(const mhc_ctx *ctx, const Layout &L) {
+    return L.n_tiles >= 32LL * ctx->n_sm ? 4 : (items_eligible(L) ? 6 : 5);
+}
+
 void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &variant, int &cull) {
     cull = ctx->cull;
     if (ctx->variant != 0) { variant = ctx->variant; return; }
@@ -539,7 +546,7 @@ void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &v
             cull = t.cull;
             return;
         }
-    variant = L.n_tiles >= 32LL * ctx->n_sm ? 4 : 5;
+    variant = default_variant(ctx, L);
 }
 
 // Device buffers for the risk outputs of one assessment, carved from the arena.
@@ -600,7 +607,13 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         std::memset(&g.prep, 0, sizeof g.prep);
         if (fused) {
             g.prep = prep_of(r);
-            g.prep_blocks = L.n_obj > 304 ? L.n_obj : 304;
+            // enough CTAs to zero the accumulators at about 2048 words each (at least one per object,
+            // at most two per SM): extra CTAs would only take residency from the generation warps
+            const long long words = acc_words(L) + L.h_e;
+            long long nb = (words + 2047) / 2048;
+            if (nb > 304) nb = 304;
+            if (nb < L.n_obj) nb = L.n_obj;
+            g.prep_blocks = (int)nb;
         }
         g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
@@ -938,7 +951,7 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
     int bv = 1, bc = 1, rc = MHC_OK;
     // the layout used without tuning (culling on); kept unless another is at least 10 % faster, so that
     // near-ties do not flip the choice from run to run
-    const int v_default = L.n_tiles >= 32LL * ctx->n_sm ? 4 : 5;
+    const int v_default = default_variant(ctx, L);
     ctx->profile = true;
     for (int cull = 1; cull >= 0 && rc == MHC_OK; --cull) {
         for (int v = 1; v <= kCollideVariants && rc == MHC_OK; ++v) {
