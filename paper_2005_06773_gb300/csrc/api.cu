@@ -212,6 +212,7 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
     S.lsum_base = L.n_lsum;
     S.mass_base = L.n_mass;
     S.step_base = L.n_steps_total;
+    S.e_traj = L.objs[S.ego].traj_off;
     L.h_e += S.h_e;
     L.n_lsum += (long long)S.h_e * N * n_obj_s;
     L.n_mass += (long long)S.h_e * n_obj_s;

@@ -419,7 +419,7 @@ __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Reg
 // holding one layout only has a smaller instruction footprint: the integration is latency-bound and
 // instruction fetch was its largest stall).
 template <int LAYOUTS>
-__global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
+__global__ void __launch_bounds__(128, 8) gen_kernel(const GenArgs a) {
     pdl_start();
     if ((int)blockIdx.x >= a.gen_blocks) {               // the risk preparation, independent of generation
         prepare_block(a.prep, blockIdx.x - a.gen_blocks, a.prep_blocks);

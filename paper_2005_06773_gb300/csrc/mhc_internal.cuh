@@ -88,6 +88,7 @@ struct ScenDesc {
     long long e_base;         // first global EGO hypothesis (per-EGO-hypothesis outputs, hits)
     long long lsum_base, mass_base;
     long long step_base;      // the scenario's n_steps entries of attr_step
+    long long e_traj;         // global index of the EGO object's hypothesis 0 (its probabilities)
 };
 
 // Sub-steps of a vehicle hypothesis's low-speed regime [low_lo, low_hi) and its stop sub-step (n_stop = N K

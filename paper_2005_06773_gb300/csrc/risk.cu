@@ -206,11 +206,14 @@ __device__ void convert_walk_totals(const RiskArgs &a, long long t, long long nt
 //    hypotheses of its scenario more probable than it, ties by index, counted 32 at a time with ballots on
 //    integer keys (probabilities are non-negative, so their bit patterns order like the values);
 //  * otherwise the chronological walk: the (step, object) cells are read in ascending order 32 at a time,
-//    128 per group with the four loads in flight together; a chunk with a non-empty cell gets an exclusive
+//    384 per group with the twelve loads in flight together; a chunk with a non-empty cell gets an exclusive
 //    warp prefix product of the survival factors (1 - q), so each cell knows the survival S of every
 //    earlier cell and contributes S q.
 // Every CTA first converts a slice of the pair totals; the last CTA to finish converts the walk's own
 // totals (or a separate grid-wide kernel does, for large batches).
+constexpr int kEscapeBatch = 8;    // escape ranking: 256 EGO hypotheses' keys in flight per round
+constexpr int kWalkBatch = 12;     // chronological walk: 384 cells in flight per round
+
 __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
     pdl_start();
     __shared__ bool s_last;
@@ -226,26 +229,25 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
         const ScenDesc sd = a.scens[lo];
         const int N = sd.n_steps, n_obj = sd.n_obj;
         const long long i = g - sd.e_base;
-        const ObjDesc &E = a.objs[sd.ego];
-        const double pe = a.prob[E.traj_off + i];
-        const float pef = a.probf[E.traj_off + i];
+        const double pe = a.prob[sd.e_traj + i];
+        const float pef = a.probf[sd.e_traj + i];
         const unsigned long long hits = a.acc.hits[g];
         double naive = 0.0, cond = 0.0, indep = 0.0;
         if (!hits) {
             if (a.escape) {
                 const long long key = __double_as_longlong(pe);
                 int rank = 0;
-                for (int q0 = 0; q0 < sd.h_e; q0 += 128) {   // 4 x 32 entries, every load issued first
-                    unsigned long long hq[4];
-                    long long kq[4];
+                for (int q0 = 0; q0 < sd.h_e; q0 += 32 * kEscapeBatch) {   // every load of a batch issued first
+                    unsigned long long hq[kEscapeBatch];
+                    long long kq[kEscapeBatch];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kEscapeBatch; ++u) {
                         const int q = q0 + 32 * u + lane;
                         hq[u] = q < sd.h_e ? a.acc.hits[sd.e_base + q] : 1ull;
-                        kq[u] = q < sd.h_e ? __double_as_longlong(a.prob[E.traj_off + q]) : 0ll;
+                        kq[u] = q < sd.h_e ? __double_as_longlong(a.prob[sd.e_traj + q]) : 0ll;
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kEscapeBatch; ++u) {
                         const int q = q0 + 32 * u + lane;
                         const bool above = hq[u] == 0ull && (kq[u] > key || (kq[u] == key && q < i));
                         rank += __popc(__ballot_sync(0xffffffffu, above));
@@ -267,19 +269,19 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
             for (int d = 16; d > 0; d >>= 1) surv *= __shfl_xor_sync(0xffffffffu, surv, d);
             naive = warp_sum(mass_sum);
             indep = 1.0 - surv;
-            // chronological walk over the cells
+            // chronological walk over the cells, kWalkBatch chunks of 32 loaded at once
             const unsigned long long *lc = a.acc.lsum + sd.lsum_base + i * N * n_obj;
             const long long cells = (long long)N * n_obj;
             double carry = 1.0, part = 0.0;   // carry: survival product of every cell before the chunk
-            for (long long g0 = 0; g0 < cells; g0 += 128) {
-                unsigned long long lv[4];
+            for (long long g0 = 0; g0 < cells; g0 += 32 * kWalkBatch) {
+                unsigned long long lv[kWalkBatch];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kWalkBatch; ++u) {
                     const long long c = g0 + 32 * u + lane;
                     lv[u] = c < cells ? lc[c] : 0ull;
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kWalkBatch; ++u) {
                     const unsigned long long lf = lv[u];
                     if (!__ballot_sync(0xffffffffu, lf != 0ull)) continue;     // empty cells change nothing
                     const long long c = g0 + 32 * u + lane;

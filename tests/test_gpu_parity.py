@@ -277,6 +277,37 @@ def test_autotune_picks_a_layout_and_keeps_results(mhc):
         c.close()
 
 
+@pytest.mark.parametrize("name", ["mixed_small", "paper_s1", "outline_shapes"])
+def test_profiled_and_overlapped_launches_agree(mhc, ctx, name):
+    """Without profiling, consecutive kernels are launched as programmatic dependents (each waits for its
+    predecessor inside the kernel); with profiling, event records separate them.  Both orders must give
+    the same poses, table and risk outputs (FP64 scalar totals to 1e-12), in every collision layout."""
+    sc = scene(name)
+    w = S.random_weights(sc, 17)
+    try:
+        for variant in (0, 4, 5, 6):
+            ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, variant)
+            ctx.profile(False)
+            p1, t1, r1 = mhc.evaluate(ctx, sc, weights=w)
+            ctx.profile(True)
+            p2, t2, r2 = mhc.evaluate(ctx, sc, weights=w)
+            ctx.profile(False)
+            ctx.profile_read(reset=True)
+            torch.cuda.synchronize()
+            for k in p1:
+                assert torch.equal(p1[k], p2[k]), (variant, k)
+            assert torch.equal(t1, t2), variant
+            for k in r1:
+                a, b = r1[k].cpu().numpy(), r2[k].cpu().numpy()
+                if k == "scalars":
+                    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-18)
+                else:
+                    np.testing.assert_array_equal(a, b, err_msg=f"{k} variant {variant}")
+    finally:
+        ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, 0)
+        ctx.profile(False)
+
+
 def test_deterministic_and_stream_independent(mhc, ctx):
     sc = scene("mixed_small")
     s2 = torch.cuda.Stream()
