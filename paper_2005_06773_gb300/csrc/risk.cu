@@ -206,11 +206,23 @@ __device__ void convert_walk_totals(const RiskArgs &a, long long t, long long nt
 //    hypotheses of its scenario more probable than it, ties by index, counted 32 at a time with ballots on
 //    integer keys (probabilities are non-negative, so their bit patterns order like the values);
 //  * otherwise the chronological walk: the (step, object) cells are read in ascending order 32 at a time,
-//    384 per group with the twelve loads in flight together; a chunk with a non-empty cell gets an exclusive
-//    warp prefix product of the survival factors (1 - q), so each cell knows the survival S of every
-//    earlier cell and contributes S q.
+//    384 per group with the twelve loads in flight together; a warp prefix sum of the cells' fixed-point
+//    log-survival sums L (exact 64-bit integers) gives each cell the survival S = exp(-sum of the earlier
+//    cells' L), and the cell contributes S q with q = 1 - exp(-L) (Eq. p21 over the cell's collisions:
+//    the product of their survival factors is exp(-L)).  Every term is formed in FP32 (relative error
+//    below 5e-7) and the terms are summed in FP64.
 // Every CTA first converts a slice of the pair totals; the last CTA to finish converts the walk's own
 // totals (or a separate grid-wide kernel does, for large batches).
+constexpr float kLogScale = 1.0f / 1099511627776.0f;   // 2^-40: the fixed point of the log-survival sums
+
+// exp(-x 2^-40) for a fixed-point log-survival sum x: x = hi + lo with hi the nearest FP32 value (exact
+// as an integer) and lo the small remainder, so the FP32 rounding of x does not reach the exponent.
+__device__ __forceinline__ float survival(unsigned long long x) {
+    const float hi = __ull2float_rn(x);
+    const long long lo = (long long)(x - __float2ull_rz(hi));
+    return expf(-hi * kLogScale) * (1.0f - (float)lo * kLogScale);
+}
+
 constexpr int kEscapeBatch = 8;    // escape ranking: 256 EGO hypotheses' keys in flight per round
 constexpr int kWalkBatch = 12;     // chronological walk: 384 cells in flight per round
 
@@ -269,10 +281,15 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
             for (int d = 16; d > 0; d >>= 1) surv *= __shfl_xor_sync(0xffffffffu, surv, d);
             naive = warp_sum(mass_sum);
             indep = 1.0 - surv;
-            // chronological walk over the cells, kWalkBatch chunks of 32 loaded at once
+            // chronological walk over the cells, kWalkBatch chunks of 32 loaded at once.  A cell holds
+            // L = sum of -log(1 - p) of its collisions in fixed point, so the survival of every earlier cell
+            // is exp(-(exact integer prefix sum of L)) and the cell's own collision probability is
+            // 1 - exp(-L): the chunks' scans are 64-bit integer additions, independent of each other but
+            // for the carried total
             const unsigned long long *lc = a.acc.lsum + sd.lsum_base + i * N * n_obj;
             const long long cells = (long long)N * n_obj;
-            double carry = 1.0, part = 0.0;   // carry: survival product of every cell before the chunk
+            unsigned long long carry = 0;     // L summed over every cell before the chunk
+            double part = 0.0;
             for (long long g0 = 0; g0 < cells; g0 += 32 * kWalkBatch) {
                 unsigned long long lv[kWalkBatch];
 #pragma unroll
@@ -283,26 +300,22 @@ __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
 #pragma unroll
                 for (int u = 0; u < kWalkBatch; ++u) {
                     const unsigned long long lf = lv[u];
-                    if (!__ballot_sync(0xffffffffu, lf != 0ull)) continue;     // empty cells change nothing
-                    const long long c = g0 + 32 * u + lane;
-                    const float qf = lf ? -expm1f(-(float)lf * (1.0f / 1099511627776.0f)) : 0.0f;  // 2^-40
-                    double incl = 1.0 - (double)qf;
+                    unsigned long long incl = lf;
 #pragma unroll
                     for (int d = 1; d < 32; d <<= 1) {
-                        const double v = __shfl_up_sync(0xffffffffu, incl, d);
-                        if (lane >= d) incl *= v;
+                        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (lane >= d) incl += v;
                     }
-                    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
-                    if (lane == 0) excl = 1.0;
-                    const double eff = carry * excl * (double)qf;
-                    part += eff;
-                    if (lf) {
-                        const int k = (int)(c / n_obj), b = (int)(c - (long long)k * n_obj);
-                        const unsigned long long w = to_fixed(pef * (float)eff, kFixProb);
-                        atomicAdd(a.acc.attr_obj + sd.obj0 + b, w);
-                        atomicAdd(a.acc.attr_step + sd.step_base + k, w);
-                    }
-                    carry *= __shfl_sync(0xffffffffu, incl, 31);
+                    const unsigned long long before = carry + (incl - lf);
+                    carry += __shfl_sync(0xffffffffu, incl, 31);
+                    if (!lf) continue;                                    // an empty cell adds nothing
+                    const long long c = g0 + 32 * u + lane;
+                    const float eff = survival(before) * -expm1f(-(float)lf * kLogScale);
+                    part += (double)eff;
+                    const int k = (int)(c / n_obj), b = (int)(c - (long long)k * n_obj);
+                    const unsigned long long w = to_fixed(pef * eff, kFixProb);
+                    atomicAdd(a.acc.attr_obj + sd.obj0 + b, w);
+                    atomicAdd(a.acc.attr_step + sd.step_base + k, w);
                 }
             }
             cond = warp_sum(part);
