@@ -27,6 +27,17 @@
  *       Euclidean distance when disjoint and minus the penetration depth when they intersect.
  *  R-i  conditional probability (Eq. p21) is applied per EGO trajectory over its colliding
  *       (CO object, CO trajectory, step) entries in ascending (step, object, trajectory) order.
+ *  R-s  path hypotheses (Section IV-B.2b): a vehicle given paths follows path i_b instead of a constant
+ *       steering angle; a path is three straight sections (a point and a direction each), the first
+ *       followed for t < 1.0 s, the second for t < 1.5 s, the third after (the paper's sampling instants
+ *       1.0 / 1.5 / 2.0 s mark the sections' sample points).
+ *  R-t  lateral controller, Eq. (controller), evaluated before every sub-step: delta_f in degrees from
+ *       v_V = v_n in m/s, d_path in m and e_psi in rad; d_path is the signed distance from the centre of
+ *       gravity predicted T_P = 0.5 s ahead along the course (x + T_P v cos(psi + beta), ...) to the
+ *       active section's line, positive when the line lies to the vehicle's left; e_psi = psi_section -
+ *       psi wrapped to [-pi, pi]; no dynamic weighting (not specified).
+ *  R-u  steering limits: |delta_f| <= 0.5 rad and |delta_n - delta_{n-1}| <= 0.5 rad/s x tau_i, with
+ *       delta_{-1} = 0 (the current steering angle is not an input).
  */
 #include <math.h>
 #include <stdint.h>
@@ -44,6 +55,39 @@
  * Trajectory generation (Section IV-B)
  * ------------------------------------------------------------------------------------------------ */
 
+/* Path following (readings R-s, R-t, R-u). */
+#define ORC_PATH_T1 1.0          /* s: end of the first section */
+#define ORC_PATH_T2 1.5          /* s: end of the second section */
+#define ORC_CTRL_TP 0.5          /* s: prediction time of the centre of gravity */
+#define ORC_DELTA_MAX 0.5        /* rad */
+#define ORC_DELTA_RATE 0.5       /* rad/s */
+
+static const double ORC_PI = 3.14159265358979323846;
+
+/* Eq. (controller): front steering angle in degrees from the distance and yaw errors. */
+static double controller_deg(double v, double d_path, double e_psi) {
+    double g = fabs((-0.018 * v + 1.5) * d_path);
+    return (g + 0.5) * d_path + (-g + 9.5) * (3.8197 * e_psi);
+}
+
+/* Steering angle for sub-step n of a path hypothesis: the controller's command for the active section,
+   then the rate and angle limits relative to the previous sub-step's angle. */
+static double path_steering(const double *path, long n, double tau_i, double x, double y, double psi,
+                            double beta, double v, double delta_prev) {
+    double t = (double)n * tau_i;
+    int s = t < ORC_PATH_T1 ? 0 : (t < ORC_PATH_T2 ? 1 : 2);
+    double sx = path[3 * s], sy = path[3 * s + 1], spsi = path[3 * s + 2];
+    double px = x + ORC_CTRL_TP * v * cos(psi + beta);            /* predicted centre of gravity */
+    double py = y + ORC_CTRL_TP * v * sin(psi + beta);
+    double d_path = (sx - px) * -sin(spsi) + (sy - py) * cos(spsi);   /* line to the left: positive */
+    double e_psi = spsi - psi;
+    e_psi -= 2.0 * ORC_PI * floor((e_psi + ORC_PI) / (2.0 * ORC_PI));
+    double cmd = controller_deg(v, d_path, e_psi) * ORC_PI / 180.0;
+    double step = ORC_DELTA_RATE * tau_i;
+    double delta = delta_prev + fmin(fmax(cmd - delta_prev, -step), step);
+    return fmin(fmax(delta, -ORC_DELTA_MAX), ORC_DELTA_MAX);
+}
+
 /* Speed at sub-step n (reading R-d). */
 static double speed_at(double v0, double vdot, double tau_i, long n) {
     return v0 + (double)n * (vdot * tau_i);
@@ -55,8 +99,8 @@ static double speed_at(double v0, double vdot, double tau_i, long n) {
  * params = {m, I_z, l_f, l_r, c_af, c_ar}.  Writes N poses (x, y, psi).
  */
 static void vehicle_trajectory(double x0, double y0, double psi0, double v0, double vdot, double delta,
-                               const double *params, int model, double tau, int n_steps, int substeps,
-                               double *ox, double *oy, double *opsi) {
+                               const double *path, const double *params, int model, double tau, int n_steps,
+                               int substeps, double *ox, double *oy, double *opsi, double *odelta) {
     const double m = params[0], Iz = params[1], lf = params[2], lr = params[3];
     const double caf = params[4], car = params[5];
     const double L = lf + lr;
@@ -66,11 +110,13 @@ static void vehicle_trajectory(double x0, double y0, double psi0, double v0, dou
     double ax = vdot, ay = 0.0;           /* vehicle-frame accelerations, reading R-b */
     int stopped = 0;
     long n_total = (long)n_steps * substeps;
+    if (path) delta = 0.0;                /* reading R-u: delta_{-1} = 0 */
     for (long n = 0; n < n_total; ++n) {
         if (!stopped) {
             double v = speed_at(v0, vdot, tau_i, n);
             double v_next = speed_at(v0, vdot, tau_i, n + 1);
             double betadot, rdot;
+            if (path) delta = path_steering(path, n, tau_i, x, y, psi, beta, v, delta);
             if (model == ORC_MODEL_KIN || v < ORC_V_MIN) {
                 /* kinematic single-track limit, reading R-e */
                 beta = atan(lr * tan(delta) / L);
@@ -110,6 +156,7 @@ static void vehicle_trajectory(double x0, double y0, double psi0, double v0, dou
                 x = xn; y = yn; psi = psi_n; beta = beta_n; r = r_n; ax = ax_n; ay = ay_n;
             }
         }
+        if (odelta) odelta[n] = delta;
         if ((n + 1) % substeps == 0) {
             long k = (n + 1) / substeps - 1;
             ox[k] = x; oy[k] = y; opsi[k] = psi;
@@ -151,6 +198,31 @@ static void pedestrian_trajectory(double x0, double y0, double heading, double v
     }
 }
 
+/* Paths of the objects (set by orc_set_paths; none by default): object o with path_off[o] >= 0 follows
+   path i_b at paths[9 (path_off[o] + i_b) ..], three sections of (x, y, psi) each (reading R-s). */
+static int g_path_n = 0;
+static const long *g_path_off = 0;
+static const double *g_path_v = 0;
+
+int orc_set_paths(int n_obj, const long *path_off, const double *paths) {
+    g_path_n = n_obj; g_path_off = path_off; g_path_v = paths;
+    return 0;
+}
+
+static const double *object_path(int o, int ib) {
+    if (!g_path_off || o >= g_path_n || g_path_off[o] < 0) return 0;
+    return g_path_v + 9 * (g_path_off[o] + ib);
+}
+
+/* The steering angle of every sub-step of one path hypothesis (test access to readings R-t, R-u). */
+int orc_path_steering(double x0, double y0, double psi0, double v0, double vdot, const double *path,
+                      const double *params, int model, double tau, int n_steps, int substeps,
+                      double *out_x, double *out_y, double *out_psi, double *out_delta) {
+    vehicle_trajectory(x0, y0, psi0, v0, vdot, 0.0, path, params, model, tau, n_steps, substeps,
+                       out_x, out_y, out_psi, out_delta);
+    return 0;
+}
+
 /*
  * Generate every hypothesis of every object.  Inputs are flat per-object arrays; grids are concatenated
  * (grid_a of object o at grid_off[o], then its grid_b).  Hypothesis h of object o uses
@@ -170,8 +242,9 @@ int orc_generate(int n_obj, const int *kind, const double *x0, const double *y0,
             for (int ib = 0; ib < n_b[o]; ++ib, ++t) {
                 double *ox = out_x + t * n_steps, *oy = out_y + t * n_steps, *op = out_psi + t * n_steps;
                 if (kind[o] == ORC_VEHICLE) {
-                    vehicle_trajectory(x0[o], y0[o], psi0[o], v0[o], ga[ia], gb[ib], params + 6 * o, model,
-                                       tau, n_steps, substeps, ox, oy, op);
+                    const double *path = object_path(o, ib);
+                    vehicle_trajectory(x0[o], y0[o], psi0[o], v0[o], ga[ia], gb[ib], path, params + 6 * o, model,
+                                       tau, n_steps, substeps, ox, oy, op, NULL);
                 } else {
                     double heading = psi0[o] + gb[ib];
                     double v_start = (flags[o] & ORC_PED_ACCEL_GRID) ? v0[o] : ga[ia];

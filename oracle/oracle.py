@@ -121,12 +121,50 @@ def generate(sc) -> Dict[str, np.ndarray]:
     off = traj_offsets(sc)
     T, N = int(off[-1]), int(sc.n_steps)
     x = np.zeros((T, N), D); y = np.zeros((T, N), D); psi = np.zeros((T, N), D)
+    keep = _set_paths(sc)  # noqa: F841 (alive during the call)
     L.orc_generate(ctypes.c_int(len(sc.objects)), _p(ob["kind"], _ip), _p(ob["x0"], _dp), _p(ob["y0"], _dp),
                    _p(ob["psi0"], _dp), _p(ob["v0"], _dp), _p(ob["n_a"], _ip), _p(ob["n_b"], _ip),
                    _p(ob["grid_off"], _lp), _p(ob["grids"], _dp), _p(ob["params"], _dp), _p(ob["v_max"], _dp),
                    _p(ob["flags"], _ip), ctypes.c_double(sc.tau), ctypes.c_int(N), ctypes.c_int(int(sc.substeps)),
                    ctypes.c_int(int(sc.model)), _p(x, _dp), _p(y, _dp), _p(psi, _dp))
     return dict(x=x, y=y, psi=psi, c=np.cos(psi), s=np.sin(psi), traj_off=off)
+
+
+def _set_paths(sc):
+    """Registers the vehicles' paths (reading R-s: [n_b, 3 sections, (x, y, psi)]) with the C oracle for the
+    next call (none: cleared).  Returns the arrays, which must stay alive during that call."""
+    L = lib()
+    has = [getattr(o, "paths", None) is not None for o in sc.objects]
+    if not any(has):
+        L.orc_set_paths(ctypes.c_int(0), None, None)
+        return None
+    off, data, at = [], [], 0
+    for o, h in zip(sc.objects, has):
+        if h:
+            pa = np.asarray(o.paths, D).reshape(-1, 9)
+            off.append(at)
+            data.append(pa.reshape(-1))
+            at += pa.shape[0]
+        else:
+            off.append(-1)
+    off = _i64(off)
+    data = _f64(np.concatenate(data))
+    L.orc_set_paths(ctypes.c_int(len(sc.objects)), _p(off, _lp), _p(data, _dp))
+    return off, data
+
+
+def path_steering(x0, y0, psi0, v0, vdot, path, params=None, model=0, tau=0.1, n_steps=20, substeps=5):
+    """One path hypothesis (readings R-s .. R-u): poses [N] x, y, psi and the steering angle of every
+    sub-step [N K]."""
+    L = lib()
+    pa = _f64(np.asarray(path, D).reshape(-1))
+    pr = _f64(params if params is not None else _DEFAULT_PARAMS)
+    N, K = int(n_steps), int(substeps)
+    x = np.zeros(N, D); y = np.zeros(N, D); psi = np.zeros(N, D); dl = np.zeros(N * K, D)
+    L.orc_path_steering(ctypes.c_double(x0), ctypes.c_double(y0), ctypes.c_double(psi0), ctypes.c_double(v0),
+                        ctypes.c_double(vdot), _p(pa, _dp), _p(pr, _dp), ctypes.c_int(model), ctypes.c_double(tau),
+                        ctypes.c_int(N), ctypes.c_int(K), _p(x, _dp), _p(y, _dp), _p(psi, _dp), _p(dl, _dp))
+    return dict(x=x, y=y, psi=psi, delta=dl)
 
 
 def _set_polygons(sc):

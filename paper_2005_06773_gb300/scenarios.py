@@ -92,6 +92,7 @@ class Obj:
     v_max: float = 0.0
     flags: int = 0
     outline: Optional[np.ndarray] = None   # vehicles: convex outline, [n, 2] body-frame vertices (x ahead)
+    paths: Optional[np.ndarray] = None     # vehicles: [n_b, 3, 3] path sections (x, y, psi) to follow
 
     def __post_init__(self):
         for f in ("length", "width", "radius", "x0", "y0", "psi0", "v0", "v_max"):
@@ -102,6 +103,8 @@ class Obj:
             self.params = np.ascontiguousarray(self.params, dtype=F32)
         if self.outline is not None:
             self.outline = np.ascontiguousarray(np.asarray(self.outline).reshape(-1, 2), dtype=F32)
+        if self.paths is not None:
+            self.paths = np.ascontiguousarray(np.asarray(self.paths).reshape(-1, 3, 3), dtype=F32)
 
     @property
     def n_hyp(self) -> int:
