@@ -73,6 +73,8 @@ WORKLOADS = {
     "stress12": "stress12: 12 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps of 0.1 s, 66 object pairs",
     "paper_s2": "paper_s2: EGO 2058 (6 x 343) + 10 COs x 42 (6 x 7), 100 steps of 20 ms, EGO-only pairs",
     "outline11": "outline11: intersection11 with every car drawn as a convex octagon (4.5x1.8 m, corners cut 0.35 m)",
+    "paths11": "paths11: intersection11 with every car following lane paths under the lateral controller "
+               "(441 hypotheses = 63 accel x 7 paths)",
 }
 WORKLOAD = "intersection11"
 
@@ -87,6 +89,8 @@ def workload(rank: int = 0):
         return S.paper_s1s2(10, 6, seed=6 + rank)
     if WORKLOAD == "outline11":
         return S.with_outlines(S.intersection11(replica_seed(rank)), cut=0.35)
+    if WORKLOAD == "paths11":
+        return S.with_lane_paths(S.intersection11(replica_seed(rank), n_acc=63))
     return S.intersection11(replica_seed(rank))
 
 
@@ -740,6 +744,10 @@ def run_mhc(args):
                               workload="the benchmark scene with every car drawn as a convex octagon (corners cut "
                                        "0.35 m); roofline fraction counts each narrow test at the rectangle cost, "
                                        "so it is a lower bound"),
+            "paths11": dict(measure_workload(mhc, torch, S.with_lane_paths(S.intersection11(2, n_acc=63)), dev, 50,
+                                             flush, peak),
+                            workload="the benchmark scene with every car following 7 lane paths under the lateral "
+                                     "controller (63 accelerations x 7 paths = 441 hypotheses per car)"),
         }
         line["batch"] = measure_batch(mhc, torch, dev, 10, flush)
         line["serving"] = measure_serving(mhc, torch, dev, args.serve_seconds)

@@ -68,6 +68,17 @@ enum { MHC_MODEL_OT = 0, MHC_MODEL_KIN = 1 };     /* vehicle motion model */
  *       turn in the same direction, one turn in total): anything else, repeated vertices, non-finite
  *       coordinates or an outline on a pedestrian returns MHC_E_INVALID.  The static entry point
  *       (mhc_detect_collisions_static) takes rectangles only.
+ *   paths (vehicles; Section IV-B.2b): NULL drives hypothesis (i_a, i_b) with the constant steering angle
+ *       grid_b[i_b].  Otherwise hypothesis (i_a, i_b) follows path i_b, and grid_b's values are unused:
+ *       paths[9 i_b + 3 s + {0, 1, 2}] = (x, y, psi) of a point on section s and its direction (host,
+ *       metres and rad); section 0 is followed for t < 1.0 s, section 1 for t < 1.5 s, section 2 after.
+ *       Before every sub-step the lateral controller (Eq. controller) sets the front steering angle, in
+ *       degrees, from the speed, the signed distance d_path from the centre of gravity predicted 0.5 s
+ *       ahead along the course to the section's line (positive when the line lies to the vehicle's left)
+ *       and the yaw error e_psi = psi_section - psi (wrapped to [-pi, pi]); the angle is then held within
+ *       0.5 rad and within 0.5 rad/s of the previous sub-step's (0 before the first).  Non-finite values
+ *       or paths on a pedestrian return MHC_E_INVALID.  Path hypotheses use the thread-per-hypothesis
+ *       generation layout.
  */
 typedef struct {
     int32_t kind;
@@ -81,6 +92,7 @@ typedef struct {
     const float *veh_params;
     int32_t n_vertices;
     const float *vertices;
+    const float *paths;
 } mhc_object;
 
 /*

@@ -197,6 +197,26 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
             for (int q = 0; q < src.n_a; ++q)
                 L.regimes.push_back(speed_regime(src.v0, src.grid_a[q], sc->model, N * sc->substeps, d.tau_i_d));
         }
+        d.path_off = -1;
+        if (src.paths) {   // path hypotheses (Section IV-B.2b): n_b paths of three sections (x, y, psi)
+            if (src.kind != MHC_VEHICLE) return fail(MHC_E_INVALID, std::string(where) + "pedestrians take no paths");
+            if (L.paths.size() / 9 + (size_t)src.n_b > (size_t)0x7fffffff)
+                return fail(MHC_E_INVALID, std::string(where) + "too many paths in the batch");
+            d.path_off = (int)(L.paths.size() / 9);
+            for (long long q = 0; q < 9LL * src.n_b; ++q) {
+                if (!finite(src.paths[q])) return fail(MHC_E_INVALID, std::string(where) + "path sections must be finite");
+                L.paths.push_back(src.paths[q]);
+            }
+            // the sections switch at t = n tau_i >= 1.0 s and >= 1.5 s, decided in FP64
+            auto first_at = [&](double t) {
+                long long n = (long long)std::ceil(t / d.tau_i_d);
+                while (n > 0 && (double)(n - 1) * d.tau_i_d >= t) --n;
+                while ((double)n * d.tau_i_d < t) ++n;
+                return (int)std::min<long long>(n, 0x7fffffffLL);
+            };
+            d.path_n1 = first_at(1.0);
+            d.path_n2 = first_at(1.5);
+        }
         for (int q = 0; q < d.n_tiles32; ++q) { L.warp_obj.push_back(L.n_obj); L.warp_first.push_back(q * kBoundTile); }
         L.objs.push_back(d);
         ++L.n_obj;
@@ -306,7 +326,8 @@ void plan_generation(Layout &L, int n_sm, int mode) {
         long long traj = 0;
         for (int o = S.obj0; o < S.obj0 + S.n_obj; ++o) traj += L.objs[o].h;
         const bool sc = mode == 1 || (mode == 2 && traj <= kGenScanMaxTraj);
-        for (int o = S.obj0; o < S.obj0 + S.n_obj; ++o) scan[o] = sc;
+        for (int o = S.obj0; o < S.obj0 + S.n_obj; ++o) scan[o] = sc && L.objs[o].path_off < 0;   // controller
+                                                                     // feedback: a path hypothesis runs in order
     }
     long long seq_traj = 0;
     for (int o = 0; o < L.n_obj; ++o) {
@@ -315,7 +336,8 @@ void plan_generation(Layout &L, int n_sm, int mode) {
     }
     L.n_gen_scan = (int)L.gen_obj.size();
     // the others: one thread per hypothesis, `lanes` per warp; with fewer hypotheses than warp schedulers
-    // (4 per SM) each warp takes fewer of them (down to 4) to occupy every scheduler
+    // (4 per SM) each warp takes fewer of them (down to 4) to occupy every scheduler (more, smaller warps
+    // measured slower on large scenes, where the sub-steps' instructions fill the issue slots)
     const long long schedulers = 4LL * (n_sm > 0 ? n_sm : 152);
     int lanes = 32;
     while (lanes > 4 && (seq_traj + lanes - 1) / lanes < schedulers) lanes >>= 1;
@@ -346,7 +368,8 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
     s.desc = align_up(sizeof(ObjDesc) * L.objs.size()) + 2 * align_up(sizeof(PairDesc) * (L.pairs.size() + 1)) +
              align_up(sizeof(ScenDesc) * L.scens.size()) + align_up(sizeof(float) * L.grids.size()) +
              2 * align_up(sizeof(int) * L.warp_obj.size()) + 2 * align_up(sizeof(int) * gen_tasks) +
-             align_up(sizeof(Regime) * L.regimes.size()) + align_up(sizeof(PolyVertex) * L.polys.size());
+             align_up(sizeof(Regime) * L.regimes.size()) + align_up(sizeof(PolyVertex) * L.polys.size()) +
+             align_up(sizeof(float) * L.paths.size());
     s.bounds = align_up(sizeof(float4) * (size_t)L.n_bounds);
     s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj);
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
@@ -386,7 +409,7 @@ int end_call(mhc_ctx *ctx, cudaStream_t st) {
 }
 
 size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char *host, char *dev, DevDesc &out) {
-    constexpr int kParts = 11;
+    constexpr int kParts = 12;
     const std::pair<const void *, size_t> parts[kParts] = {
         {L.objs.data(), sizeof(ObjDesc) * L.objs.size()},
         {L.pairs.data(), sizeof(PairDesc) * L.pairs.size()},
@@ -399,6 +422,7 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
         {L.gen_first.data(), sizeof(int) * L.gen_first.size()},
         {L.regimes.data(), sizeof(Regime) * L.regimes.size()},
         {L.polys.data(), sizeof(PolyVertex) * L.polys.size()},
+        {L.paths.data(), sizeof(float) * L.paths.size()},
     };
     size_t caps[kParts];
     for (int q = 0; q < kParts; ++q) caps[q] = align_up(parts[q].second);
@@ -427,6 +451,7 @@ size_t pack_descriptors(const Layout &L, const std::vector<float> *weights, char
     out.gen_first = reinterpret_cast<int *>(ptrs[8]);
     out.regimes = reinterpret_cast<Regime *>(ptrs[9]);
     out.polys = L.polys.empty() ? nullptr : reinterpret_cast<PolyVertex *>(ptrs[10]);
+    out.paths = L.paths.empty() ? nullptr : reinterpret_cast<float *>(ptrs[11]);
     out.weights = weights ? reinterpret_cast<float *>(ptrs[kParts]) : nullptr;
     return off;
 }
@@ -616,6 +641,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
             if (nb < L.n_obj) nb = L.n_obj;
             g.prep_blocks = (int)nb;
         }
+        g.paths = D.paths;
         g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
         cudaError_t e = launch_generate(g, st);

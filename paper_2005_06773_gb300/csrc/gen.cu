@@ -136,6 +136,120 @@ __device__ void vehicle(const ObjDesc &o, float acc, float delta, const Regime &
     }
 }
 
+// Path hypotheses (Section IV-B.2b): before every sub-step the lateral controller of Eq. (controller) sets
+// the front steering angle, in degrees, from the speed, the signed distance d_path from the centre of
+// gravity predicted kCtrlTp ahead along the course to the active section's line (positive when the line
+// lies to the left) and the yaw error e_psi = psi_section - psi; the angle is held within kDeltaMax and
+// within kDeltaRate x tau_i of the previous sub-step's (0 before the first).  The one-track step is then
+// the constant-steering one of `vehicle` with that angle.
+constexpr float kCtrlTp = 0.5f;       // s: prediction time of the centre of gravity
+constexpr float kDeltaMax = 0.5f;     // rad
+constexpr float kDeltaRate = 0.5f;    // rad/s
+constexpr float kPi = 3.14159265358979f;
+
+__device__ void vehicle_path(const ObjDesc &o, float acc, const float *path, const Regime &g, int N, int K,
+                             double tau_i_d, long long base, int h, int i, float *X, float *Y, float *C, float *S) {
+    const float dv = (float)__dmul_rn((double)acc, tau_i_d);
+    const int low_lo = g.low_lo, low_hi = g.low_hi, n_stop = g.n_stop;
+    const float ti = (float)tau_i_d;
+    const float hti2 = 0.5f * ti * ti;
+    const float L = o.lf + o.lr;
+    const float inv_m = 1.0f / o.m, inv_iz = 1.0f / o.Iz;
+    const float k11 = -(o.caf + o.car) * inv_m;
+    const float k12 = (o.car * o.lr - o.caf * o.lf) * inv_m;
+    const float k21 = (o.car * o.lr - o.caf * o.lf) * inv_iz;
+    const float k22 = -(o.caf * o.lf * o.lf + o.car * o.lr * o.lr) * inv_iz;
+    const float kb1u = o.caf * inv_m;                           // b1 * v per rad of steering
+    const float kb2u = o.caf * o.lf * inv_iz;                   // b2 per rad of steering
+    const float stop_den = 0.5f / fabsf(acc == 0.0f ? 1.0f : acc);
+    const float step_max = kDeltaRate * ti;
+    float sec_x[3], sec_y[3], sec_psi[3], sec_nx[3], sec_ny[3];  // sections: point, direction, left normal
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        sec_x[q] = path[3 * q];
+        sec_y[q] = path[3 * q + 1];
+        sec_psi[q] = path[3 * q + 2];
+        float sn, cs;
+        sincosf(sec_psi[q], &sn, &cs);
+        sec_nx[q] = -sn;
+        sec_ny[q] = cs;
+    }
+
+    float xh = o.x0, xc = 0.0f, yh = o.y0, yc = 0.0f, ph = o.psi0, pc = 0.0f;   // Kahan sums
+    float cps, sps;
+    sincos2(ph, -pc, sps, cps);
+    float beta = 0.0f, r = 0.0f, ax = acc, ay = 0.0f, delta = 0.0f;
+    bool stopped = false;
+    int n = 0;
+    for (int k = 0; k < N; ++k) {
+        for (int q = 0; q < K; ++q, ++n) {
+            const bool low = n >= low_lo && n < low_hi;
+            const bool stop_now = n == n_stop;
+            const float v = fmaf((float)n, dv, o.v0);
+            float sb0, cb0;                                      // the course of the state before the step
+            sincos_half(beta, sb0, cb0);
+            if (!stopped) {   // the controller, on the state before this sub-step
+                const int sec = n < o.path_n1 ? 0 : (n < o.path_n2 ? 1 : 2);
+                const float px = (xh - xc) + kCtrlTp * v * fmaf(cps, cb0, -sps * sb0);
+                const float py = (yh - yc) + kCtrlTp * v * fmaf(sps, cb0, cps * sb0);
+                const float d_path = fmaf(sec_x[sec] - px, sec_nx[sec], (sec_y[sec] - py) * sec_ny[sec]);
+                float e_psi = sec_psi[sec] - (ph - pc);
+                e_psi -= 2.0f * kPi * floorf((e_psi + kPi) * (0.5f / kPi));
+                const float gd = fabsf(fmaf(-0.018f, v, 1.5f) * d_path);
+                const float cmd = ((gd + 0.5f) * d_path + (9.5f - gd) * (3.8197f * e_psi)) * (kPi / 180.0f);
+                delta = fminf(fmaxf(delta + fminf(fmaxf(cmd - delta, -step_max), step_max), -kDeltaMax), kDeltaMax);
+            }
+            const float kb1 = kb1u * delta, kb2 = kb2u * delta;
+            float beta_kin = 0.0f, kappa = 0.0f;
+            float sb = sb0, cb = cb0;                            // the one-track step keeps the course
+            if (low) {                                           // the kinematic limit at the new angle
+                const float tdel = tanf(delta);
+                beta_kin = atanf(o.lr * tdel / L);
+                kappa = cosf(beta_kin) * tdel / L;
+                sincos_half(beta_kin, sb, cb);
+            }
+            const float iv = __fdividef(1.0f, fmaxf(v, 1e-3f));
+            const float bd_ot = fmaf(k11 * iv, beta, fmaf(fmaf(k12 * iv, iv, -1.0f), r, kb1 * iv));
+            const float rd_ot = fmaf(k21, beta, fmaf(k22 * iv, r, kb2));
+            const float b_use = low ? beta_kin : beta;
+            const float r_use = low ? v * kappa : r;
+            const float bd = low ? 0.0f : bd_ot;
+            const float rd = low ? 0.0f : rd_ot;
+            const float cpb = fmaf(cps, cb, -sps * sb);
+            const float spb = fmaf(sps, cb, cps * sb);
+            const float d_stop = v * v * stop_den;
+            const float dx = stop_now ? cpb * d_stop : fmaf(cpb * v, ti, fmaf(cps, ax, -sps * ay) * hti2);
+            const float dy = stop_now ? spb * d_stop : fmaf(spb * v, ti, fmaf(sps, ax, cps * ay) * hti2);
+            const float w = v * (bd + r_use);
+            const float ax_n = fmaf(cb, acc, -sb * w);
+            const float ay_n = fmaf(sb, acc, cb * w);
+            const float dpsi = fmaf(r_use, ti, rd * hti2);
+            const bool move = !stopped && !stop_now;
+            kahan_add(xh, xc, stopped ? 0.0f : dx);
+            kahan_add(yh, yc, stopped ? 0.0f : dy);
+            kahan_add(ph, pc, move ? dpsi : 0.0f);
+            if (move) {
+                beta = fmaf(bd, ti, b_use);
+                r = fmaf(rd, ti, r_use);
+                ax = ax_n;
+                ay = ay_n;
+                float sd, cd;
+                sincos_tenth(dpsi, sd, cd);
+                const float c2 = fmaf(cps, cd, -sps * sd);
+                sps = fmaf(sps, cd, cps * sd);
+                cps = c2;
+            }
+            stopped = stopped || stop_now;
+        }
+        sincos2(ph, -pc, sps, cps);
+        const long long idx = base + (long long)k * h + i;
+        X[idx] = xh - xc;
+        Y[idx] = yh - yc;
+        C[idx] = cps;
+        S[idx] = sps;
+    }
+}
+
 // output steps k0, k0 + dk, ... of one pedestrian hypothesis (closed form)
 __device__ void pedestrian(const ObjDesc &o, float ga, float gb, int N, float tau, long long base, int h, int i,
                            float *X, float *Y, float *C, float *S, int k0 = 0, int dk = 1) {
@@ -449,7 +563,10 @@ __global__ void __launch_bounds__(128, 8) gen_kernel(const GenArgs a) {
     const int ia = i / o.n_b, ib = i - ia * o.n_b;
     const float ga = a.grids[o.grid_off + ia];
     const float gb = a.grids[o.grid_off + o.n_a + ib];
-    if (o.kind == kVehicle)
+    if (o.kind == kVehicle && o.path_off >= 0)
+        vehicle_path(o, ga, a.paths + 9LL * (o.path_off + ib), a.regimes[o.regime_off + ia], o.n_steps, o.substeps,
+                     o.tau_i_d, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
+    else if (o.kind == kVehicle)
         vehicle(o, ga, gb, a.regimes[o.regime_off + ia], o.n_steps, o.substeps, o.tau_i_d, o.pose_base, o.h, i,
                 a.x, a.y, a.c, a.s);
     else

@@ -47,6 +47,9 @@ struct ObjDesc {
     double tau_i_d;     // (double)tau / substeps, the sub-step of the speed recurrence
     int poly_off;       // vehicles of scenarios with convex outlines: the outline's vertices at
     int n_poly;         // polys[poly_off .. + n_poly) (a rectangle as its 4 corners); n_poly = 0 otherwise
+    int path_off;       // vehicles with paths: path i_b's three sections (x, y, psi) at paths[9 (path_off +
+                        // i_b) ..]; -1 for constant steering angles
+    int path_n1, path_n2;   // the first sub-steps of the second and third sections (t >= 1.0 s, t >= 1.5 s)
 };
 
 // One vertex of a convex outline in the body frame with the outward unit normal of the edge to the next
@@ -124,6 +127,7 @@ struct GenArgs {
     PrepArgs prep;
     int n_scan;               // warp tasks [0, n_scan): one hypothesis each, parallel in time (warp_first =
                               // the hypothesis); the rest: `lanes` hypotheses each, one thread per hypothesis
+    const float *paths;       // path sections of the vehicles that follow paths (ObjDesc::path_off)
     float *x, *y, *c, *s;
 };
 

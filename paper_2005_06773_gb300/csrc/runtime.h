@@ -43,6 +43,7 @@ struct Layout {
     std::vector<float> grids;
     std::vector<Regime> regimes;                     // per vehicle and acceleration value
     std::vector<PolyVertex> polys;                   // vehicles' outlines in scenarios that have convex outlines
+    std::vector<float> paths;                        // path sections of the vehicles that follow paths
     std::vector<int> warp_obj, warp_first;          // 32-hypothesis bound tiles
     std::vector<int> gen_obj, gen_first;            // generation warp tasks of gen_lanes hypotheses
     std::vector<int> pair0;                         // first pair of each scenario (n_scen + 1 entries)
@@ -92,6 +93,7 @@ struct DevDesc {
     int *gen_obj, *gen_first;
     Regime *regimes;
     PolyVertex *polys;       // null when the batch has no outlines
+    float *paths;            // null when no vehicle follows paths
     float *weights;
 };
 

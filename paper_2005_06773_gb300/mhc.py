@@ -39,7 +39,7 @@ class MhcObject(ctypes.Structure):
                 ("radius", c_float), ("x0", c_float), ("y0", c_float), ("psi0", c_float), ("v0", c_float),
                 ("v_max", c_float), ("n_a", c_int32), ("n_b", c_int32), ("grid_a", POINTER(c_float)),
                 ("grid_b", POINTER(c_float)), ("veh_params", POINTER(c_float)), ("n_vertices", c_int32),
-                ("vertices", POINTER(c_float))]
+                ("vertices", POINTER(c_float)), ("paths", POINTER(c_float))]
 
 
 class MhcScenario(ctypes.Structure):
@@ -193,6 +193,13 @@ class CScenario:
                 self._keep.append(vv)
                 d.n_vertices = vv.size // 2
                 d.vertices = vv.ctypes.data_as(POINTER(c_float))
+            paths = getattr(o, "paths", None)
+            if paths is not None:
+                pp = np.ascontiguousarray(np.asarray(paths, np.float32).reshape(-1))
+                if pp.size != 9 * gb.size:
+                    raise ValueError("paths must hold n_b x 3 sections x (x, y, psi)")
+                self._keep.append(pp)
+                d.paths = pp.ctypes.data_as(POINTER(c_float))
         self._objs = objs
         self.c = MhcScenario(len(sc.objects), objs, sc.tau, int(sc.n_steps), int(sc.substeps), int(sc.pair_mode),
                              int(sc.ego), int(sc.model))

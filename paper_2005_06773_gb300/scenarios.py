@@ -346,6 +346,35 @@ def with_outlines(sc: Scenario, cut: float = 0.35, every: int = 1) -> Scenario:
     return dataclasses.replace(sc, objects=objs, name=f"{sc.name}_outline{cut:g}")
 
 
+LANE_W = 3.5
+PATH_OFFSETS = (-0.875, 0.0, 0.875, LANE_W - 0.6, LANE_W + 0.6, -LANE_W - 0.6, -LANE_W + 0.6)
+
+
+def lane_paths(o: "Obj", offsets=PATH_OFFSETS, times=(1.0, 1.5, 2.0)) -> np.ndarray:
+    """Paths of Section IV-B.2b for a car driving along its current lane: per lateral offset (three samples
+    in the own lane, two in each neighbouring lane, relative to the car's current line), three sections
+    parallel to the lane through the points the car would reach at the sampling instants at its current
+    speed.  [len(offsets), 3, 3] of (x, y, psi)."""
+    c, s_ = math.cos(o.psi0), math.sin(o.psi0)
+    out = np.zeros((len(offsets), 3, 3), dtype=np.float64)
+    for q, off in enumerate(offsets):
+        for k, t in enumerate(times):
+            along = o.v0 * t
+            out[q, k] = (o.x0 + along * c - off * s_, o.y0 + along * s_ + off * c, o.psi0)
+    return out.astype(F32)
+
+
+def with_lane_paths(sc: Scenario, offsets=PATH_OFFSETS, every: int = 1) -> Scenario:
+    """The scenario with every `every`-th car following lane paths (hypotheses = accelerations x paths)
+    instead of constant steering angles."""
+    objs = []
+    for i, o in enumerate(sc.objects):
+        if o.kind == VEHICLE and i % every == 0:
+            o = dataclasses.replace(o, grid_b=np.zeros(len(offsets), dtype=F32), paths=lane_paths(o, offsets))
+        objs.append(o)
+    return dataclasses.replace(sc, objects=objs, name=f"{sc.name}_paths")
+
+
 def paper_pedestrians(sc: Scenario, n_acc: int = 9, n_head: int = 12, seed: int = 15) -> Scenario:
     """The scenario with its pedestrians sampled as in Section IV-B.3: accelerations evenly over
     [-12, 12] m/s^2 from an initial walking speed U[0.5, 1.5] m/s, the speed held within [0, 2.7] m/s, and

@@ -151,3 +151,20 @@ def test_outlines_accepted_in_either_orientation(mhc):
                 outline=np.array([[1, 0], [0, 1], [-1, 0]], np.float32))
     with pytest.raises(mhc.MhcError):
         mhc.layout(S.Scenario([S.tiny_crossing(1).objects[0], ped]))
+
+
+def test_invalid_paths_rejected(mhc):
+    sc = S.with_lane_paths(S.tiny_crossing(1))
+    sc.objects[0].paths[2, 1, 0] = np.nan
+    with pytest.raises(mhc.MhcError):
+        mhc.layout(sc)
+    car = S.tiny_crossing(1).objects[0]
+    ped = S.Obj(S.PEDESTRIAN, 0, 0, 0.4, 0, 0, 0, 0, np.array([1.0]), np.zeros(2),
+                paths=np.zeros((2, 3, 3), np.float32))
+    with pytest.raises(mhc.MhcError):
+        mhc.layout(S.Scenario([car, ped]))
+    bad = S.with_lane_paths(S.tiny_crossing(1))
+    bad.objects[1].paths = bad.objects[1].paths[:3]                 # fewer paths than n_b
+    with pytest.raises(ValueError):
+        mhc.layout(bad)
+    assert mhc.layout(S.with_lane_paths(S.tiny_crossing(1)))["n_traj"] == 2 * 4 * 7

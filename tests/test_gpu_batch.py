@@ -126,6 +126,25 @@ def test_batch_with_outlines(mhc, ctx, orc):
         check_table(orc, sc, t_g, tab_o, ref, pairs, poff)
 
 
+def test_batch_with_lane_paths(mhc, ctx, orc):
+    """Path hypotheses (the controller in the generation loop) batched with constant-steering scenarios
+    small enough for the warp-per-hypothesis layout: each scenario gets exactly what it gets alone, and
+    the path scenario's poses match the oracle."""
+    from test_gpu_parity import scene
+    batch = [S.tiny_crossing(1), copy.deepcopy(scene("lane_paths")), copy.deepcopy(scene("ragged"))]
+    w = _weights(batch, 70)
+    info, sls = mhc.batch_slices(batch)
+    poses, table, out = mhc.evaluate_batch(ctx, batch, weights=w)
+    torch.cuda.synchronize()
+    _compare_single(mhc, ctx, batch, poses, table, out, sls, weights=w)
+    sc, sl = batch[1], sls[1]
+    ref = orc.generate(sc)
+    n_pose = int(sum(o.n_hyp for o in sc.objects)) * sc.n_steps
+    g = {k: mhc.poses_by_trajectory(sc, poses[k][sl["pose0"]: sl["pose0"] + n_pose]).astype(np.float64)
+         for k in ("x", "y", "c", "s")}
+    assert corner_error(sc, ref, g["x"], g["y"], g["c"], g["s"]) < POSE_TOL
+
+
 def test_batch_pair_table_is_the_concatenation(mhc):
     batch = mixed_batch()
     pa, pb, poff = mhc.batch_pair_table(batch)

@@ -87,6 +87,9 @@ def _scenes():
         "outline_ragged": S.with_outlines(_ragged(), cut=0.4),
         "outline_half": S.with_outlines(S.intersection11(5, n_steps=40, n_acc=9, n_str=7, n_ped_v=5, n_ped_h=9),
                                         cut=0.35, every=2),
+        "lane_paths": S.with_lane_paths(S.intersection11(17, n_steps=30, n_acc=5, n_str=7, n_ped_v=3, n_ped_h=3)),
+        "lane_paths_long": S.with_lane_paths(S.intersection11(18, n_steps=60, n_acc=4, n_str=3, n_ped_v=2, n_ped_h=3),
+                                             every=2),
         "outline_paper_peds": S.paper_pedestrians(
             S.with_outlines(S.intersection11(16, n_steps=50, n_acc=7, n_str=7), cut=0.3), n_acc=9, n_head=12),
         "tiny": S.tiny_crossing(1),
@@ -119,7 +122,7 @@ def _scenes():
 _CACHE = {}
 SCENE_NAMES = ["tiny", "tiny_near", "mixed_small", "ragged", "ped_accel", "paper_s1", "ego_only_ego2_n70",
                "kinematic", "one_step", "long_n1200", "ego_only_n300", "outline_shapes", "outline_ragged",
-               "outline_half", "outline_paper_peds"]
+               "outline_half", "outline_paper_peds", "lane_paths", "lane_paths_long"]
 
 
 def scene(name):
