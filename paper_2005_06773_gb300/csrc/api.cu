@@ -31,31 +31,31 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // Speed regimes of a vehicle hypothesis with acceleration acc (Eq. EulerVelocity, readings of the low-speed
 // limit and the stop rule): the first sub-steps at which the FP64 speed v_0 + n vdot tau_i reaches or leaves
-// 2 m/s and at which the next speed turns negative, by binary search on these monotone predicates.
+// 2 m/s and at which the next speed turns negative.  Each predicate is monotone in n; the search starts at
+// the real-valued crossing and steps to the exact first sub-step, evaluating the predicate itself, so the
+// decision is the FP64 one a full search would take.
 Regime speed_regime(float v0f, float acc, int model, int NK, double tau_i_d) {
     const double dv = (double)acc * tau_i_d;
     const double v0 = (double)v0f;
     auto speed = [&](int n) { return v0 + (double)n * dv; };
-    auto first = [&](auto pred) {   // smallest n in [0, NK) with pred(n), NK if none
-        int lo = 0, hi = NK;
-        while (lo < hi) {
-            const int mid = lo + (hi - lo) / 2;
-            if (pred(mid)) hi = mid; else lo = mid + 1;
-        }
-        return lo;
+    auto first = [&](auto pred, double guess) {   // smallest n in [0, NK) with pred(n), NK if none
+        int n = !(guess > 0.0) ? 0 : (guess >= (double)NK ? NK : (int)std::ceil(guess));
+        while (n > 0 && pred(n - 1)) --n;
+        while (n < NK && !pred(n)) ++n;
+        return n;
     };
     Regime g{0, 0, NK, 0};
     if (model == MHC_MODEL_KIN) {
         g.low_hi = NK;
     } else if (acc > 0.0f) {
-        g.low_hi = first([&](int n) { return speed(n) >= kVMinD; });
+        g.low_hi = first([&](int n) { return speed(n) >= kVMinD; }, (kVMinD - v0) / dv);
     } else if (acc < 0.0f) {
-        g.low_lo = first([&](int n) { return speed(n) < kVMinD; });
+        g.low_lo = first([&](int n) { return speed(n) < kVMinD; }, (kVMinD - v0) / dv);
         g.low_hi = NK;
     } else if (v0 < kVMinD) {
         g.low_hi = NK;
     }
-    if (acc < 0.0f) g.n_stop = first([&](int n) { return speed(n + 1) < 0.0; });
+    if (acc < 0.0f) g.n_stop = first([&](int n) { return speed(n + 1) < 0.0; }, -v0 / dv - 1.0);
     return g;
 }
 
@@ -288,6 +288,31 @@ int build_layout(const mhc_scenario *sc, int n_scen, Layout &L) {
     if (!sc) return fail(MHC_E_INVALID, "scenario is NULL");
     if (n_scen < 1 || n_scen > MHC_MAX_SCENARIOS) return fail(MHC_E_INVALID, "n_scenarios must be in [1, 65536]");
     L = Layout();
+    {   // capacities from a first look at the inputs (no reallocation while appending)
+        size_t objs = 0, pairs = 0, grids = 0, accs = 0, tiles = 0;
+        for (int s = 0; s < n_scen; ++s) {
+            const int n = sc[s].n_objects;
+            if (n < 1 || n > MHC_MAX_OBJECTS || !sc[s].objects) break;      // reported by the validation
+            objs += n;
+            pairs += sc[s].pair_mode == MHC_EGO_ONLY ? (size_t)(n - 1) : (size_t)n * (n - 1) / 2;
+            for (int o = 0; o < n; ++o) {
+                const mhc_object &src = sc[s].objects[o];
+                if (src.n_a < 1 || src.n_b < 1 || (long long)src.n_a * src.n_b > (1LL << 30)) continue;
+                grids += (size_t)src.n_a + src.n_b;
+                accs += (size_t)src.n_a;
+                tiles += ((size_t)src.n_a * src.n_b + kBoundTile - 1) / kBoundTile;
+            }
+        }
+        L.objs.reserve(objs);
+        L.pairs.reserve(pairs);
+        L.grids.reserve(grids);
+        L.regimes.reserve(accs);
+        L.warp_obj.reserve(tiles);
+        L.warp_first.reserve(tiles);
+        L.scens.reserve(n_scen);
+        L.pair0.reserve(n_scen + 1);
+        L.entry0.reserve(n_scen + 1);
+    }
     L.pair0.push_back(0);
     for (int s = 0; s < n_scen; ++s)
         if (int r = append_scenario(sc + s, s, n_scen > 1, L)) return r;
@@ -319,6 +344,8 @@ int build_layout(const mhc_scenario *sc, Layout &L) { return build_layout(sc, 1,
 void plan_generation(Layout &L, int n_sm, int mode) {
     L.gen_obj.clear();
     L.gen_first.clear();
+    L.gen_obj.reserve((size_t)L.n_traj + L.n_obj);
+    L.gen_first.reserve((size_t)L.n_traj + L.n_obj);
     // one warp per hypothesis (parallel in time) for the objects of scenarios with few hypotheses, so that
     // a scenario gets the same poses alone and in any batch
     std::vector<char> scan(L.n_obj, 0);
