@@ -38,6 +38,16 @@
  *       psi wrapped to [-pi, pi]; no dynamic weighting (not specified).
  *  R-u  steering limits: |delta_f| <= 0.5 rad and |delta_n - delta_{n-1}| <= 0.5 rad/s x tau_i, with
  *       delta_{-1} = 0 (the current steering angle is not an input).
+ *  R-v  lane dividers (Section IV-A) are given in the vehicle's frame at t = 0 (x ahead, y to the left) as
+ *       three points each, ordered from right to left; divider j is y = a x^2 + b x + c through its
+ *       points (Gauss-Jordan with partial pivoting).  The vehicle's lane is the pair of adjacent dividers
+ *       that encloses its position; the lanes beside it (if their dividers are given) are its neighbours.
+ *  R-w  path sampling (Section IV-B.2b): at the instants 1.0 / 1.5 / 2.0 s the reference position is
+ *       x_t = v0 t ahead; the own lane is sampled at 1/4, 1/2 and 3/4 of its width at x_t, each
+ *       neighbouring lane at 1/3 and 2/3 (right to left); a section passes through a sample point with the
+ *       direction of the lane's centre line there (atan of its slope).  A CO gets one path per sample
+ *       index (the same index at every instant, m paths); the EGO every combination (m^3 paths, index of
+ *       the first instant slowest).  Sections are returned in the scenario frame.
  */
 #include <math.h>
 #include <stdint.h>
@@ -86,6 +96,81 @@ static double path_steering(const double *path, long n, double tau_i, double x, 
     double step = ORC_DELTA_RATE * tau_i;
     double delta = delta_prev + fmin(fmax(cmd - delta_prev, -step), step);
     return fmin(fmax(delta, -ORC_DELTA_MAX), ORC_DELTA_MAX);
+}
+
+/* Section IV-A: divider y = a x^2 + b x + c through three points (x_i, y_i), by Gauss-Jordan elimination
+   of [x_i^2, x_i, 1 | y_i] with partial pivoting.  Returns 0, or -1 if the points fix no such curve. */
+int orc_divider_fit(const double *pts, double *coef) {
+    double m[3][4];
+    for (int r = 0; r < 3; ++r) {
+        double x = pts[2 * r], y = pts[2 * r + 1];
+        m[r][0] = x * x; m[r][1] = x; m[r][2] = 1.0; m[r][3] = y;
+    }
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 3; ++r) if (fabs(m[r][col]) > fabs(m[piv][col])) piv = r;
+        if (!(fabs(m[piv][col]) > 1e-12)) return -1;
+        for (int q = 0; q < 4; ++q) { double t = m[col][q]; m[col][q] = m[piv][q]; m[piv][q] = t; }
+        double d = m[col][col];
+        for (int q = 0; q < 4; ++q) m[col][q] /= d;
+        for (int r = 0; r < 3; ++r) {
+            if (r == col) continue;
+            double f = m[r][col];
+            for (int q = 0; q < 4; ++q) m[r][q] -= f * m[col][q];
+        }
+    }
+    coef[0] = m[0][3]; coef[1] = m[1][3]; coef[2] = m[2][3];
+    return 0;
+}
+
+/* Paths of one vehicle from its lane dividers (readings R-v, R-w).  div: n_div (2..4) dividers x 3 points
+   (x, y) in the vehicle frame, right to left.  Writes up to 343 paths x 3 sections x (x, y, psi) to out and
+   returns their number, or -1 if a divider has no fit or no lane encloses the vehicle. */
+int orc_lane_paths(const double *div, int n_div, double x0, double y0, double psi0, double v0, int ego,
+                   double *out) {
+    double cf[4][3];
+    if (n_div < 2 || n_div > 4) return -1;
+    for (int j = 0; j < n_div; ++j) if (orc_divider_fit(div + 6 * j, cf[j])) return -1;
+    int own = -1;                                   /* lane between dividers own and own + 1 */
+    for (int j = 0; j + 1 < n_div; ++j)
+        if (cf[j][2] <= 0.0 && 0.0 <= cf[j + 1][2]) { own = j; break; }
+    if (own < 0) return -1;
+    const double times[3] = {1.0, 1.5, 2.0};
+    double sy[3][7], spsi[3][7];                    /* per instant: lateral position and direction */
+    int m = 0;
+    for (int k = 0; k < 3; ++k) {
+        double x = v0 * times[k];
+        int q = 0;
+        for (int lane = own - 1; lane <= own + 1; ++lane) {   /* right neighbour, own, left neighbour */
+            if (lane < 0 || lane + 1 >= n_div) continue;
+            const double *r = cf[lane], *l = cf[lane + 1];
+            double yr = (r[0] * x + r[1]) * x + r[2], yl = (l[0] * x + l[1]) * x + l[2];
+            double slope = ((2.0 * r[0] * x + r[1]) + (2.0 * l[0] * x + l[1])) / 2.0;
+            int n = lane == own ? 3 : 2;
+            for (int u = 1; u <= n; ++u) {
+                sy[k][q] = yr + (yl - yr) * u / (n + 1);
+                spsi[k][q] = atan(slope);
+                ++q;
+            }
+        }
+        m = q;
+    }
+    const double c = cos(psi0), s = sin(psi0);
+    int n_paths = 0;
+    for (int i0 = 0; i0 < m; ++i0)
+        for (int i1 = 0; i1 < (ego ? m : 1); ++i1)
+            for (int i2 = 0; i2 < (ego ? m : 1); ++i2) {
+                int idx[3] = {i0, ego ? i1 : i0, ego ? i2 : i0};
+                for (int k = 0; k < 3; ++k) {
+                    double bx = v0 * times[k], by = sy[k][idx[k]];
+                    double *o = out + 9 * n_paths + 3 * k;
+                    o[0] = x0 + c * bx - s * by;
+                    o[1] = y0 + s * bx + c * by;
+                    o[2] = psi0 + spsi[k][idx[k]];
+                }
+                ++n_paths;
+            }
+    return n_paths;
 }
 
 /* Speed at sub-step n (reading R-d). */

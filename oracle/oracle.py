@@ -167,6 +167,24 @@ def path_steering(x0, y0, psi0, v0, vdot, path, params=None, model=0, tau=0.1, n
     return dict(x=x, y=y, psi=psi, delta=dl)
 
 
+def divider_fit(points):
+    """y = a x^2 + b x + c through three (x, y) points (Section IV-A, Gauss-Jordan); None if undetermined."""
+    pts = _f64(np.asarray(points, D).reshape(-1))
+    cf = np.zeros(3, D)
+    rc = lib().orc_divider_fit(_p(pts, _dp), _p(cf, _dp))
+    return None if rc else cf
+
+
+def lane_paths(dividers, x0, y0, psi0, v0, ego=False):
+    """Paths of one vehicle from its lane dividers (readings R-v, R-w): dividers [n_div, 3, 2] in the
+    vehicle frame, right to left.  Returns [n_paths, 3, 3] (x, y, psi) in the scenario frame, or None."""
+    dv = _f64(np.asarray(dividers, D).reshape(-1))
+    out = np.zeros((343, 3, 3), D)
+    n = lib().orc_lane_paths(_p(dv, _dp), ctypes.c_int(len(dv) // 6), ctypes.c_double(x0), ctypes.c_double(y0),
+                             ctypes.c_double(psi0), ctypes.c_double(v0), ctypes.c_int(int(ego)), _p(out, _dp))
+    return None if n < 0 else out[:n].copy()
+
+
 def _set_polygons(sc):
     """Registers the objects' convex outlines with the C oracle for the next call (none: cleared).
     Returns the arrays, which must stay alive during that call."""
