@@ -464,6 +464,23 @@ void mhc_pool_destroy(mhc_pool *pool);
  */
 int mhc_detect_collisions_static(const mhc_scenario *scen, const mhc_poses *poses, int16_t *table, void *stream);
 
+/*
+ * Street data processing (Section IV-A) and the controller's paths (Section IV-B.2b), on the calling host
+ * thread (a few dividers: no device work).  dividers: host, n_dividers (2..4) lane dividers x 3 points
+ * (x, y) in the vehicle's frame at t = 0 (x ahead, y to the left), ordered from right to left; each
+ * divider is the curve y = a x^2 + b x + c through its points (Gauss-Jordan).  The vehicle's lane is the
+ * pair of adjacent dividers enclosing its position (the origin).  At 1.0, 1.5 and 2.0 s the reference
+ * position is x = v0 t; the own lane is sampled at 1/4, 1/2 and 3/4 of its width there and each
+ * neighbouring lane present at 1/3 and 2/3, right to left (m = 3, 5 or 7 samples per instant); a section
+ * passes through a sample along the lane's centre-line direction.  ego = 0: m paths (sample q at every
+ * instant); ego != 0: m^3 paths, path (q0 m + q1) m + q2 taking sample q_k at instant k.  paths: host,
+ * n_paths x 3 sections x (x, y, psi) in the scenario frame (the vehicle at x0, y0 heading psi0), ready
+ * for mhc_object.paths; NULL returns the count only (*n_paths).  MHC_E_INVALID: non-finite input,
+ * v0 < 0, repeated abscissae in a divider, or no lane enclosing the vehicle.
+ */
+int mhc_lane_paths(const float *dividers, int32_t n_dividers, float x0, float y0, float psi0, float v0,
+                   int32_t ego, float *paths, int32_t *n_paths);
+
 #ifdef __cplusplus
 }
 #endif

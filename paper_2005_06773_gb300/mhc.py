@@ -210,6 +210,20 @@ def as_c(sc) -> CScenario:
     return sc if isinstance(sc, CScenario) else CScenario(sc)
 
 
+def lane_paths(dividers, x0: float, y0: float, psi0: float, v0: float, ego: bool = False) -> np.ndarray:
+    """Paths of one vehicle from its lane dividers (mhc_lane_paths): dividers [n_div, 3, 2] in the
+    vehicle frame, right to left.  Returns [n_paths, 3, 3] float32 (x, y, psi), ready for Obj.paths."""
+    dv = np.ascontiguousarray(np.asarray(dividers, np.float32).reshape(-1))
+    n = c_int32(0)
+    fp = POINTER(c_float)
+    _check(lib.mhc_lane_paths(dv.ctypes.data_as(fp), c_int32(dv.size // 6), c_float(x0), c_float(y0), c_float(psi0),
+                              c_float(v0), c_int32(int(ego)), None, ctypes.byref(n)), "mhc_lane_paths")
+    out = np.zeros((n.value, 3, 3), np.float32)
+    _check(lib.mhc_lane_paths(dv.ctypes.data_as(fp), c_int32(dv.size // 6), c_float(x0), c_float(y0), c_float(psi0),
+                              c_float(v0), c_int32(int(ego)), out.ctypes.data_as(fp), ctypes.byref(n)), "mhc_lane_paths")
+    return out
+
+
 def layout(sc) -> Dict[str, int]:
     cs = as_c(sc)
     nt, ne = c_int64(), c_int64()

@@ -168,3 +168,44 @@ def test_invalid_paths_rejected(mhc):
     with pytest.raises(ValueError):
         mhc.layout(bad)
     assert mhc.layout(S.with_lane_paths(S.tiny_crossing(1)))["n_traj"] == 2 * 4 * 7
+
+
+def _random_lanes(rng, n_div):
+    """n_div dividers, right to left, 3.5 m apart with a common curvature, around the vehicle's lane."""
+    a, b = rng.uniform(-0.004, 0.004), rng.uniform(-0.05, 0.05)
+    own = rng.randint(0, n_div - 2)                        # the vehicle sits between dividers own and own + 1
+    base = -rng.uniform(0.3, 3.2) - 3.5 * own
+    xs = [rng.uniform(-2, 2), rng.uniform(15, 25), rng.uniform(40, 60)]
+    return np.array([[[x, a * x * x + b * x + base + 3.5 * j] for x in xs] for j in range(n_div)], np.float32)
+
+
+def test_lane_paths_match_the_oracle(mhc, orc):
+    """Street data processing runs on the host inside the library (FP64, FP32 output): the same paths as
+    the oracle's FP64 restatement on the same FP32 inputs, for 2 to 4 dividers, COs and the EGO."""
+    from paper_2005_06773_gb300.scenarios import SplitMix64
+    rng = SplitMix64(77)
+    for trial in range(60):
+        n_div = 2 + trial % 3
+        div = _random_lanes(rng, n_div)
+        x0, y0, psi0, v0 = (float(np.float32(v)) for v in (rng.uniform(-50, 50), rng.uniform(-50, 50),
+                                                           rng.uniform(-3, 3), rng.uniform(0, 30)))
+        for ego in (False, True):
+            got = mhc.lane_paths(div, x0, y0, psi0, v0, ego=ego)
+            ref = orc.lane_paths(div.astype(np.float64), x0, y0, psi0, v0, ego=ego)
+            assert got.shape == ref.shape
+            np.testing.assert_allclose(got, ref, rtol=0, atol=2e-5)
+
+
+def test_lane_paths_errors(mhc):
+    flat = np.array([[[0, y], [30, y], [60, y]] for y in (-1.75, 1.75)], np.float32)
+    assert mhc.lane_paths(flat, 0, 0, 0, 10).shape == (3, 3, 3)
+    assert mhc.lane_paths(flat, 0, 0, 0, 10, ego=True).shape == (27, 3, 3)
+    for bad in (flat[:1], flat + np.array([0, 5], np.float32), np.concatenate([flat] * 3)):
+        with pytest.raises(mhc.MhcError):
+            mhc.lane_paths(bad, 0, 0, 0, 10)
+    rep = flat.copy()
+    rep[0, 1, 0] = rep[0, 0, 0]                             # repeated abscissa
+    with pytest.raises(mhc.MhcError):
+        mhc.lane_paths(rep, 0, 0, 0, 10)
+    with pytest.raises(mhc.MhcError):
+        mhc.lane_paths(flat, 0, 0, 0, -1.0)

@@ -311,6 +311,32 @@ def test_profiled_and_overlapped_launches_agree(mhc, ctx, name):
         ctx.profile(False)
 
 
+def test_paths_from_lane_dividers(mhc, ctx, orc):
+    """The street-data step feeding the controller: each car's paths from three curved lane dividers
+    (mhc_lane_paths on the host, the EGO with every combination), then generation and the whole pipeline
+    on the GPU against the oracle on the same paths."""
+    import dataclasses
+    base = S.intersection11(19, n_steps=30, n_acc=3, n_str=1, n_ped_v=3, n_ped_h=3)
+    objs = []
+    for q, o in enumerate(base.objects):
+        if o.kind == S.VEHICLE:
+            xs = np.array([0.0, 25.0, 50.0])
+            curv = 0.002 * (1 if q % 2 else -1)
+            div = np.array([[[x, curv * x * x + y] for x in xs] for y in (-5.25, -1.75, 1.75, 5.25)], np.float32)
+            paths = mhc.lane_paths(div, o.x0, o.y0, o.psi0, o.v0, ego=(q == base.ego))
+            o = dataclasses.replace(o, grid_b=np.zeros(len(paths), np.float32), paths=paths)
+        objs.append(o)
+    sc = dataclasses.replace(base, objects=objs, name="lane_dividers")
+    assert sc.objects[base.ego].n_hyp == 3 * 343
+    ref = orc.generate(sc)
+    p = mhc.generate(ctx, sc)
+    g = {k: mhc.poses_by_trajectory(sc, p[k]).astype(np.float64) for k in ("x", "y", "c", "s")}
+    assert corner_error(sc, ref, g["x"], g["y"], g["c"], g["s"]) < POSE_TOL
+    tab_o, poff, pairs = orc.table(sc, ref)
+    t = mhc.detect(ctx, sc, p).cpu().numpy()
+    check_table(orc, sc, t, tab_o, ref, pairs, poff)
+
+
 def test_deterministic_and_stream_independent(mhc, ctx):
     sc = scene("mixed_small")
     s2 = torch.cuda.Stream()
