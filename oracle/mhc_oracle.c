@@ -42,6 +42,16 @@
  *       three points each, ordered from right to left; divider j is y = a x^2 + b x + c through its
  *       points (Gauss-Jordan with partial pivoting).  The vehicle's lane is the pair of adjacent dividers
  *       that encloses its position; the lanes beside it (if their dividers are given) are its neighbours.
+ *  R-x  trajectory scores (Eq. normTraj; the paper fixes neither its weights nor its factors):
+ *       n_h = (w_acc n_acc + w_str d_str) / (c_com c_cou) with w_acc = w_str = 0.5;
+ *       vehicles: n_acc = 1 / (1 + |vdot| / 2 m/s^2) (the reference keeps its speed);
+ *         constant steering: d_str = 1 / (1 + |delta| / 0.05 rad), c_com = c_cou = 1;
+ *         paths: with o_s the lateral offset of section s's point from the vehicle's initial line
+ *         (positive to the left), d_str = 1 / (1 + max |o_s| / 1.75 m), c_com = 1 + (|o_1 - o_0| +
+ *         |o_2 - o_1|) / 3.5 m, c_cou = 2 if max o_s > 1.75 m (the lane to the left carries counter
+ *         traffic), else 1;
+ *       pedestrians: n_acc = 1 / (1 + |v - v0| / 1 m/s) for speed grids, 1 / (1 + |vdot| / 2 m/s^2) for
+ *         acceleration grids; d_str = 1 / (1 + |heading offset| / 0.5 rad); c_com = c_cou = 1.
  *  R-w  path sampling (Section IV-B.2b): at the instants 1.0 / 1.5 / 2.0 s the reference position is
  *       x_t = v0 t ahead; the own lane is sampled at 1/4, 1/2 and 3/4 of its width at x_t, each
  *       neighbouring lane at 1/3 and 2/3 (right to left); a section passes through a sample point with the
@@ -810,6 +820,48 @@ int orc_risk(int n_obj, const long *traj_off, int n_steps, int ego,
     *n_escape = ne;
     free(list);
     free(mass);
+    return 0;
+}
+
+/* Eq. (normTraj) with the factors of reading R-x: the score of every hypothesis of every object, in
+   the generation's order (hypothesis h of object o at traj index traj_off[o] + h uses grid_a[h / n_b] and
+   grid_b[h % n_b], or path h % n_b).  Inputs as orc_generate; paths as registered by orc_set_paths. */
+int orc_scores(int n_obj, const int *kind, const double *x0, const double *y0, const double *psi0,
+               const double *v0, const int *n_a, const int *n_b, const long *grid_off, const double *grids,
+               const int *flags, double *out) {
+    const double w_acc = 0.5, w_str = 0.5;
+    long t = 0;
+    for (int o = 0; o < n_obj; ++o) {
+        const double *ga = grids + grid_off[o];
+        const double *gb = ga + n_a[o];
+        for (int ia = 0; ia < n_a[o]; ++ia) {
+            for (int ib = 0; ib < n_b[o]; ++ib, ++t) {
+                double n_acc, d_str, c_com = 1.0, c_cou = 1.0;
+                if (kind[o] == ORC_VEHICLE) {
+                    n_acc = 1.0 / (1.0 + fabs(ga[ia]) / 2.0);
+                    const double *path = object_path(o, ib);
+                    if (!path) {
+                        d_str = 1.0 / (1.0 + fabs(gb[ib]) / 0.05);
+                    } else {
+                        double off[3], nx = -sin(psi0[o]), ny = cos(psi0[o]), o_abs = 0.0, o_max = -INFINITY;
+                        for (int k = 0; k < 3; ++k) {
+                            off[k] = (path[3 * k] - x0[o]) * nx + (path[3 * k + 1] - y0[o]) * ny;
+                            o_abs = fmax(o_abs, fabs(off[k]));
+                            o_max = fmax(o_max, off[k]);
+                        }
+                        d_str = 1.0 / (1.0 + o_abs / 1.75);
+                        c_com = 1.0 + (fabs(off[1] - off[0]) + fabs(off[2] - off[1])) / 3.5;
+                        c_cou = o_max > 1.75 ? 2.0 : 1.0;
+                    }
+                } else {
+                    n_acc = (flags[o] & ORC_PED_ACCEL_GRID) ? 1.0 / (1.0 + fabs(ga[ia]) / 2.0)
+                                                            : 1.0 / (1.0 + fabs(ga[ia] - v0[o]) / 1.0);
+                    d_str = 1.0 / (1.0 + fabs(gb[ib]) / 0.5);
+                }
+                out[t] = (w_acc * n_acc + w_str * d_str) / (c_com * c_cou);
+            }
+        }
+    }
     return 0;
 }
 

@@ -280,6 +280,19 @@ def overlap_pip(len_a, wid_a, xa, ya, psi_a, len_b, wid_b, xb, yb, psi_b) -> boo
                                       len_b, wid_b, xb, yb, np.cos(psi_b), np.sin(psi_b)))
 
 
+def scores(sc) -> List[np.ndarray]:
+    """Eq. (normTraj) scores n_h of every hypothesis (reading R-x), one array per object."""
+    L = lib()
+    ob = _objects(sc)
+    off = traj_offsets(sc)
+    out = np.zeros(int(off[-1]), D)
+    keep = _set_paths(sc)  # noqa: F841 (alive during the call)
+    L.orc_scores(ctypes.c_int(len(sc.objects)), _p(ob["kind"], _ip), _p(ob["x0"], _dp), _p(ob["y0"], _dp),
+                 _p(ob["psi0"], _dp), _p(ob["v0"], _dp), _p(ob["n_a"], _ip), _p(ob["n_b"], _ip),
+                 _p(ob["grid_off"], _lp), _p(ob["grids"], _dp), _p(ob["flags"], _ip), _p(out, _dp))
+    return [out[off[q]:off[q + 1]].copy() for q in range(len(sc.objects))]
+
+
 def normalise(sc, weights: Optional[Sequence[np.ndarray]] = None) -> np.ndarray:
     """Per-object L1 normalisation of trajectory weights into occurrence probabilities (Section IV-D.1).
     None means uniform weights."""
