@@ -205,6 +205,18 @@ void mhc_destroy(mhc_ctx *ctx);
  *                 scenario gets the same poses alone and in any batch).  Both follow Eqs. onetrack,
  *                 EulerVelocity and pedestrianmotion; they differ in FP32 rounding only. */
 #define MHC_OPT_GEN_SCAN 4
+/*   MHC_OPT_SCORE  occurrence probabilities when a call passes no weights: 0 (default) uniform per object;
+ *                 1 each hypothesis scored by Eq. (normTraj), n_h = (w_acc n_acc + w_str d_str) /
+ *                 (c_com c_cou), then L1-normalised per object (Section IV-D.1).  The paper fixes neither
+ *                 weights nor factors; the library's defaults: w_acc = w_str = 1/2; vehicles n_acc =
+ *                 1 / (1 + |vdot| / 2 m/s^2); constant steering d_str = 1 / (1 + |delta| / 0.05 rad);
+ *                 paths, from the lateral offsets o_s of their section points from the vehicle's initial
+ *                 line (positive to the left): d_str = 1 / (1 + max |o_s| / 1.75 m), c_com = 1 + (|o_1 -
+ *                 o_0| + |o_2 - o_1|) / 3.5 m, c_cou = 2 when max o_s > 1.75 m (the lane to the left
+ *                 carries counter traffic), else 1; pedestrians n_acc = 1 / (1 + |v - v0| / 1 m/s) for
+ *                 speed grids or 1 / (1 + |vdot| / 2 m/s^2) for acceleration grids, d_str = 1 / (1 +
+ *                 |heading offset| / 0.5 rad), c_com = c_cou = 1. */
+#define MHC_OPT_SCORE 5
 int mhc_set_option(mhc_ctx *ctx, int option, long long value);
 
 /* Work counters of the collision kernel since the last reset, summed over calls on this context:

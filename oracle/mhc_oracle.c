@@ -52,6 +52,7 @@
  *         traffic), else 1;
  *       pedestrians: n_acc = 1 / (1 + |v - v0| / 1 m/s) for speed grids, 1 / (1 + |vdot| / 2 m/s^2) for
  *         acceleration grids; d_str = 1 / (1 + |heading offset| / 0.5 rad); c_com = c_cou = 1.
+ *       orc_scores: parity unpinned beyond this reading's own properties (the paper gives no values).
  *  R-w  path sampling (Section IV-B.2b): at the instants 1.0 / 1.5 / 2.0 s the reference position is
  *       x_t = v0 t ahead; the own lane is sampled at 1/4, 1/2 and 3/4 of its width at x_t, each
  *       neighbouring lane at 1/3 and 2/3 (right to left); a section passes through a sample point with the

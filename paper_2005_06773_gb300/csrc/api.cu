@@ -639,6 +639,9 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     fused = fused && risk && coll_in;
     if (risk) {
         if (int rc = make_risk_args(L, D, bump, table, rout, r)) return rc;
+        r.score = ctx->score;
+        r.grids = D.grids;
+        r.paths = D.paths;
     }
     // after_kernel: the last operation put on the stream here is one of this sequence's kernels, so the
     // next may be a programmatic dependent launch (not while profiling: event records sit in between)
@@ -814,6 +817,7 @@ int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
     if (int r = check_ctx(ctx)) return r;
     if (option == MHC_OPT_CULL) { ctx->cull = value != 0; return MHC_OK; }
     if (option == MHC_OPT_PROFILE) { ctx->profile = value != 0; return MHC_OK; }
+    if (option == MHC_OPT_SCORE) { ctx->score = value != 0; return MHC_OK; }
     if (option == MHC_OPT_GEN_SCAN) {
         if (value < 0 || value > 2) return fail(MHC_E_INVALID, "generation layout must be 0, 1 or 2");
         ctx->gen_scan = (int)value;

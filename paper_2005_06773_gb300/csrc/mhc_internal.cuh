@@ -108,9 +108,12 @@ struct PrepArgs {
     long long h_e;
     const ObjDesc *objs;
     int n_obj;
-    const float *weights;          // [n_traj] raw weights, or null for uniform
+    const float *weights;          // [n_traj] raw weights, or null for uniform (or scored)
     double *prob;                  // [n_traj] normalised probabilities
     float *probf;                  // [n_traj] the same rounded to FP32
+    int score;                     // no weights: 1 scores every hypothesis by Eq. normTraj, 0 uniform
+    const float *grids;            // the hypothesis grids and paths the scores read
+    const float *paths;
 };
 
 struct GenArgs {
@@ -246,7 +249,9 @@ struct RiskArgs {
     int convert_in_walk;           // set by launch_risk_tail: the EGO walk's last CTA converts the totals
     long long n_tiles;
     const int16_t *table;
-    const float *weights;          // [n_traj] raw non-negative weights, or null for uniform
+    const float *weights;          // [n_traj] raw non-negative weights, or null for uniform (or scored)
+    int score;                     // no weights: score the hypotheses by Eq. normTraj (prepare.cuh)
+    const float *grids, *paths;
     double *prob;                  // [n_traj] normalised probabilities (scratch)
     float *probf;                  // [n_traj] the same rounded to FP32 (the per-hit arithmetic)
     RiskScratch acc;

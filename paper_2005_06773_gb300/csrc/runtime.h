@@ -116,7 +116,8 @@ struct mhc_ctx {
     int cull = 1;
     int variant = 0;
     int collide_max_ctas = 0;        // > 0: CTA cap of the warp-per-block collision layouts (serving's large lane)
-    int gen_scan = 2;                // generation: 1 a warp per hypothesis (parallel in time), 0 a thread each, 2 auto
+    int gen_scan = 2;
+    bool score = false;                            // MHC_OPT_SCORE                // generation: 1 a warp per hypothesis (parallel in time), 0 a thread each, 2 auto
     int n_sm = 152;
     // autotuned collision configuration per size class (log2 of the tile count, log2 of the steps)
     struct Tuned { int tiles_log2, steps_log2, fused, variant, cull; };

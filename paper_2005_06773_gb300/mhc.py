@@ -21,6 +21,7 @@ MHC_OPT_CULL = 1
 MHC_OPT_PROFILE = 2
 MHC_OPT_COLLIDE_VARIANT = 3
 MHC_OPT_GEN_SCAN = 4
+MHC_OPT_SCORE = 5
 KERNEL_CLASSES = ("generate", "bounds", "collide", "risk")
 
 

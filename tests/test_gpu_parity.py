@@ -337,6 +337,27 @@ def test_paths_from_lane_dividers(mhc, ctx, orc):
     check_table(orc, sc, t, tab_o, ref, pairs, poff)
 
 
+@pytest.mark.parametrize("name", ["mixed_small", "lane_paths", "ped_accel"])
+def test_scored_probabilities_match_oracle(mhc, ctx, orc, name):
+    """MHC_OPT_SCORE: with no caller weights the risk preparation scores every hypothesis by Eq. normTraj
+    (constant steering, paths, pedestrian speed and acceleration grids); the risk outputs match the
+    oracle's from its own scores, and caller weights still take precedence."""
+    sc = scene(name)
+    ref = orc.generate(sc)
+    tab_o, poff, pairs = orc.table(sc, ref)
+    dev_tab = torch.from_numpy(tab_o).cuda()
+    try:
+        ctx.set_option(mhc.MHC_OPT_SCORE, 1)
+        r_g = mhc.assess(ctx, sc, dev_tab)
+        w = S.random_weights(sc, 5)
+        r_w = mhc.assess(ctx, sc, dev_tab, weights=w)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_option(mhc.MHC_OPT_SCORE, 0)
+    check_risk(r_g, orc.risk(sc, tab_o, pairs, orc.scores(sc)), mhc.layout(sc)["h_ego"])
+    check_risk(r_w, orc.risk(sc, tab_o, pairs, w), mhc.layout(sc)["h_ego"])
+
+
 def test_deterministic_and_stream_independent(mhc, ctx):
     sc = scene("mixed_small")
     s2 = torch.cuda.Stream()
