@@ -328,15 +328,17 @@ __device__ __forceinline__ Aff aff_then(const Aff &first, const Aff &second) {
     return r;
 }
 
-// One vehicle hypothesis by the whole warp (every lane calls it).  Rounds of 32 x 8 sub-steps; lane L
-// takes sub-steps L*8 .. L*8+7 of the round.  Per round: compose and scan the lanes' state maps, run the
-// lanes' sub-steps from their start states (the same per-sub-step arithmetic as the sequential
-// integration), scan the heading increments, form the position increments (heading trig exact at the
-// lane's first sub-step, then rotated by each increment as the sequential integration rotates it), scan
-// them, and store the poses of the output steps that end in each lane's sub-steps (exact heading trig).
+// One vehicle hypothesis by the whole warp (every lane calls it).  Rounds of 32 x 5 sub-steps; lane L
+// takes sub-steps L*5 .. L*5+4 of the round (five per lane keeps the unrolled loops short and out of
+// local memory; a 150-sub-step horizon still takes one round).  Per round: compose and scan the lanes'
+// state maps, run the lanes' sub-steps from their start states (the same per-sub-step arithmetic as the
+// sequential integration), scan the heading increments, form the position increments (heading trig
+// exact at the lane's first sub-step, then rotated by each increment as the sequential integration
+// rotates it), scan them, and store the poses of the output steps that end in each lane's sub-steps
+// (exact heading trig).
 __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Regime &g, int N, int K, int lane,
                              long long base, int h, int i, float *X, float *Y, float *C, float *S) {
-    constexpr int CS = 8;
+    constexpr int CS = 5;
     const int NK = N * K;
     const float ti = (float)o.tau_i_d;
     const float hti2 = 0.5f * ti * ti;
@@ -358,7 +360,7 @@ __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Reg
     float ax = acc, ay = 0.0f;                        // acceleration used by the round's first sub-step
     float ph = o.psi0, pl = 0.0f, xh = o.x0, xl = 0.0f, yh = o.y0, yl = 0.0f;
     for (int nr = 0; nr < NK; nr += 32 * CS) {
-        // sub-steps per lane this round: 8 for full rounds, fewer for the last (150 sub-steps: 5 per lane)
+        // sub-steps per lane this round: CS for full rounds, fewer for the last (100 sub-steps: 4 per lane)
         const int csa = min(CS, (min(NK - nr, 32 * CS) + 31) / 32);
         const int n0 = nr + lane * csa;
         // 1. the lane's state map, composed over its sub-steps, and the warp scan of the maps
