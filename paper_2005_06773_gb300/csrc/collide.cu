@@ -27,6 +27,7 @@
 // (outline kernels only).  Closed sets: touching overlaps.
 // Culling: steps at which two blocks' pose-centre bounding boxes, inflated by R, do not meet are skipped
 // whole (result-preserving).
+#include <algorithm>
 #include <cstdint>
 
 #include "mhc_internal.cuh"
@@ -1212,21 +1213,24 @@ __global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
 }
 
 // The table of the step-item layout from the first-step array, and (probf set) the risk terms of its first
-// hits: one warp per block (grid-stride, lane = column) takes the block's rows 8 at a time (the 8 loads in
-// flight together), writes the int16 entries and adds each first hit's terms with the fixed-point atomics
-// of the fused layouts (the same sums, in any order).
+// hits: one CTA per active block (grid-stride), lane = column, warp w takes rows 8w .. 8w + 7 (its 8 loads
+// in flight together), writes the int16 entries and adds each first hit's terms with the fixed-point
+// atomics of the fused layouts (the same sums, in any order).  Four short chains per block instead of one
+// warp walking 32 rows: the launch is latency-bound.
+constexpr int kTableCtasPerSm = 18;
+
 __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
     pdl_start();
-    __shared__ float s_pa[4][32];                    // the block's row probabilities
-    __shared__ unsigned long long s_sub[4][8][16];   // EGO rows: sums of the CO masses of any subset of
+    __shared__ float s_pa[32];                       // the block's row probabilities
+    __shared__ unsigned long long s_sub[8][16];      // EGO rows: sums of the CO masses of any subset of
                                                      // columns 4q .. 4q + 3 (bit b of m: column 4q + b)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const bool risk = a.probf != nullptr;
     const unsigned long long listed = *a.active_count;
     const long long total = listed < (unsigned long long)(a.n_tiles * 4) ? (long long)listed : a.n_tiles * 4;
-    for (long long q = (long long)blockIdx.x * 4 + w; q < total; q += (long long)gridDim.x * 4) {
+    for (long long q = blockIdx.x; q < total; q += gridDim.x) {
         const BlockAt blk = block_at(a, a.active[q]);
-        if (blk.rows <= 0 || blk.cols <= 0) continue;
+        if (blk.rows <= 0 || blk.cols <= 0) continue;      // the same for the whole CTA
         const PairDesc &P = a.pairs[blk.pair];
         const ObjDesc &A = a.objs[P.a];
         const ObjDesc &B = a.objs[P.b];
@@ -1234,80 +1238,77 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
         const long long kofs = P.kofs, lsum_base = P.lsum_base, hb = B.h;
         const bool col_ok = lane < blk.cols;
         const float pb = risk && col_ok ? a.probf[B.traj_off + blk.j0 + lane] : 0.0f;
-        __syncwarp();                                // the previous block's slots are no longer read
-        s_pa[w][lane] = risk && lane < blk.rows ? a.probf[A.traj_off + blk.i0 + lane] : 0.0f;
+        __syncthreads();                             // the previous block's slots are no longer read
+        if (w == 0) s_pa[lane] = risk && lane < blk.rows ? a.probf[A.traj_off + blk.i0 + lane] : 0.0f;
         if (risk && ego_side == 0) {                 // a row's CO mass = the sum over its colliding columns
             const unsigned long long c = to_fixed(pb, kFixProb);   // zero past the block's columns
+            const int g = threadIdx.x >> 4, m = threadIdx.x & 15;  // one subset sum per thread
+            unsigned long long sum = 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = lane + 32 * u, g = e >> 4, m = e & 15;
-                unsigned long long sum = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const unsigned long long cb = __shfl_sync(0xffffffffu, c, 4 * g + b);
-                    if (m >> b & 1) sum += cb;
-                }
-                s_sub[w][g][m] = sum;
+            for (int bt = 0; bt < 4; ++bt) {
+                const unsigned long long cb = __shfl_sync(0xffffffffu, c, 4 * g + bt);   // column 4g + bt (every warp holds them)
+                if (m >> bt & 1) sum += cb;
             }
+            s_sub[g][m] = sum;
         }
-        __syncwarp();
+        __syncthreads();
+        const int r0 = 8 * w;
+        if (r0 >= blk.rows) continue;                // a ragged block's missing rows (uniform per warp)
         const long long base = P.off + (long long)blk.i0 * hb + blk.j0 + lane;
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = col_ok && r0 + u < blk.rows ? a.first32[base + (long long)(r0 + u) * hb] : 0x7fffffff;
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) any |= v[u] != 0x7fffffff;
+        if (!__ballot_sync(0xffffffffu, any)) {      // no hit in these 8 rows
+            if (col_ok)
+                for (int u = 0; u < 8 && r0 + u < blk.rows; ++u) a.table[base + (long long)(r0 + u) * hb] = -1;
+            continue;
+        }
+        // each lane adds its own first hits' terms; an EGO row's totals come from one ballot
         unsigned long long cnt = 0, mass = 0, col_mass = 0;
         unsigned col_hits = 0;
-        for (int r0 = 0; r0 < blk.rows; r0 += 8) {
-            int v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = col_ok && r0 + u < blk.rows ? a.first32[base + (long long)(r0 + u) * hb] : 0x7fffffff;
-            bool any = false;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) any |= v[u] != 0x7fffffff;
-            if (!__ballot_sync(0xffffffffu, any)) {          // no hit in these 8 rows
-                if (col_ok)
-                    for (int u = 0; u < 8 && r0 + u < blk.rows; ++u) a.table[base + (long long)(r0 + u) * hb] = -1;
-                continue;
-            }
-            // each lane adds its own first hits' terms; an EGO row's totals come from one ballot
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int r = r0 + u;
-                if (r >= blk.rows) break;                     // uniform over the warp
-                const int k = v[u] == 0x7fffffff ? -1 : v[u];
-                if (col_ok) a.table[base + (long long)r * hb] = (int16_t)k;
-                if (!risk) continue;
-                if (k >= 0) {
-                    const float pa = s_pa[w][r];
-                    const unsigned long long wt = to_fixed(pa * pb, kFixProb);
-                    ++cnt;
-                    mass += wt;
-                    atomicAdd(a.acc.count_k + kofs + k, 1ull);
-                    atomicAdd(a.acc.H + kofs + k, wt);
-                    if (ego_side >= 0) {
-                        const long long e = ego_side == 0 ? blk.i0 + r : blk.j0 + lane;   // the EGO hypothesis
-                        const float pco = ego_side == 0 ? pb : pa;                        // the CO hypothesis
-                        atomicAdd(a.acc.lsum + lsum_base + (e * N + k) * n_obj_s + co_local,
-                                  to_fixed(neg_log_survival(pco), kFixLog));
-                        if (ego_side == 1) {
-                            col_mass += to_fixed(pco, kFixProb);
-                            ++col_hits;
-                        }
+        for (int u = 0; u < 8; ++u) {
+            const int r = r0 + u;
+            if (r >= blk.rows) break;                 // uniform over the warp
+            const int k = v[u] == 0x7fffffff ? -1 : v[u];
+            if (col_ok) a.table[base + (long long)r * hb] = (int16_t)k;
+            if (!risk) continue;
+            if (k >= 0) {
+                const float pa = s_pa[r];
+                const unsigned long long wt = to_fixed(pa * pb, kFixProb);
+                ++cnt;
+                mass += wt;
+                atomicAdd(a.acc.count_k + kofs + k, 1ull);
+                atomicAdd(a.acc.H + kofs + k, wt);
+                if (ego_side >= 0) {
+                    const long long e = ego_side == 0 ? blk.i0 + r : blk.j0 + lane;   // the EGO hypothesis
+                    const float pco = ego_side == 0 ? pb : pa;                        // the CO hypothesis
+                    atomicAdd(a.acc.lsum + lsum_base + (e * N + k) * n_obj_s + co_local,
+                              to_fixed(neg_log_survival(pco), kFixLog));
+                    if (ego_side == 1) {
+                        col_mass += to_fixed(pco, kFixProb);
+                        ++col_hits;
                     }
                 }
-                if (ego_side == 0) {                     // the row's EGO hypothesis: CO mass and hits
-                    const unsigned hm = __ballot_sync(0xffffffffu, k >= 0);
-                    if (hm && lane == 0) {
-                        unsigned long long rm = 0;
+            }
+            if (ego_side == 0) {                     // the row's EGO hypothesis: CO mass and hits
+                const unsigned hm = __ballot_sync(0xffffffffu, k >= 0);
+                if (hm && lane == 0) {
+                    unsigned long long rm = 0;
 #pragma unroll
-                        for (int g = 0; g < 8; ++g) rm += s_sub[w][g][(hm >> (4 * g)) & 15];
-                        const long long e = blk.i0 + r;
-                        atomicAdd(a.acc.mass + P.mass_base + e * n_obj_s + co_local, rm);
-                        atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)__popc(hm));
-                    }
+                    for (int g = 0; g < 8; ++g) rm += s_sub[g][(hm >> (4 * g)) & 15];
+                    const long long e = blk.i0 + r;
+                    atomicAdd(a.acc.mass + P.mass_base + e * n_obj_s + co_local, rm);
+                    atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)__popc(hm));
                 }
             }
         }
         if (!risk) continue;
-        if (ego_side == 1 && col_hits) {                                // the block's EGO columns
+        if (ego_side == 1 && col_hits) {             // the warp's share of the block's EGO columns
             const long long e = blk.j0 + lane;
             atomicAdd(a.acc.mass + P.mass_base + e * n_obj_s + co_local, col_mass);
             atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)col_hits);
@@ -1406,7 +1407,9 @@ cudaError_t launch_collide_t(const CollideArgs &a, cudaStream_t st, bool pdl) {
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         e = launch_kernel(items_kernel<OUTL>, dim3((unsigned)(32 * n_sm)), dim3(32), 0, st, true, a);
         if (e != cudaSuccess) return e;
-        return launch_kernel(items_table_kernel, dim3((unsigned)blocks), dim3(128), 0, st, true, a);   // active blocks only
+        // one CTA per active block, at most kTableCtasPerSm per SM (the rest grid-stride)
+        const long long tblocks = std::min(a.n_tiles * 4, (long long)kTableCtasPerSm * n_sm);
+        return launch_kernel(items_table_kernel, dim3((unsigned)tblocks), dim3(128), 0, st, true, a);
     }
     if (a.variant == 4)
         return a.probf ? launch_tile_variant<4, 64, true, OUTL>(a, st, pdl) : launch_tile_variant<4, 64, false, OUTL>(a, st, pdl);
