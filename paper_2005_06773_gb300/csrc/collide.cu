@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
     const PairDesc P = a.pairs[lo];
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
-    const long long t = g - P.tile_start;
-    const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
+    const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
+    const int ta = t / P.tiles_b, tb = t - ta * P.tiles_b;
     const int i0 = ta * kTile, j0 = tb * kTile;
     const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
     const int tid = threadIdx.x, ti = tid / TJ, tj = tid % TJ;
@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
     const PairDesc P = a.pairs[lo];
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
-    const long long t = g - P.tile_start;
-    const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
+    const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
+    const int ta = t / P.tiles_b, tb = t - ta * P.tiles_b;
     const int i0 = ta * kTile, j0 = tb * kTile;
     const int rows = min(kTile, A.h - i0), cols = min(kTile, B.h - j0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -805,8 +805,8 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
     const PairDesc &P = a.pairs[lo];   // fields read where used (fewer live registers)
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
-    const long long t = g - P.tile_start;
-    const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
+    const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
+    const int ta = t / P.tiles_b, tb = t - ta * P.tiles_b;
     const int ba_idx = ta * SUB + quarter / SUB, bb_idx = tb * SUB + quarter % SUB;   // blocks along a, b
     const int i0 = ba_idx * TE, j0 = bb_idx * TE;
     const int rows = min(TE, A.h - i0), cols = min(TE, B.h - j0);
@@ -1054,8 +1054,8 @@ __device__ __forceinline__ BlockAt block_at(const CollideArgs &a, long long gw) 
     const int quarter = (int)(gw & 3);
     const int lo = pair_of_tile(a, g);
     const PairDesc &P = a.pairs[lo];
-    const long long t = g - P.tile_start;
-    const int ta = (int)(t / P.tiles_b), tb = (int)(t - (long long)ta * P.tiles_b);
+    const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
+    const int ta = t / P.tiles_b, tb = t - ta * P.tiles_b;
     BlockAt r;
     r.pair = lo;
     r.i0 = (ta * 2 + (quarter >> 1)) * 32;
@@ -1128,26 +1128,34 @@ __global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
     }
 }
 
-// Persistent one-warp CTAs take items it = blockIdx.x, + gridDim.x, ...: stage the block's 32 + 32 poses
-// of the item's step, broad phase on a 4 x 8 micro-block per lane, candidates compacted and tested one per
-// lane, hits kept with atomicMin on the first-step array (no return value: nothing waits on it).
+// Persistent warps (kItemWarps independent warps per CTA, 32 per SM) take items it = warp, + warps, ...:
+// stage the block's 32 + 32 poses of the item's step, broad phase on a 4 x 8 micro-block per lane,
+// candidates compacted and tested one per lane, hits kept with atomicMin on the first-step array (no
+// return value: nothing waits on it).  One warp per CTA: on the 11-object scene 1, 2 and 4 warps per CTA
+// ran alike, and with octagon outlines one was 12 % faster than two or four.
+constexpr int kItemWarps = 1;
+
 template <bool OUTL>
-__global__ void __launch_bounds__(32, 32) items_kernel(const CollideArgs a) {
+__global__ void __launch_bounds__(32 * kItemWarps, 32 / kItemWarps) items_kernel(const CollideArgs a) {
     pdl_start();
     constexpr int MI = 4, MJ = 8;
-    __shared__ float4 pa_s[32], pb_s[32];   // x, y, h
-    __shared__ float2 ra_s[32], rb_s[32];   // c, s
-    __shared__ unsigned short queue[256];
-    const int lane = threadIdx.x, lr = lane >> 2, lc = lane & 3;
+    __shared__ float4 pa_w[kItemWarps][32], pb_w[kItemWarps][32];   // x, y, h
+    __shared__ float2 ra_w[kItemWarps][32], rb_w[kItemWarps][32];   // c, s
+    __shared__ unsigned short queue_w[kItemWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, lr = lane >> 2, lc = lane & 3;
+    float4 *pa_s = pa_w[w], *pb_s = pb_w[w];
+    float2 *ra_s = ra_w[w], *rb_s = rb_w[w];
+    unsigned short *queue = queue_w[w];
     const float ka = 0.5f * (1.0f - kEps);
     const unsigned long long listed = *a.item_count;
     const long long count = listed < (unsigned long long)a.max_items ? (long long)listed : a.max_items;
+    const long long first = (long long)blockIdx.x * kItemWarps + w, stride = (long long)gridDim.x * kItemWarps;
     unsigned long long narrow = 0, executed = 0;
     StepItem next;                                                   // one item ahead
-    if (blockIdx.x < count) next = a.items[blockIdx.x];
-    for (long long it = blockIdx.x; it < count; it += gridDim.x) {
+    if (first < count) next = a.items[first];
+    for (long long it = first; it < count; it += stride) {
         const StepItem item = next;
-        if (it + gridDim.x < count) next = a.items[it + gridDim.x];
+        if (it + stride < count) next = a.items[it + stride];
         const int k = item.k;
         const ItemBlock bk = a.blocks[item.gw];                      // loaded beside the poses
         const float rc2 = bk.rc2 + kEps0;
@@ -1405,7 +1413,8 @@ cudaError_t launch_collide_t(const CollideArgs &a, cudaStream_t st, bool pdl) {
         if (e != cudaSuccess) return e;
         int n_sm = 152, dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        e = launch_kernel(items_kernel<OUTL>, dim3((unsigned)(32 * n_sm)), dim3(32), 0, st, true, a);
+        e = launch_kernel(items_kernel<OUTL>, dim3((unsigned)(32 / kItemWarps * n_sm)), dim3(32 * kItemWarps), 0, st,
+                          true, a);
         if (e != cudaSuccess) return e;
         // one CTA per active block, at most kTableCtasPerSm per SM (the rest grid-stride)
         const long long tblocks = std::min(a.n_tiles * 4, (long long)kTableCtasPerSm * n_sm);
