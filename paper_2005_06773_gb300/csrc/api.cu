@@ -687,32 +687,8 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         // small tables: the quarter-tile layout writes the -1s of its own blocks (one launch less); large ones
         // are filled by the HBM-rate fill kernel (in-kernel 2-byte row stores cost issue slots there)
         const bool fill_in_collide = (variant == 5 && L.n_entries <= kFillInCollideMax) || variant == 6;
-        {
-            TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_in_collide ? 0 : 1));
-            cudaError_t e = fill_in_collide ? cudaSuccess : launch_fill_table(table, L.n_entries, st, pdl());
-            if (e != cudaSuccess) return cuda_fail(e, "table fill launch");
-            if (!fill_in_collide && L.n_entries > 0) after_kernel = true;
-            if (cull) {
-                BoundsArgs b;
-                b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
-                b.n_warps = (int)L.warp_obj.size(); b.max_steps = L.max_steps; b.x = coll_in->x; b.y = coll_in->y;
-                b.bounds = bounds;
-                e = launch_bounds(b, st, pdl());
-                if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
-                if ((long long)b.n_warps * b.max_steps > 0) after_kernel = true;
-            }
-        }
         CollideArgs c{};
-        c.objs = D.objs; c.pairs = D.pairs_c; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
-        c.max_steps = L.max_steps; c.cull = cull; c.variant = variant; c.fill_blocks = fill_in_collide;
-        c.max_ctas = ctx->collide_max_ctas;
-        c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
-        c.bounds = bounds; c.polys = D.polys; c.table = table; c.counters = ctx->counters;
-        if (fused) {
-            c.probf = r.probf;
-            c.acc = r.acc;
-        }
-        if (variant == 6) {   // the item list and its length (zeroed here)
+        if (variant == 6) {   // the item list and its two counters (zeroed by the bounds kernel, else a memset)
             c.max_items = 4 * L.n_tiles * (long long)L.max_steps;
             c.item_count = static_cast<unsigned long long *>(bump.take(kAlign));
             c.items = static_cast<StepItem *>(bump.take(sizeof(StepItem) * (size_t)c.max_items));
@@ -722,6 +698,36 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
             c.blocks = static_cast<ItemBlock *>(bump.take(sizeof(ItemBlock) * (size_t)(4 * L.n_tiles)));
             if (!c.items || !c.item_count || !c.first32 || !c.active || !c.blocks)
                 return fail(MHC_E_NOMEM, "arena too small for the step items");
+        }
+        bool counts_zeroed = false;
+        {
+            TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_in_collide ? 0 : 1));
+            cudaError_t e = fill_in_collide ? cudaSuccess : launch_fill_table(table, L.n_entries, st, pdl());
+            if (e != cudaSuccess) return cuda_fail(e, "table fill launch");
+            if (!fill_in_collide && L.n_entries > 0) after_kernel = true;
+            if (cull) {
+                BoundsArgs b{};
+                b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
+                b.n_warps = (int)L.warp_obj.size(); b.max_steps = L.max_steps; b.x = coll_in->x; b.y = coll_in->y;
+                b.bounds = bounds;
+                const bool launches = (long long)b.n_warps * b.max_steps > 0;
+                if (variant == 6 && launches) b.zero_counts = c.item_count;
+                e = launch_bounds(b, st, pdl());
+                if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
+                if (launches) after_kernel = true;
+                counts_zeroed = b.zero_counts != nullptr;
+            }
+        }
+        c.objs = D.objs; c.pairs = D.pairs_c; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
+        c.max_steps = L.max_steps; c.cull = cull; c.variant = variant; c.fill_blocks = fill_in_collide;
+        c.max_ctas = ctx->collide_max_ctas;
+        c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
+        c.bounds = bounds; c.polys = D.polys; c.table = table; c.counters = ctx->counters;
+        if (fused) {
+            c.probf = r.probf;
+            c.acc = r.acc;
+        }
+        if (variant == 6 && !counts_zeroed) {
             MHC_CUDA(cudaMemsetAsync(c.item_count, 0, 2 * sizeof(unsigned long long), st));
             after_kernel = false;
         }

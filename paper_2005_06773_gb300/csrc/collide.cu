@@ -1065,24 +1065,55 @@ __device__ __forceinline__ BlockAt block_at(const CollideArgs &a, long long gw) 
     return r;
 }
 
+// What the listing needs of one block, from the descriptors alone (no output of an earlier kernel).
+struct ListBlock {
+    BlockAt blk;
+    int n, ha, hb;
+    float rc;
+    long long bounds_a, bounds_b, pose_a, pose_b, entry0;
+};
+
+__device__ __forceinline__ ListBlock list_block(const CollideArgs &a, long long gw) {
+    ListBlock L;
+    L.blk = block_at(a, gw);
+    const PairDesc &P = a.pairs[L.blk.pair];
+    const ObjDesc &A = a.objs[P.a];
+    const ObjDesc &B = a.objs[P.b];
+    L.n = P.n_steps;
+    L.ha = A.h;
+    L.hb = B.h;
+    L.rc = P.r_cull;
+    L.bounds_a = A.bounds_base + (long long)(L.blk.i0 / kBoundTile) * L.n;
+    L.bounds_b = B.bounds_base + (long long)(L.blk.j0 / kBoundTile) * L.n;
+    L.pose_a = A.pose_base + L.blk.i0;
+    L.pose_b = B.pose_base + L.blk.j0;
+    L.entry0 = P.off + (long long)L.blk.i0 * B.h + L.blk.j0;
+    return L;
+}
+
 // One warp per block (grid-stride): its active steps appended to the item list (one ballot per 32 steps,
 // one atomic per ballot); then a block without any writes its table entries (-1) at once, and an active
-// block sets its first-step entries to INT_MAX and joins the list of active blocks.
-__global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
-    pdl_start();
+// block sets its first-step entries to INT_MAX and joins the list of active blocks.  The first block's
+// descriptors are read before the wait for the bounds kernel, so their chain of dependent loads (pair
+// search, pair, objects) overlaps the bounds kernel's tail.  Bounded to 48 registers (ten CTAs per SM), so
+// that one CTA per tile, up to 1520 tiles, is resident at once.
+__global__ void __launch_bounds__(128, 10) items_list_kernel(const CollideArgs a) {
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
-    const long long total = a.n_tiles * 4;
-    for (long long gw = (long long)blockIdx.x * 4 + (threadIdx.x >> 5); gw < total; gw += (long long)gridDim.x * 4) {
-        const BlockAt blk = block_at(a, gw);
+    const long long total = a.n_tiles * 4, stride = (long long)gridDim.x * 4;
+    long long gw = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+    ListBlock L{};
+    if (gw < total) L = list_block(a, gw);
+    pdl_wait();
+    for (bool first = true; gw < total; gw += stride, first = false) {
+        if (!first) L = list_block(a, gw);
+        const BlockAt &blk = L.blk;
         if (blk.rows <= 0 || blk.cols <= 0) continue;            // a quarter past a ragged edge
-        const PairDesc &P = a.pairs[blk.pair];
-        const ObjDesc &A = a.objs[P.a];
-        const ObjDesc &B = a.objs[P.b];
-        const int N = P.n_steps;
+        const int N = L.n;
         int n_active = 0;
-        const float4 *bA0 = a.bounds + A.bounds_base + (long long)(blk.i0 / kBoundTile) * N;
-        const float4 *bB0 = a.bounds + B.bounds_base + (long long)(blk.j0 / kBoundTile) * N;
-        const float rc = P.r_cull;
+        const float4 *bA0 = a.bounds + L.bounds_a;
+        const float4 *bB0 = a.bounds + L.bounds_b;
+        const float rc = L.rc;
         for (int k0 = 0; k0 < N; k0 += 32) {
             const int k = k0 + lane;
             bool act = k < N;
@@ -1100,28 +1131,31 @@ __global__ void __launch_bounds__(128) items_list_kernel(const CollideArgs a) {
                 const unsigned long long at = base + __popc(m & ((1u << lane) - 1u));
                 if (at < (unsigned long long)a.max_items) {
                     StepItem itm;
-                    itm.pa = A.pose_base + (long long)k * A.h + blk.i0;
-                    itm.pb = B.pose_base + (long long)k * B.h + blk.j0;
+                    itm.pa = L.pose_a + (long long)k * L.ha;
+                    itm.pb = L.pose_b + (long long)k * L.hb;
                     itm.gw = (int)gw;
                     itm.k = k;
                     a.items[at] = itm;
                 }
             }
         }
-        const long long base = P.off + (long long)blk.i0 * B.h + blk.j0 + lane;
+        const long long base = L.entry0 + lane;
         if (n_active == 0) {                    // never close: the table entries are final now
             if (lane < blk.cols)
-                for (int r = 0; r < blk.rows; ++r) a.table[base + (long long)r * B.h] = (int16_t)-1;
+                for (int r = 0; r < blk.rows; ++r) a.table[base + (long long)r * L.hb] = (int16_t)-1;
             continue;
         }
         if (lane < blk.cols)
-            for (int r = 0; r < blk.rows; ++r) a.first32[base + (long long)r * B.h] = 0x7fffffff;
+            for (int r = 0; r < blk.rows; ++r) a.first32[base + (long long)r * L.hb] = 0x7fffffff;
         if (lane == 0) {
+            const PairDesc &P = a.pairs[blk.pair];
+            const ObjDesc &A = a.objs[P.a];
+            const ObjDesc &B = a.objs[P.b];
             const unsigned long long at = atomicAdd(a.active_count, 1ull);
             if (at < (unsigned long long)(a.n_tiles * 4)) a.active[at] = (int)gw;
             ItemBlock rec;
-            rec.entry0 = P.off + (long long)blk.i0 * B.h + blk.j0;
-            rec.h_b = B.h; rec.pair = blk.pair; rec.rows = blk.rows; rec.cols = blk.cols;
+            rec.entry0 = L.entry0;
+            rec.h_b = L.hb; rec.pair = blk.pair; rec.rows = blk.rows; rec.cols = blk.cols;
             rec.rc2 = P.rc2; rec.la = A.hl; rec.wa = A.hw; rec.ra = A.rad; rec.lb = B.hl; rec.wb = B.hw; rec.rb = B.rad;
             a.blocks[gw] = rec;
         }

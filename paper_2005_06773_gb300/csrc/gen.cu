@@ -575,20 +575,37 @@ __global__ void __launch_bounds__(128, 8) gen_kernel(const GenArgs a) {
         pedestrian(o, ga, gb, o.n_steps, o.tau, o.pose_base, o.h, i, a.x, a.y, a.c, a.s);
 }
 
-// Bounding box of the 32 pose centres of each bound tile at each step (warp min/max reduction).
+// Bounding box of the 32 pose centres of each bound tile at each step: one warp per (32-hypothesis group,
+// step), a warp min/max reduction.  The descriptors are read before the wait for the generation kernel,
+// the poses after it.
 __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
-    pdl_start();
+    pdl_trigger();
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long total = (long long)a.n_warps * a.max_steps;
-    if (g >= total) return;
-    const int w = (int)(g / a.max_steps), k = (int)(g - (long long)w * a.max_steps);
-    const ObjDesc &o = a.objs[a.warp_obj[w]];
-    if (k >= o.n_steps) return;
     const int lane = threadIdx.x & 31;
-    const int i = a.warp_first[w] + lane;
+    bool live = g < total;
+    int k = 0, first = 0, h = 0, n_steps = 0;
+    long long pose_base = 0, bounds_base = 0;
+    if (live) {
+        const int w = (int)(g / a.max_steps);
+        k = (int)(g - (long long)w * a.max_steps);
+        const ObjDesc &o = a.objs[a.warp_obj[w]];
+        first = a.warp_first[w];
+        h = o.h;
+        n_steps = o.n_steps;
+        pose_base = o.pose_base;
+        bounds_base = o.bounds_base;
+    }
+    pdl_wait();
+    if (a.zero_counts && g == 0 && lane == 0) {
+        a.zero_counts[0] = 0ull;
+        a.zero_counts[1] = 0ull;
+    }
+    if (!live || k >= n_steps) return;
+    const int i = first + lane;
     float x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
-    if (i < o.h) {
-        const long long idx = o.pose_base + (long long)k * o.h + i;
+    if (i < h) {
+        const long long idx = pose_base + (long long)k * h + i;
         x0 = x1 = a.x[idx];
         y0 = y1 = a.y[idx];
     }
@@ -599,8 +616,7 @@ __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
         x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, d));
         y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, d));
     }
-    if (lane == 0) a.bounds[o.bounds_base + (long long)(a.warp_first[w] / kBoundTile) * o.n_steps + k] =
-        make_float4(x0, y0, x1, y1);
+    if (lane == 0) a.bounds[bounds_base + (long long)(first / kBoundTile) * n_steps + k] = make_float4(x0, y0, x1, y1);
 }
 
 }  // namespace

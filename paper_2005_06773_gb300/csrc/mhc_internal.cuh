@@ -140,6 +140,7 @@ struct BoundsArgs {
     int n_warps, max_steps;   // grid covers n_warps x max_steps; steps beyond an object's own are skipped
     const float *x, *y;
     float4 *bounds;
+    unsigned long long *zero_counts;   // if set: two words zeroed after the wait (the step-item counters)
 };
 
 // Risk accumulators: one contiguous block of 64-bit words, zeroed before every assessment.  Masses and
@@ -151,10 +152,15 @@ struct BoundsArgs {
 // without the attribute).  A dependent's blocks thus sit resident, waiting, while its predecessor's tail
 // runs, instead of being launched after it ends.  Because every block waits first, a kernel completes only
 // after its predecessor did, so the ordering stays transitive along the chain.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_start() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_trigger();
+    pdl_wait();
 }
+// Between pdl_trigger() and pdl_wait() a kernel may read only what was in memory before the first kernel
+// of its chain began (the uploaded descriptors): the first kernel after a copy is launched in plain stream
+// order, so every later kernel starts after that copy completed.
 
 // kernel<<<grid, block, smem, st>>>(args...), with programmatic stream serialization when pdl is set.
 template <typename... KArgs, typename... Args>

@@ -194,7 +194,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
     const int *d_warp_first = reinterpret_cast<const int *>(dev + kObjBytes + kPairBytes + kWarpBytes);
     float4 *d_bounds = reinterpret_cast<float4 *>(dev + kDescBytes);
 
-    BoundsArgs b;
+    BoundsArgs b{};
     b.objs = d_objs;
     b.warp_obj = d_warp_obj;
     b.warp_first = d_warp_first;
