@@ -227,18 +227,24 @@ constexpr int kEscapeBatch = 8;    // escape ranking: 256 EGO hypotheses' keys i
 constexpr int kWalkBatch = 12;     // chronological walk: 384 cells in flight per round
 
 __global__ void __launch_bounds__(64) ego_kernel(const RiskArgs a) {
-    pdl_start();
+    pdl_trigger();
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31;
-    convert_pair_totals(a, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // the scenario of EGO hypothesis g and its descriptor: uploaded data, read before the wait
+    int lo = 0;
+    ScenDesc sd{};
     if (g < a.h_e) {
-        int lo = 0, hi = a.n_scen - 1;     // the scenario of EGO hypothesis g
+        int hi = a.n_scen - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (a.scens[mid].e_base <= g) lo = mid; else hi = mid - 1;
         }
-        const ScenDesc sd = a.scens[lo];
+        sd = a.scens[lo];
+    }
+    pdl_wait();
+    convert_pair_totals(a, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    if (g < a.h_e) {
         const int N = sd.n_steps, n_obj = sd.n_obj;
         const long long i = g - sd.e_base;
         const double pe = a.prob[sd.e_traj + i];
