@@ -27,6 +27,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from typing import Optional
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -37,7 +38,7 @@ UNIT = "tests/s"
 PROFILE_NOTES = {5: os.path.join(ROOT, "profiles", "collide_tile_kernel_intersection11.md"),
                  6: os.path.join(ROOT, "profiles", "items_kernels_intersection11.md")}
 COLLIDE_SRC = [os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", f) for f in ("collide.cu", "mhc_internal.cuh")]
-# algorithmic FP32-pipe lane instructions per unit of collision work (roofline section)
+# algorithmic FP32-pipe lane instructions per unit of collision work
 OPS_PER_BROAD_TEST = 3.0      # 2 FFMA (expanded squared distance) + 1 compare
 OPS_PER_NARROW_TEST = 30.0    # separating-axis test of two rectangles, worst shape combination
 FP32_LANES_PER_SM = 128
@@ -143,8 +144,65 @@ def traffic_from_profile(variant: int):
     return float(m_b.group(1))
 
 
+class NvmlClocks:
+    """SM clock, its maximum, power and clock-event reasons polled through NVML (read-only queries, driver
+    library via ctypes) every `period_s` in a thread while the timed region runs, so that even a region of a
+    few milliseconds has samples inside it."""
+    BITS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
+
+    def __init__(self, uuid: Optional[str], index: int, period_s: float = 0.002):
+        import ctypes as C
+        import threading
+        self.C, self.period, self.rows, self.stop_flag = C, period_s, [], threading.Event()
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.lib, self.h = lib, C.c_void_p()
+        found = False
+        for u in ([uuid, "GPU-" + uuid] if uuid else []):
+            if lib.nvmlDeviceGetHandleByUUID(C.c_char_p(u.encode()), C.byref(self.h)) == 0:
+                found = True
+                break
+        if not found and lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = C.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(self.h, C.c_int(1), C.byref(mx))     # NVML_CLOCK_SM
+        self.max_mhz = float(mx.value)
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _sample(self):
+        C, lib = self.C, self.lib
+        mhz, mw, rs = C.c_uint(0), C.c_uint(0), C.c_ulonglong(0)
+        if lib.nvmlDeviceGetClockInfo(self.h, C.c_int(1), C.byref(mhz)) != 0:
+            return
+        lib.nvmlDeviceGetPowerUsage(self.h, C.byref(mw))
+        self.reasons_fn(self.h, C.byref(rs))
+        self.rows.append((float(mhz.value), mw.value / 1e3, int(rs.value)))
+
+    def _run(self):
+        while not self.stop_flag.is_set():
+            self._sample()
+            time.sleep(self.period)
+
+    def start(self):
+        self._sample()
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        self._sample()
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({name for r in self.rows for bit, name in self.BITS.items() if r[2] & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(self.rows), "power_w_max": max((r[1] for r in self.rows), default=None),
+                "source": f"NVML every {self.period * 1e3:g} ms during the timed region"}
+
+
 class Clocks:
-    """nvidia-smi sampler (200 ms) around the timed region."""
+    """nvidia-smi sampler (200 ms) around the timed region: the fallback when NVML cannot be loaded."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -628,7 +686,14 @@ def run_mhc(args):
         step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(local)
+    try:   # NVML (samples inside even a short timed region), else nvidia-smi
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            uuid = None
+        clocks = NvmlClocks(uuid, local)
+    except Exception:
+        clocks = Clocks(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
