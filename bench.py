@@ -222,6 +222,8 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            self.tmp.close()
+            os.unlink(self.tmp.name)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.proc.terminate()
         try:
