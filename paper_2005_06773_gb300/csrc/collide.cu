@@ -1157,6 +1157,7 @@ __global__ void __launch_bounds__(128, 10) items_list_kernel(const CollideArgs a
             rec.entry0 = L.entry0;
             rec.h_b = L.hb; rec.pair = blk.pair; rec.rows = blk.rows; rec.cols = blk.cols;
             rec.rc2 = P.rc2; rec.la = A.hl; rec.wa = A.hw; rec.ra = A.rad; rec.lb = B.hl; rec.wb = B.hw; rec.rb = B.rad;
+            rec.i0 = blk.i0; rec.j0 = blk.j0;
             a.blocks[gw] = rec;
         }
     }
@@ -1271,17 +1272,22 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
     const unsigned long long listed = *a.active_count;
     const long long total = listed < (unsigned long long)(a.n_tiles * 4) ? (long long)listed : a.n_tiles * 4;
     for (long long q = blockIdx.x; q < total; q += gridDim.x) {
-        const BlockAt blk = block_at(a, a.active[q]);
-        if (blk.rows <= 0 || blk.cols <= 0) continue;      // the same for the whole CTA
-        const PairDesc &P = a.pairs[blk.pair];
-        const ObjDesc &A = a.objs[P.a];
-        const ObjDesc &B = a.objs[P.b];
+        // the block's record (written by the listing kernel): its first-step rows are one load away, and this
+        // warp's 8 rows are loaded before the shared set-up below
+        const ItemBlock bk = a.blocks[a.active[q]];
+        const int r0 = 8 * w;
+        const long long hb = bk.h_b, base = bk.entry0 + lane;
+        const bool col_ok = lane < bk.cols;
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = col_ok && r0 + u < bk.rows ? a.first32[base + (long long)(r0 + u) * hb] : 0x7fffffff;
+        const PairDesc &P = a.pairs[bk.pair];
         const int N = P.n_steps, ego_side = P.ego_side, n_obj_s = P.n_obj_s, co_local = P.co_local;
-        const long long kofs = P.kofs, lsum_base = P.lsum_base, hb = B.h;
-        const bool col_ok = lane < blk.cols;
-        const float pb = risk && col_ok ? a.probf[B.traj_off + blk.j0 + lane] : 0.0f;
+        const long long kofs = P.kofs, lsum_base = P.lsum_base;
+        const float pb = risk && col_ok ? a.probf[a.objs[P.b].traj_off + bk.j0 + lane] : 0.0f;
         __syncthreads();                             // the previous block's slots are no longer read
-        if (w == 0) s_pa[lane] = risk && lane < blk.rows ? a.probf[A.traj_off + blk.i0 + lane] : 0.0f;
+        if (w == 0) s_pa[lane] = risk && lane < bk.rows ? a.probf[a.objs[P.a].traj_off + bk.i0 + lane] : 0.0f;
         if (risk && ego_side == 0) {                 // a row's CO mass = the sum over its colliding columns
             const unsigned long long c = to_fixed(pb, kFixProb);   // zero past the block's columns
             const int g = threadIdx.x >> 4, m = threadIdx.x & 15;  // one subset sum per thread
@@ -1294,19 +1300,13 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
             s_sub[g][m] = sum;
         }
         __syncthreads();
-        const int r0 = 8 * w;
-        if (r0 >= blk.rows) continue;                // a ragged block's missing rows (uniform per warp)
-        const long long base = P.off + (long long)blk.i0 * hb + blk.j0 + lane;
-        int v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            v[u] = col_ok && r0 + u < blk.rows ? a.first32[base + (long long)(r0 + u) * hb] : 0x7fffffff;
+        if (r0 >= bk.rows) continue;                 // a ragged block's missing rows (uniform per warp)
         bool any = false;
 #pragma unroll
         for (int u = 0; u < 8; ++u) any |= v[u] != 0x7fffffff;
         if (!__ballot_sync(0xffffffffu, any)) {      // no hit in these 8 rows
             if (col_ok)
-                for (int u = 0; u < 8 && r0 + u < blk.rows; ++u) a.table[base + (long long)(r0 + u) * hb] = -1;
+                for (int u = 0; u < 8 && r0 + u < bk.rows; ++u) a.table[base + (long long)(r0 + u) * hb] = -1;
             continue;
         }
         // each lane adds its own first hits' terms; an EGO row's totals come from one ballot
@@ -1315,7 +1315,7 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int r = r0 + u;
-            if (r >= blk.rows) break;                 // uniform over the warp
+            if (r >= bk.rows) break;                 // uniform over the warp
             const int k = v[u] == 0x7fffffff ? -1 : v[u];
             if (col_ok) a.table[base + (long long)r * hb] = (int16_t)k;
             if (!risk) continue;
@@ -1327,7 +1327,7 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
                 atomicAdd(a.acc.count_k + kofs + k, 1ull);
                 atomicAdd(a.acc.H + kofs + k, wt);
                 if (ego_side >= 0) {
-                    const long long e = ego_side == 0 ? blk.i0 + r : blk.j0 + lane;   // the EGO hypothesis
+                    const long long e = ego_side == 0 ? bk.i0 + r : bk.j0 + lane;   // the EGO hypothesis
                     const float pco = ego_side == 0 ? pb : pa;                        // the CO hypothesis
                     atomicAdd(a.acc.lsum + lsum_base + (e * N + k) * n_obj_s + co_local,
                               to_fixed(neg_log_survival(pco), kFixLog));
@@ -1343,7 +1343,7 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
                     unsigned long long rm = 0;
 #pragma unroll
                     for (int g = 0; g < 8; ++g) rm += s_sub[g][(hm >> (4 * g)) & 15];
-                    const long long e = blk.i0 + r;
+                    const long long e = bk.i0 + r;
                     atomicAdd(a.acc.mass + P.mass_base + e * n_obj_s + co_local, rm);
                     atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)__popc(hm));
                 }
@@ -1351,7 +1351,7 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
         }
         if (!risk) continue;
         if (ego_side == 1 && col_hits) {             // the warp's share of the block's EGO columns
-            const long long e = blk.j0 + lane;
+            const long long e = bk.j0 + lane;
             atomicAdd(a.acc.mass + P.mass_base + e * n_obj_s + co_local, col_mass);
             atomicAdd(a.acc.hits + P.hits_base + e, (unsigned long long)col_hits);
         }

@@ -199,12 +199,14 @@ struct RiskScratch {
 };
 
 // A 32 x 32 block of the step-item layout (variant 6) with active steps, recorded by the listing kernel so
-// that an item needs no descriptor search: table entry (i, j) of the block at entry0 + i h_b + j, the
-// pair's squared circumradius sum and the two shapes' half extents and radii.
+// that an item (and the table kernel) needs no descriptor search: table entry (i, j) of the block at
+// entry0 + i h_b + j, the pair's squared circumradius sum, the two shapes' half extents and radii, and the
+// block's origin in its pair.
 struct __align__(16) ItemBlock {
     long long entry0;
     int h_b, pair, rows, cols;
     float rc2, la, wa, ra, lb, wb, rb;
+    int i0, j0;               // the block's first row and column within its pair
 };
 
 // One item of the step-item layout: an active step k of block gw, with the pose indices of the step's first
