@@ -533,9 +533,11 @@ __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Reg
 
 // LAYOUTS: 1 every task is a warp per hypothesis, 2 every task is a thread per hypothesis, 3 both (a kernel
 // holding one layout only has a smaller instruction footprint: the integration is latency-bound and
-// instruction fetch was its largest stall).
+// instruction fetch was its largest stall).  Bounded to 80 registers (six CTAs per SM), where the
+// integration has no spills: faster than 64 (eight per SM, all of the 11-object scene's CTAs resident)
+// on the 11-object and 32-vehicle scenes.
 template <int LAYOUTS>
-__global__ void __launch_bounds__(128, 8) gen_kernel(const GenArgs a) {
+__global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
     pdl_start();
     if ((int)blockIdx.x >= a.gen_blocks) {               // the risk preparation, independent of generation
         prepare_block(a.prep, blockIdx.x - a.gen_blocks, a.prep_blocks);
