@@ -7,7 +7,7 @@
  * Algorithm for Criticality Estimation in Traffic and Collision Avoidance") in its own order and
  * notation, in double precision, without blocking, fusion or reordering.
  *
- * Readings taken where the paper is silent or ambiguous (each listed in the design notes):
+ * Readings taken where the paper is silent or ambiguous:
  *  R-a  yaw rate update r_{n+1} = r_n + rdot_n tau (omitted in Eq. EulerVelocity).
  *  R-b  a_x,0 = vdot, a_y,0 = 0 (a_{.,n} is used before it is defined); this makes straight-line
  *       constant-acceleration motion exact.

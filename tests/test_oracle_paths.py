@@ -111,3 +111,27 @@ def test_scenario_paths_feed_generation(orc):
                                   n_steps=30, tau=TAU, substeps=K)
             np.testing.assert_array_equal(ref["x"][2 * ia + ib], r["x"])
             np.testing.assert_array_equal(ref["y"][2 * ia + ib], r["y"])
+
+
+# Eq. (controller) by hand, in degrees: g = |(-0.018 v + 1.5) d|, delta = (g + 0.5) d + (-g + 9.5)(3.8197 e).
+# (v m/s, d_path m, e_psi rad, delta deg); each gain changes at least one of these values.
+CONTROLLER_CASES = [
+    (10.0, 1.0, 0.0, 1.82),            # g = 1.32
+    (10.0, -1.0, 0.0, -1.82),          # the magnitude in g, the sign from d
+    (100.0, 1.0, 0.0, 0.8),            # -0.018 v + 1.5 < 0: g = |-0.3| = 0.3
+    (5.0, 0.0, -0.1, -3.628715),       # g = 0: 9.5 x 3.8197 x (-0.1)
+    (20.0, -0.5, 0.05, 1.17049605),    # g = 0.57: -0.535 + 8.93 x 0.190985
+    (30.0, 2.0, 0.02, 5.41906652),     # g = 1.92: 4.84 + 7.58 x 0.076394
+]
+
+
+@pytest.mark.parametrize("v,d,e,want_deg", CONTROLLER_CASES)
+def test_controller_gains_by_hand(orc, v, d, e, want_deg):
+    """The first sub-step's steering angle is the controller's command itself: the vehicle starts at the
+    origin heading along x with beta = 0, so its centre of gravity predicted 0.5 s ahead is (0.5 v, 0);
+    section 0 passes through (0.5 v, d / cos e) with direction e, so the line lies d to the left of that
+    point (d_path = d) and the yaw error is e.  With tau_i = 10 s the rate limit (0.5 rad/s x tau_i) is out of
+    reach and every command here stays below the 0.5 rad angle limit."""
+    path = [[0.5 * v, d / math.cos(e), e]] * 3
+    r = orc.path_steering(0.0, 0.0, 0.0, v, 0.0, path, n_steps=1, tau=10.0, substeps=1)
+    assert r["delta"][0] == pytest.approx(math.radians(want_deg), rel=1e-12, abs=1e-15)
