@@ -38,14 +38,35 @@ UNIT = "tests/s"
 PROFILE_NOTES = {5: os.path.join(ROOT, "profiles", "collide_tile_kernel_intersection11.md"),
                  6: os.path.join(ROOT, "profiles", "items_kernels_intersection11.md")}
 COLLIDE_SRC = [os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", f) for f in ("collide.cu", "mhc_internal.cuh")]
-# algorithmic FP32-pipe lane instructions per unit of collision work
-OPS_PER_BROAD_TEST = 3.0      # 2 FFMA (expanded squared distance) + 1 compare
-OPS_PER_NARROW_TEST = 30.0    # separating-axis test of two rectangles, worst shape combination
+# Algorithmic lane instructions (FP32 pipe + ALU) per unit of collision work:
+#   broad-phase test: dx, dy (2 FADD), d^2 (FMUL + FFMA), compare = 4 FP32 + 1 ALU = 5;
+#   narrow-phase test by shape pair: rectangle-rectangle separating axes (relative rotation 4, frame
+#   transforms 8, projected radii 8, abs 4, compares 4) = 24 FP32 + 8 ALU = 32; rectangle-disc (frame
+#   transform 4, clamps 4, distance 2, compare) = 10 FP32 + 6 ALU = 16; disc-disc (dx, dy, d^2, compare) = 5;
+#   convex outlines of n vertices: outline-outline 2 n^2 + 16 n (each edge against every vertex of the
+#   other, both ways), outline-disc 5 n + 4.
+OPS_PER_BROAD_TEST = 5.0
+OPS_PER_NARROW = {"rect_rect": 32.0, "rect_disc": 16.0, "disc_disc": 5.0}
 FP32_LANES_PER_SM = 128
+
+
+def collide_ops(work: dict, n_vertices: float = 0.0) -> float:
+    """Algorithmic lane instructions of the collision work counted by the kernels (mhc_collision_counters)."""
+    nv = float(n_vertices)
+    ops = OPS_PER_BROAD_TEST * work["executed"]
+    ops += sum(c * work[k] for k, c in OPS_PER_NARROW.items())
+    ops += (2 * nv * nv + 16 * nv) * work.get("outline_outline", 0) + (5 * nv + 4) * work.get("outline_disc", 0)
+    return ops
+
+
+def mean_vertices(sc) -> float:
+    nv = [len(o.outline) for o in sc.objects if getattr(o, "outline", None) is not None]
+    return sum(nv) / len(nv) if nv else 0.0
 # the kernel behind each collision layout (MHC_OPT_COLLIDE_VARIANT)
 COLLIDE_KERNELS = {1: "collide_kernel<256, 4, 4, 16>", 2: "collide_kernel<64, 8, 8, 8>", 3: "collide_warp_kernel<4, 8>",
                    4: "collide_tile_kernel<4, 64>", 5: "collide_tile_kernel<1, 32>",
-                   6: "items_list_kernel + items_kernel + items_table_kernel (per-launch figures average the three)"}
+                   6: "items_list_kernel + items_kernel + items_table_kernel (per-launch figures average the three)",
+                   7: "block_kernel<4>", 8: "block_list_kernel + block_rec_kernel<4> (per-launch figures average the two)"}
 
 
 def parse():
@@ -59,8 +80,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the stress32 / paper_s2 / batch / serving measurements")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="window of the serving measurement")
-    ap.add_argument("--collide-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="window of the serving measurement at 2000/s")
+    ap.add_argument("--serve-rates", default="4000,8000",
+                    help="further offered rates (requests/s) of the serving sweep, 2 s windows each ('' for none)")
+    ap.add_argument("--collide-variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8],
                     help="collision kernel layout; 0 = chosen by mhc_autotune in the set-up (profiling fixes one)")
     ap.add_argument("--workload", default="intersection11", choices=sorted(WORKLOADS),
                     help="the timed workload (the default is the benchmark's; the others serve profiling)")
@@ -272,7 +295,7 @@ def cpu_baseline(sc, budget_s: float):
     return {"value": passes * sc.n_tests() / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{passes} full pass(es) of the 11-object scene (generate + table + risk, "
                       f"{sc.n_tests():.3e} tests each) in {dt:.1f} s on 1 host thread",
-            "seconds": dt}
+            "seconds": dt}, out
 
 
 _ORACLE_STATE = {}
@@ -427,22 +450,22 @@ def measure_workload(mhc, torch, sc, dev, steps, flush, peak):
     torch.cuda.synchronize()
     ctx.profile(False)
     prof = ctx.profile_read(reset=True)
-    executed, narrow = ctx.counters(reset=True)
+    work = ctx.work(reset=True)
     coll_ms, coll_n = prof["collide"]
     coll_s = coll_ms / 1e3 / max(coll_n, 1)
-    ops = (OPS_PER_BROAD_TEST * executed + OPS_PER_NARROW_TEST * narrow) / max(coll_n, 1)
+    ops = collide_ops(work, mean_vertices(sc)) / max(coll_n, 1)
     out = {"tests_per_step": sc.n_tests(), "ms_per_step": ms, "tests_per_s": sc.n_tests() / (ms / 1e3),
            "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
-           "executed_tests_per_launch": executed / max(coll_n, 1),
+           "work_per_step": {k: v / steps for k, v in work.items() if v},
            "collide_roofline_frac": ops / coll_s / 1e12 / peak, "collide_achieved": ops / coll_s / 1e12,
-           "collide_layout": {"variant": tuned[0], "cull": tuned[1]}}
+           "collide_layout": [tuned[0], tuned[1]]}
     ctx.close()
     del table
     torch.cuda.empty_cache()
     return out
 
 
-def measure_batch(mhc, torch, dev, steps, flush, count=256):
+def measure_batch(mhc, torch, dev, steps, flush, batch_peak, count=256):
     """The uneven batch (256 scenarios, 2-24 objects, 64-1024 hypotheses, 20-50 steps) three ways, device
     time per batch with CUDA events (L2 flushed before each): a plan replayed as one CUDA graph, one
     mhc_evaluate_batch call, and the plain path of one mhc_evaluate call per scenario."""
@@ -487,7 +510,7 @@ def measure_batch(mhc, torch, dev, steps, flush, count=256):
     torch.cuda.synchronize()
     ctx.profile(False)
     prof = ctx.profile_read(reset=True)
-    executed, narrow = ctx.counters(reset=True)
+    work = ctx.work(reset=True)
     # plain path: one mhc_evaluate per scenario into its own slice of the same buffers
     singles = []
     for sc, sl in zip(cb.items, sls):
@@ -513,7 +536,9 @@ def measure_batch(mhc, torch, dev, steps, flush, count=256):
         "batch_call": {"ms_per_batch": b_ms, "scenarios_per_s": count / (b_ms / 1e3),
                        "tests_per_s": tests / (b_ms / 1e3), "host_ms_per_call": b_host,
                        "kernels_ms_per_batch": {k: v[0] / n_calls for k, v in prof.items()},
-                       "executed_tests_per_batch": executed / n_calls, "narrow_tests_per_batch": narrow / n_calls},
+                       "work_per_batch": {k: v / n_calls for k, v in work.items() if v},
+                       "collide_roofline_frac": collide_ops(work) / n_calls / (prof["collide"][0] / n_calls / 1e3) / 1e12
+                                                / batch_peak},
         "plain_per_scenario": {"ms_per_batch": p_ms, "scenarios_per_s": count / (p_ms / 1e3),
                                "tests_per_s": tests / (p_ms / 1e3), "host_ms_per_batch": p_host},
     }
@@ -531,7 +556,7 @@ def arrivals(rate: float, seconds: float, large_share: float, seed: int = 5):
         out.append((t, 1 if rng.uniform(0.0, 1.0) < large_share else 0))
 
 
-def measure_serving(mhc, torch, dev, seconds: float, rate: float = 2000.0, large_share: float = 0.05):
+def measure_serving(mhc, torch, dev, seconds: float, rates: str = "", rate: float = 2000.0, large_share: float = 0.05):
     """Served requests (continuous batching, mhc_submit / mhc_poll) against the plain path (one synchronous
     mhc_run per request in arrival order) at the same offered load: Poisson arrivals at `rate`, 95 % shaped
     like the 11-object scene (64 placements, cycled) and 5 % like the 32-vehicle scene (4 placements).
@@ -728,7 +753,7 @@ def run_mhc(args):
     torch.cuda.synchronize()
     ctx.profile(False)
     prof = ctx.profile_read(reset=True)
-    executed, narrow = ctx.counters(reset=True)
+    work = ctx.work(reset=True)
     # the same step replayed from a plan (the scenario laid out once, its launch sequence a CUDA graph)
     plan = mhc.Plan(ctx, [sc], graph=True)
     pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(prof_steps)]
@@ -763,7 +788,7 @@ def run_mhc(args):
 
     coll_ms, coll_n = prof["collide"]
     avg_coll_s = coll_ms / 1e3 / max(coll_n, 1)
-    ops_per_launch = (OPS_PER_BROAD_TEST * executed + OPS_PER_NARROW_TEST * narrow) / max(coll_n, 1)
+    ops_per_launch = collide_ops(work, mean_vertices(sc)) / max(coll_n, 1)
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -776,60 +801,87 @@ def run_mhc(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(sc),
-        "latency_ms": {"scene_device_p50": pct(step_ms, 50), "scene_device_p99": pct(step_ms, 99),
-                       "scene_e2e_p50": pct(e2e_ms, 50), "scene_e2e_p99": pct(e2e_ms, 99)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "mhc_run: host scenario -> device -> host risk outputs (pinned), stream synchronised"},
         "gpu_launches": launches,
-        "kernels_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
-        "kernel_split_note": f"library per-kernel CUDA events over {prof_steps} further steps (not the timed ones)",
-        "plan_graph": {"ms_per_step_p50": pct(plan_ms, 50), "tests_per_s": sc.n_tests() / (statistics.mean(plan_ms) / 1e3),
-                       "note": "the same step replayed from a plan: layout once, descriptor upload + kernels as one CUDA graph"},
-        "collision_work": {"nominal_tests_per_launch": sc.n_tests(), "executed_tests_per_launch": executed / max(coll_n, 1),
-                           "narrow_tests_per_launch": narrow / max(coll_n, 1),
-                           "collide_launches_per_step": coll_n / max(prof_steps, 1),
-                           "nominal_tests_per_s_collide_only": sc.n_tests() * prof_steps / (coll_ms / 1e3)},
         "roofline": {"bound": "alu", "kernel": COLLIDE_KERNELS.get(tuned[0], "collide"), "achieved": achieved, "peak": peak,
-                     "unit": "T FP32-lane-instr/s", "frac": achieved / peak, "traffic": traffic,
+                     "unit": "T lane-instr/s", "frac": achieved / peak, "traffic": traffic,
                      "avg_launch_ms": 1e3 * avg_coll_s, "ops_per_launch": ops_per_launch,
                      "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
-                                    "(sm_max_mhz of MEASURED_PEAKS.json)"},
+                                    "(sm_max_mhz of MEASURED_PEAKS.json)",
+                     "ops": "5 per executed broad test + 32 rect-rect / 16 rect-disc / 5 disc-disc per narrow test"},
         "clocks": clk,
-        "collide_layout": {"variant": tuned[0], "cull": tuned[1],
-                           "chosen_by": "--collide-variant" if args.collide_variant else "mhc_autotune (untimed set-up)"},
+        "latency_ms": {"device_p50": pct(step_ms, 50), "device_p99": pct(step_ms, 99),
+                       "e2e_p50": pct(e2e_ms, 50), "e2e_p99": pct(e2e_ms, 99)},
+        "kernels_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items()},
+        "plan_graph_ms_p50": pct(plan_ms, 50),
+        "collision_work": dict({k: v / max(coll_n, 1) for k, v in work.items()}, launches_per_step=coll_n / max(prof_steps, 1)),
+        "collide_layout": [tuned[0], tuned[1], "--collide-variant" if args.collide_variant else "mhc_autotune"],
         "wall_s_timed_region": wall,
     }
     if not args.no_extra:
         from paper_2005_06773_gb300 import scenarios as S
         line["extra_workloads"] = {
-            "stress32": dict(measure_workload(mhc, torch, S.stress32(4), dev, 5, flush, peak),
-                             workload="32 cars x 2048 hypotheses (64 accel x 32 steer), 50 steps, 496 pairs"),
-            "paper_s2": dict(measure_workload(mhc, torch, S.paper_s1s2(10, 6), dev, 50, flush, peak),
-                             workload="paper Table I S2 shape: EGO 2058 x 10 CO 42, 100 steps of 20 ms, EGO-only"),
-            "outline11": dict(measure_workload(mhc, torch, S.with_outlines(S.intersection11(2), cut=0.35), dev, 50,
-                                               flush, peak),
-                              workload="the benchmark scene with every car drawn as a convex octagon (corners cut "
-                                       "0.35 m); roofline fraction counts each narrow test at the rectangle cost, "
-                                       "so it is a lower bound"),
-            "paths11": dict(measure_workload(mhc, torch, S.with_lane_paths(S.intersection11(2, n_acc=63)), dev, 50,
-                                             flush, peak),
-                            workload="the benchmark scene with every car following 7 lane paths under the lateral "
-                                     "controller (63 accelerations x 7 paths = 441 hypotheses per car)"),
+            "stress32": measure_workload(mhc, torch, S.stress32(4), dev, 5, flush, peak),
+            "paper_s2": measure_workload(mhc, torch, S.paper_s1s2(10, 6), dev, 50, flush, peak),
+            "outline11": measure_workload(mhc, torch, S.with_outlines(S.intersection11(2), cut=0.35), dev, 50,
+                                          flush, peak),
+            "paths11": measure_workload(mhc, torch, S.with_lane_paths(S.intersection11(2, n_acc=63)), dev, 50,
+                                        flush, peak),
         }
-        line["batch"] = measure_batch(mhc, torch, dev, 10, flush)
-        line["serving"] = measure_serving(mhc, torch, dev, args.serve_seconds)
+        line["batch"] = measure_batch(mhc, torch, dev, 10, flush, peak)
+        line["serving"] = measure_serving(mhc, torch, dev, args.serve_seconds, rates=args.serve_rates)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORKLOAD == "intersection11":
-        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+        base, oracle_out = cpu_baseline(sc, args.cpu_seconds)
         # the oracle on every host core as well (the whole table of the scene), and on a sample of the
         # 32-vehicle stress scene
         line["cpu_oracle_cores"] = {"intersection11": cpu_oracle_cores(sc, 1 << 40),
                                     "stress32": cpu_oracle_cores(__import__("paper_2005_06773_gb300.scenarios",
                                                                             fromlist=["x"]).stress32(4), 2_000_000)}
+        # the benchmarked step's own outputs (the last timed step's table and risk) against the oracle's
+        line["parity"] = parity_vs_oracle(sc, table, risk, oracle_out)
+        line["cpu_baseline"] = base
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(compact(line)), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def compact(v, top=True):
+    """The JSON line with nested figures at 4 significant digits (the contract's top-level numbers stay
+    exact), so that the whole line stays short."""
+    if isinstance(v, dict):
+        return {k: (x if top and k in ("value", "ms_per_step") else compact(x, False)) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [compact(x, False) for x in v]
+    if isinstance(v, float) and math.isfinite(v) and not top:
+        return float(f"{v:.4g}")
+    return v
+
+
+def parity_vs_oracle(sc, table, risk, oracle_out):
+    """The benchmarked step's table and risk outputs against the oracle's on the same scene: entries that
+    differ, how many of them are borderline (excused: the oracle's margin within 1 mm of zero at every
+    disagreeing step), the pose tests inside the +-1 mm band, and the largest relative difference of the
+    risk probabilities (the oracle's risk taken from the GPU's own table)."""
+    import numpy as np
+    from oracle import oracle, parity
+    t = table.cpu().numpy()
+    poses, tab_o, pairs, poff = (oracle_out[k] for k in ("poses", "table", "pairs", "pair_off"))
+    agree = parity.table_agreement(sc, t, tab_o, poses, pairs, poff)
+    r_o = oracle.risk(sc, t, pairs)
+    g = {k: v.cpu().numpy() for k, v in risk.items()}
+    ints_equal = all(np.array_equal(g[k], r_o[k]) for k in ("count", "count_k", "hits"))
+    rel = 0.0
+    for k in ("P", "H", "naive", "cond", "indep", "attr_obj", "attr_step"):
+        d = np.abs(g[k] - r_o[k]) / np.maximum(np.abs(r_o[k]), 1e-300)
+        rel = max(rel, float(d[np.abs(r_o[k]) > 1e-15].max(initial=0.0)))
+    return {"tables_equal": agree["n_disagree"] == 0, "n_disagree": agree["n_disagree"],
+            "n_excused": agree["n_excused"], "n_bad": agree["n_bad"],
+            "excused_per_test": agree["n_excused"] / sc.n_tests(),
+            "band_tests_1mm": parity.band_count(sc, poses), "risk_ints_equal": ints_equal,
+            "risk_max_rel_err": rel}
 
 
 def main():

@@ -195,8 +195,14 @@ void mhc_destroy(mhc_ctx *ctx);
  *                 6: every active (quarter tile, step) an item, all tested in parallel by persistent warps (a
  *                    pair's first step by atomicMin in scratch, the table and the risk terms written after);
  *                    for small scenes (at most 2^22 items and 2^26 table entries; larger ones use 5);
+ *                 7: one 128-thread CTA per 32 x 32 quarter tile, its active steps spread over the four
+ *                    warps (each in ascending order), first hits kept in shared memory and a candidate of a
+ *                    pair that already hit at an earlier step dropped before its exact test; the CTA stores
+ *                    the first hits and their risk terms (the table's -1s are written beforehand);
+ *                 8: as 7 for the quarter tiles with an active step only, listed first by one warp per
+ *                    quarter tile (records in scratch; up to 2^19 quarter tiles, larger scenarios use 7);
  *                 0 (default): the one mhc_autotune chose for the scenario's size class, else 4 for at
- *                 least 32 tiles per SM, and below that 6 where it applies, else 5. */
+ *                 least 32 tiles per SM, and 7 below that. */
 #define MHC_OPT_COLLIDE_VARIANT 3
 /*   MHC_OPT_GEN_SCAN  trajectory generation: 1 one warp per hypothesis, its sub-steps in parallel (warp
  *                 scans of the state maps and of the heading / position increments); 0 one thread per
@@ -219,10 +225,14 @@ void mhc_destroy(mhc_ctx *ctx);
 #define MHC_OPT_SCORE 5
 int mhc_set_option(mhc_ctx *ctx, int option, long long value);
 
-/* Work counters of the collision kernel since the last reset, summed over calls on this context:
-   out[0] = pose-pair broad-phase tests executed (after culling, 64 x 64 per tile step), out[1] = exact
-   narrow-phase tests.  Synchronises `stream`; reset != 0 zeroes them afterwards. */
-int mhc_collision_counters(mhc_ctx *ctx, uint64_t out[2], int reset, void *stream);
+/* Work counters of the collision kernel since the last reset, summed over calls on this context (host
+   array out, n_out <= MHC_COUNTER_WORDS words written): out[0] = pose-pair broad-phase tests executed
+   (after culling, a whole block of hypothesis pairs per active step), out[1] = exact narrow-phase tests,
+   out[2 .. 6] = those narrow-phase tests by shape class: rectangle-rectangle, rectangle-disc, disc-disc,
+   outline-outline, outline-disc (a rectangle in a pair with an outline counts as an outline).  Synchronises `stream`; reset != 0 zeroes them all afterwards.
+   MHC_E_INVALID: out NULL or n_out outside 1..MHC_COUNTER_WORDS. */
+#define MHC_COUNTER_WORDS 7
+int mhc_collision_counters(mhc_ctx *ctx, uint64_t *out, int32_t n_out, int reset, void *stream);
 
 /* Kernel timing (mhc_set_option(ctx, MHC_OPT_PROFILE, 1)): the library records a CUDA event pair on the
    launching stream around every kernel it launches.  mhc_profile_read synchronises those events and
@@ -464,14 +474,17 @@ void mhc_pool_destroy(mhc_pool *pool);
  * allocation can block, synchronise the device or fail at a deadline, and plugins whose host framework
  * owns all device memory.  It takes no context and calls no cudaMalloc, cudaFree, cudaHostAlloc or host
  * heap allocation.  Its scratch (scenario descriptors and per-tile bounding boxes) is one static device
- * array of 8 MiB, created when the library is loaded and held by every GPU that loads it until the process
- * exits.  Limits: at most 64 objects and 524,288 hypotheses, and descriptors + n_steps x
+ * array of 8 MiB that every GPU which loads the library holds until the process exits.  With CUDA's lazy
+ * module loading the array (and the kernels) are loaded into a device's context on first use, so the first
+ * call on each device is a warm-up that reserves those 8 MiB: make it at start-up; later calls allocate
+ * nothing.  Limits: at most 64 objects and 524,288 hypotheses, and descriptors + n_steps x
  * ceil(h_a / 32) summed over objects x 16 bytes must fit in the 8 MiB; larger scenarios return
  * MHC_E_INVALID with the needed size in mhc_last_error().  The device is the calling thread's current one;
- * the first call on each device looks up the array's device address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  Every call shares the one array (nothing in it needs to start at
- * zero; each call rewrites what it reads): calls whose work overlaps on the GPU -- different streams
- * without ordering, or several host threads -- race, and one host thread at a time may call it.
+ * every call looks up the array's device address there (cudaGetSymbolAddress, a host query).  A stream
+ * in capture is refused with MHC_E_INVALID (the descriptors are staged in a static host array that later
+ * calls rewrite).  Every call shares the one array (nothing in it needs to start at zero; each call
+ * rewrites what it reads): calls whose work overlaps on the GPU -- different streams without ordering, or
+ * several host threads -- race, and one host thread at a time may call it.
  * poses / table / stream as for mhc_detect_collisions.
  */
 int mhc_detect_collisions_static(const mhc_scenario *scen, const mhc_poses *poses, int16_t *table, void *stream);

@@ -381,6 +381,10 @@ bool items_eligible(const Layout &L) {
            L.n_entries <= kItemsMaxEntries;
 }
 
+// The block-list layout (collision variant 8) applies while its records (128 bytes per 32 x 32 block) stay
+// small; they live in the call's scratch.
+bool blocklist_eligible(const Layout &L) { return 4 * L.n_tiles <= kBlockListMax; }
+
 // Device scratch each call needs (besides caller buffers).
 // 64-bit accumulator words of one assessment
 long long acc_words(const Layout &L) {
@@ -398,7 +402,8 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
              align_up(sizeof(Regime) * L.regimes.size()) + align_up(sizeof(PolyVertex) * L.polys.size()) +
              align_up(sizeof(float) * L.paths.size());
     s.bounds = align_up(sizeof(float4) * (size_t)L.n_bounds);
-    s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj);
+    s.prob = align_up(sizeof(double) * (size_t)L.n_traj) + align_up(sizeof(float) * (size_t)L.n_traj) +
+             2 * align_up(sizeof(unsigned long long) * (size_t)L.n_traj);
     s.weights = with_weights ? align_up(sizeof(float) * (size_t)L.n_traj) : 0;
     s.acc_words = acc_words(L);
     s.acc = align_up(8 * (size_t)s.acc_words);
@@ -406,6 +411,8 @@ Scratch scratch_of(const Layout &L, bool with_weights) {
                                       align_up(4 * (size_t)L.n_entries) + align_up(16 * (size_t)L.n_tiles) +
                                       align_up(4 * sizeof(ItemBlock) * (size_t)L.n_tiles)
                                 : 0;
+    if (blocklist_eligible(L))   // variant 6 or 8 takes the space, never both in one call
+        s.items = std::max(s.items, kAlign + align_up(4 * sizeof(ActiveBlock) * (size_t)L.n_tiles));
     s.total = s.desc + s.weights + s.bounds + s.prob + s.acc + s.items;
     return s;
 }
@@ -548,10 +555,12 @@ int make_risk_args(const Layout &L, const DevDesc &D, Bump &bump, const int16_t 
     r.weights = D.weights;
     r.prob = static_cast<double *>(bump.take(sizeof(double) * (size_t)L.n_traj));
     r.probf = static_cast<float *>(bump.take(sizeof(float) * (size_t)L.n_traj));
+    r.pfix = static_cast<unsigned long long *>(bump.take(sizeof(unsigned long long) * (size_t)L.n_traj));
+    r.lfix = static_cast<unsigned long long *>(bump.take(sizeof(unsigned long long) * (size_t)L.n_traj));
     const long long np = (long long)L.pairs.size();
     const long long words = acc_words(L);
     unsigned long long *w = static_cast<unsigned long long *>(bump.take(8 * (size_t)words));
-    if (!r.prob || !r.probf || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
+    if (!r.prob || !r.probf || !r.pfix || !r.lfix || !w) return fail(MHC_E_NOMEM, "arena too small for risk scratch");
     RiskScratch &A = r.acc;
     A.base = w; A.n_words = words;
     A.count = w; w += np;
@@ -586,7 +595,7 @@ int log2_floor(long long v) {
 // time is the closest pairs' long step chains: every active step in parallel where the item list fits,
 // else a warp per quarter tile.
 int default_variant(const mhc_ctx *ctx, const Layout &L) {
-    return L.n_tiles >= 32LL * ctx->n_sm ? 4 : (items_eligible(L) ? 6 : 5);
+    return L.n_tiles >= 32LL * ctx->n_sm ? 4 : 7;
 }
 
 void pick_collide_config(const mhc_ctx *ctx, const Layout &L, bool fused, int &variant, int &cull) {
@@ -682,11 +691,13 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         int variant = 1, cull = 1;
         pick_collide_config(ctx, L, fused, variant, cull);
         if (variant == 6 && !items_eligible(L)) variant = 5;
+        if (variant == 8 && !blocklist_eligible(L)) variant = 7;
         float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_bounds));
         if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
         // small tables: the quarter-tile layout writes the -1s of its own blocks (one launch less); large ones
         // are filled by the HBM-rate fill kernel (in-kernel 2-byte row stores cost issue slots there)
         const bool fill_in_collide = (variant == 5 && L.n_entries <= kFillInCollideMax) || variant == 6;
+        const bool fill_in_bounds = (variant == 7 || variant == 8) && cull && (long long)L.warp_obj.size() * L.max_steps > 0;
         CollideArgs c{};
         if (variant == 6) {   // the item list and its two counters (zeroed by the bounds kernel, else a memset)
             c.max_items = 4 * L.n_tiles * (long long)L.max_steps;
@@ -699,39 +710,49 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
             if (!c.items || !c.item_count || !c.first32 || !c.active || !c.blocks)
                 return fail(MHC_E_NOMEM, "arena too small for the step items");
         }
+        if (variant == 8) {   // the block records and their count (zeroed by the bounds kernel, else a memset)
+            c.item_count = static_cast<unsigned long long *>(bump.take(kAlign));
+            c.active_count = c.item_count + 1;
+            c.recs = static_cast<ActiveBlock *>(bump.take(sizeof(ActiveBlock) * (size_t)(4 * L.n_tiles)));
+            if (!c.item_count || !c.recs) return fail(MHC_E_NOMEM, "arena too small for the block records");
+        }
         bool counts_zeroed = false;
         {
-            TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_in_collide ? 0 : 1));
-            cudaError_t e = fill_in_collide ? cudaSuccess : launch_fill_table(table, L.n_entries, st, pdl());
+            const bool fill_alone = !fill_in_collide && !fill_in_bounds;
+            TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_alone ? 1 : 0));
+            cudaError_t e = fill_alone ? launch_fill_table(table, L.n_entries, st, pdl()) : cudaSuccess;
             if (e != cudaSuccess) return cuda_fail(e, "table fill launch");
-            if (!fill_in_collide && L.n_entries > 0) after_kernel = true;
+            if (fill_alone && L.n_entries > 0) after_kernel = true;
             if (cull) {
                 BoundsArgs b{};
                 b.objs = D.objs; b.warp_obj = D.warp_obj; b.warp_first = D.warp_first;
                 b.n_warps = (int)L.warp_obj.size(); b.max_steps = L.max_steps; b.x = coll_in->x; b.y = coll_in->y;
                 b.bounds = bounds;
                 const bool launches = (long long)b.n_warps * b.max_steps > 0;
-                if (variant == 6 && launches) b.zero_counts = c.item_count;
+                if ((variant == 6 || variant == 8) && launches) b.zero_counts = c.item_count;
+                if (fill_in_bounds) { b.fill = table; b.n_fill = L.n_entries; }
                 e = launch_bounds(b, st, pdl());
                 if (e != cudaSuccess) return cuda_fail(e, "bounds kernel launch");
                 if (launches) after_kernel = true;
                 counts_zeroed = b.zero_counts != nullptr;
             }
         }
-        c.objs = D.objs; c.pairs = D.pairs_c; c.n_pairs = (int)L.pairs.size(); c.n_tiles = L.n_tiles;
+        c.objs = D.objs; c.pairs = D.pairs_c; c.n_pairs = (int)L.pairs.size(); c.n_obj = L.n_obj; c.n_tiles = L.n_tiles;
         c.max_steps = L.max_steps; c.cull = cull; c.variant = variant; c.fill_blocks = fill_in_collide;
         c.max_ctas = ctx->collide_max_ctas;
         c.x = coll_in->x; c.y = coll_in->y; c.c = coll_in->c; c.s = coll_in->s;
         c.bounds = bounds; c.polys = D.polys; c.table = table; c.counters = ctx->counters;
         if (fused) {
             c.probf = r.probf;
+            c.pfix = r.pfix;
+            c.lfix = r.lfix;
             c.acc = r.acc;
         }
-        if (variant == 6 && !counts_zeroed) {
+        if ((variant == 6 || variant == 8) && !counts_zeroed) {
             MHC_CUDA(cudaMemsetAsync(c.item_count, 0, 2 * sizeof(unsigned long long), st));
             after_kernel = false;
         }
-        TimedScope ts(ctx, st, MHC_K_COLLIDE, variant == 6 ? 3 : 1);
+        TimedScope ts(ctx, st, MHC_K_COLLIDE, variant == 6 ? 3 : (variant == 8 ? 2 : 1));
         cudaError_t e = launch_collide(c, st, pdl());
         if (e != cudaSuccess) return cuda_fail(e, "collision kernel launch");
         if (L.n_tiles > 0) after_kernel = true;
@@ -830,7 +851,7 @@ int mhc_set_option(mhc_ctx *ctx, int option, long long value) {
         return MHC_OK;
     }
     if (option == MHC_OPT_COLLIDE_VARIANT) {
-        if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 6");
+        if (value < 0 || value > kCollideVariants) return fail(MHC_E_INVALID, "collide variant must be 0 to 8");
         ctx->variant = (int)value;
         return MHC_OK;
     }
@@ -865,15 +886,16 @@ int mhc_transfer_bytes(mhc_ctx *ctx, int64_t *h2d, int64_t *d2h) {
     return MHC_OK;
 }
 
-int mhc_collision_counters(mhc_ctx *ctx, uint64_t out[2], int reset, void *stream) {
+int mhc_collision_counters(mhc_ctx *ctx, uint64_t *out, int32_t n_out, int reset, void *stream) {
     if (int r = check_ctx(ctx)) return r;
     if (!out) return fail(MHC_E_INVALID, "out is NULL");
+    if (n_out < 1 || n_out > MHC_COUNTER_WORDS) return fail(MHC_E_INVALID, "n_out must be 1 to MHC_COUNTER_WORDS");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MHC_CUDA(cudaSetDevice(ctx->device));
-    MHC_CUDA(cudaMemcpyAsync(out, ctx->counters, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    MHC_CUDA(cudaMemcpyAsync(out, ctx->counters, n_out * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     MHC_CUDA(cudaStreamSynchronize(st));
     if (reset) {
-        MHC_CUDA(cudaMemsetAsync(ctx->counters, 0, 2 * sizeof(uint64_t), st));
+        MHC_CUDA(cudaMemsetAsync(ctx->counters, 0, MHC_COUNTER_WORDS * sizeof(uint64_t), st));
         MHC_CUDA(cudaStreamSynchronize(st));
     }
     return MHC_OK;

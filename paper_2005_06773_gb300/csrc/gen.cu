@@ -8,6 +8,8 @@
 // compensated (hi, lo) sums so that 250+ sub-steps add no more than ~1e-6 m of rounding.
 // Pedestrians: Eq. (pedestrianmotion) with a constant acceleration integrates exactly, so every output
 // pose is evaluated in closed form (speed saturating at 0 or at the cap).
+#include <algorithm>
+
 #include "mhc_internal.cuh"
 #include "prepare.cuh"
 
@@ -580,10 +582,30 @@ __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
 // Bounding box of the 32 pose centres of each bound tile at each step: one warp per (32-hypothesis group,
 // step), a warp min/max reduction.  The descriptors are read before the wait for the generation kernel,
 // the poses after it.
+// With `fill` set, the CTAs past the bounds write the table's -1s (16-byte stores on the aligned body) before
+// the wait: nothing earlier in the launch sequence reads the table, so the HBM-rate fill overlaps the
+// generation kernel's tail, and the collision kernel stores first hits only.
+constexpr int kFillCtas = 152 * 4;
+
 __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
     pdl_trigger();
-    const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long total = (long long)a.n_warps * a.max_steps;
+    const long long bound_ctas = (total + 7) / 8;
+    if ((long long)blockIdx.x >= bound_ctas) {   // a fill CTA
+        const long long n = a.n_fill;
+        const long long tid = ((long long)blockIdx.x - bound_ctas) * blockDim.x + threadIdx.x;
+        const long long stride = (long long)(gridDim.x - bound_ctas) * blockDim.x;
+        const long long head = min(n, (long long)((16 - ((uintptr_t)a.fill & 15)) & 15) / 2);
+        if (tid < head) a.fill[tid] = (int16_t)-1;
+        const long long body = (n - head) / 8;
+        int4 *v = reinterpret_cast<int4 *>(a.fill + head);
+        const int4 ones = make_int4(-1, -1, -1, -1);
+        for (long long q = tid; q < body; q += stride) v[q] = ones;
+        for (long long q = head + body * 8 + tid; q < n; q += stride) a.fill[q] = (int16_t)-1;
+        pdl_wait();
+        return;
+    }
+    const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     bool live = g < total;
     int k = 0, first = 0, h = 0, n_steps = 0;
@@ -644,7 +666,9 @@ cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
 cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st, bool pdl) {
     const long long total = (long long)a.n_warps * a.max_steps;
     if (total <= 0) return cudaSuccess;
-    const long long blocks = (total + 7) / 8;
+    long long blocks = (total + 7) / 8;
+    if (a.fill && a.n_fill > 0) blocks += std::min((long long)kFillCtas, (a.n_fill / 8 + 255) / 256 + 1);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     return launch_kernel(bounds_kernel, dim3((unsigned)blocks), dim3(256), 0, st, pdl, a);
 }
 

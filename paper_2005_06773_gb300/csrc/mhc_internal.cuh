@@ -21,7 +21,7 @@ constexpr float kVMin = 2.0f;      // below this speed the one-track model gives
 constexpr double kVMinD = 2.0;
 
 constexpr int kTile = 64;           // collision tile edge (hypotheses per side)
-constexpr int kCollideVariants = 6; // thread layouts of the collision kernel (MHC_OPT_COLLIDE_VARIANT 1..6)
+constexpr int kCollideVariants = 8; // thread layouts of the collision kernel (MHC_OPT_COLLIDE_VARIANT 1..8)
 constexpr int kBoundTile = 32;     // hypotheses per bounding-box tile (one warp)
 constexpr int16_t kNoHit = 0x7fff; // in-kernel sentinel, stored as -1
 
@@ -111,6 +111,8 @@ struct PrepArgs {
     const float *weights;          // [n_traj] raw weights, or null for uniform (or scored)
     double *prob;                  // [n_traj] normalised probabilities
     float *probf;                  // [n_traj] the same rounded to FP32
+    unsigned long long *pfix;      // [n_traj] or null: to_fixed(probf, kFixProb)
+    unsigned long long *lfix;      // [n_traj] or null: to_fixed(neg_log_survival(probf), kFixLog)
     int score;                     // no weights: 1 scores every hypothesis by Eq. normTraj, 0 uniform
     const float *grids;            // the hypothesis grids and paths the scores read
     const float *paths;
@@ -141,6 +143,8 @@ struct BoundsArgs {
     const float *x, *y;
     float4 *bounds;
     unsigned long long *zero_counts;   // if set: two words zeroed after the wait (the step-item counters)
+    int16_t *fill;            // if set: further CTAs of the launch write table[0, n_fill) = -1 (no collision)
+    long long n_fill;
 };
 
 // Risk accumulators: one contiguous block of 64-bit words, zeroed before every assessment.  Masses and
@@ -209,6 +213,19 @@ struct __align__(16) ItemBlock {
     int i0, j0;               // the block's first row and column within its pair
 };
 
+// A 32 x 32 block with at least one active step, recorded by the listing kernel of the block-list layout
+// (variant 8) with everything its block kernel needs but the pair's risk fields: table entry (i, j) of the
+// block at entry0 + i h_b + j, pose (k, i) of its row object at pose_a + k h_a + i (columns alike), its two
+// bound tiles' boxes of step k at bounds_a + k and bounds_b + k, the shapes, and the first 32-step chunk
+// with an active step (steps k0 .. k0 + 31, active ones in `mask`).
+struct __align__(16) ActiveBlock {
+    long long entry0, pose_a, pose_b, bounds_a, bounds_b, traj_a, traj_b;
+    int h_a, h_b, n_steps, pair, rows, cols, i0, j0;
+    float rcull, rc2, la, wa, ra, lb, wb, rb;
+    int k0;
+    unsigned mask;
+};
+
 // One item of the step-item layout: an active step k of block gw, with the pose indices of the step's first
 // row of A and first column of B (pa = pose_a + k h_a, pb = pose_b + k h_b), so that its poses are one
 // load away from the item.
@@ -221,6 +238,7 @@ struct CollideArgs {
     const ObjDesc *objs;
     const PairDesc *pairs;    // in collision-grid order (tile_start over that order; index = table order)
     int n_pairs;
+    int n_obj;                // objects (the descriptors at objs)
     long long n_tiles;        // total collision tiles over all pairs
     int max_steps;            // the longest horizon of the batch (sizes the per-CTA accumulators)
     int cull;                 // 1: skip steps whose tile bounding boxes cannot meet
@@ -233,16 +251,20 @@ struct CollideArgs {
     int *active;              // [4 n_tiles] blocks with at least one active step, and their number (zeroed)
     ItemBlock *blocks;        // [4 n_tiles] the records of the active blocks (indexed by block)
     unsigned long long *active_count;
+    ActiveBlock *recs;        // variant 8: [4 n_tiles] the records of the active blocks ([*active_count] valid)
     long long max_items;      // capacity: 4 n_tiles x max_steps
     int variant;              // 1: 256 threads x 4 x 4, 2: 64 threads x 8 x 8, 3: warp per step, 4: warp per tile,
-                              // 5: warp per quarter tile, 6: step items
+                              // 5: warp per quarter tile, 6: step items, 7: CTA per quarter tile,
+                              // 8: CTA per listed active quarter tile
     const float *x, *y, *c, *s;
     const float4 *bounds;
     const PolyVertex *polys;       // convex outlines (pairs of combo 4..6), or null when there are none
     int16_t *table;
-    unsigned long long *counters;  // optional: [0] broad-phase tests executed, [1] narrow-phase tests
+    unsigned long long *counters;  // optional: [0] broad-phase tests executed, [1] narrow-phase tests,
+                                   // [2 .. 6] narrow-phase tests by shape class (collide.cu narrow_class)
     // fused risk accumulation at first-hit time (probf null: table only)
     const float *probf;            // [n_traj] FP32 probabilities
+    const unsigned long long *pfix, *lfix;   // [n_traj] the same and -log(1 - p) in fixed point
     RiskScratch acc;               // accumulators, zeroed beforehand
 };
 
@@ -262,6 +284,8 @@ struct RiskArgs {
     const float *grids, *paths;
     double *prob;                  // [n_traj] normalised probabilities (scratch)
     float *probf;                  // [n_traj] the same rounded to FP32 (the per-hit arithmetic)
+    unsigned long long *pfix;      // [n_traj] each probability in fixed point (kFixProb)
+    unsigned long long *lfix;      // [n_traj] each -log(1 - p) in fixed point (kFixLog)
     RiskScratch acc;
     // outputs (device); any may be null
     long long *count, *count_k;

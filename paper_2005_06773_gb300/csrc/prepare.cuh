@@ -1,5 +1,6 @@
 // prepare.cuh -- the first step of a risk assessment (Section IV-D.1): zero the accumulators, fill the
-// escape lists with -1 and L1-normalise each object's weights into probabilities.  risk.cu launches it on
+// escape lists with -1, L1-normalise each object's weights into probabilities and convert each hypothesis's
+// probability p and -log(1 - p) to the fixed point of the risk sums once.  risk.cu launches it on
 // its own; on the fused path (generation, then collisions with the risk terms added at each first hit) it
 // runs as extra CTAs of the generation launch, since the two are independent.
 #pragma once
@@ -18,6 +19,8 @@ inline PrepArgs prep_of(const RiskArgs &r) {
     p.weights = r.weights;
     p.prob = r.prob;
     p.probf = r.probf;
+    p.pfix = r.pfix;
+    p.lfix = r.lfix;
     p.score = r.score;
     p.grids = r.grids;
     p.paths = r.paths;
@@ -89,6 +92,10 @@ __device__ __forceinline__ void prepare_block(const PrepArgs &a, int b, int nb) 
         const double p = (a.weights ? (double)a.weights[o.traj_off + i] : (a.score ? a.prob[o.traj_off + i] : 1.0)) / sum;
         a.prob[o.traj_off + i] = p;
         a.probf[o.traj_off + i] = (float)p;
+        if (a.pfix) {   // the per-hypothesis terms of every first hit, converted once
+            a.pfix[o.traj_off + i] = to_fixed((float)p, kFixProb);
+            a.lfix[o.traj_off + i] = to_fixed(neg_log_survival((float)p), kFixLog);
+        }
     }
 }
 

@@ -26,6 +26,7 @@ constexpr int kSlots = 4;
 constexpr long long kFillInCollideMax = 1LL << 25;   // table entries up to which the collision kernel fills
 constexpr long long kItemsMax = 1LL << 22;             // step items (8 B each) up to which variant 6 applies
 constexpr long long kItemsMaxEntries = 1LL << 26;      // and table entries (4 B of first-step scratch each)
+constexpr long long kBlockListMax = 1LL << 19;         // 32 x 32 blocks (128 B records) up to which variant 8 applies
 constexpr long long kGenScanMaxTraj = 4096;           // a scenario's hypotheses up to which generation is parallel in time
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }

@@ -10,12 +10,18 @@
 //
 // In host code `g_scratch` is only a host-side stand-in for the device array, never a device address:
 // handing it to a kernel would fault or, where the GPU can reach host memory, silently use the wrong
-// memory.  The device address is therefore looked up once per device with cudaGetSymbolAddress (with that
-// device current) on the first call made on the device, and that address is what the kernels receive.
+// memory.  Every call therefore looks the device address up with cudaGetSymbolAddress (with the calling
+// thread's current device) and hands that address to the kernels; the lookup is a host query, so a
+// context torn down and created again (the array may then sit elsewhere) is picked up by the next call.
+// With CUDA's lazy module loading the library's device code, this array included, is loaded into a
+// device's context on first use: the first call on each device is the warm-up that loads it (and so
+// reserves the 8 MiB), and belongs at start-up.
+//
+// The descriptors are staged in a static host array that every call rewrites, so a call recorded into a
+// CUDA graph would upload whatever a later call left there: a stream in capture is refused.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/mhc.h"
 #include "mhc_internal.cuh"
@@ -33,7 +39,6 @@ constexpr int kMaxObjects = 64;
 constexpr int kMaxPairs = kMaxObjects * (kMaxObjects - 1) / 2;
 constexpr int kMaxWarps = 16384;                    // 32-hypothesis bound tiles (524,288 hypotheses)
 constexpr size_t kAlign = 256;
-constexpr int kMaxDevices = 128;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
@@ -44,9 +49,6 @@ constexpr size_t kDescBytes = kObjBytes + kPairBytes + 2 * kWarpBytes;
 
 // Host staging of the descriptor blob: static storage, reused by every call (one host thread at a time).
 alignas(256) unsigned char h_blob[kDescBytes];
-
-std::mutex g_setup_mutex;
-void *g_dev_scratch[kMaxDevices] = {};
 
 int fail(int code, const char *why) {
     set_last_error(why);
@@ -59,20 +61,12 @@ int cuda_fail(cudaError_t e, const char *what) {
     return fail(MHC_E_CUDA, msg);
 }
 
-// Device address of g_scratch on the current device (looked up on the first call on each device).
+// Device address of g_scratch in the calling thread's current context (looked up on every call).
 int scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(MHC_E_INVALID, "device index beyond the static-scratch table");
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_dev_scratch[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
-        g_dev_scratch[dev] = p;
-    }
-    *out = g_dev_scratch[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
+    *out = p;
     return MHC_OK;
 }
 
@@ -172,17 +166,21 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
         return fail(MHC_E_INVALID, msg);
     }
 
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &capturing);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (capturing != cudaStreamCaptureStatusNone)
+        return fail(MHC_E_INVALID, "the allocation-free entry point does not run on a stream in capture");
     void *base = nullptr;
     if (int r = scratch_address(&base)) return r;
     unsigned char *dev = static_cast<unsigned char *>(base);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // Only the used part of each descriptor region is copied.  The source is pageable, so each copy has
     // read h_blob by the time cudaMemcpyAsync returns.
     const size_t parts[4][2] = {{0, sizeof(ObjDesc) * sc->n_objects},
                                 {kObjBytes, sizeof(PairDesc) * n_pairs},
                                 {kObjBytes + kPairBytes, sizeof(int) * tiles32},
                                 {kObjBytes + kPairBytes + kWarpBytes, sizeof(int) * tiles32}};
-    cudaError_t e = cudaSuccess;
     for (const auto &part : parts) {
         if (!part[1]) continue;
         e = cudaMemcpyAsync(dev + part[0], h_blob + part[0], part[1], cudaMemcpyHostToDevice, st);
@@ -209,6 +207,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
     c.objs = d_objs;
     c.pairs = d_pairs;
     c.n_pairs = n_pairs;
+    c.n_obj = sc->n_objects;
     c.n_tiles = tiles;
     c.max_steps = N;
     c.cull = 1;

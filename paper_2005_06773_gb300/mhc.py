@@ -22,6 +22,7 @@ MHC_OPT_PROFILE = 2
 MHC_OPT_COLLIDE_VARIANT = 3
 MHC_OPT_GEN_SCAN = 4
 MHC_OPT_SCORE = 5
+COUNTER_WORDS = 7
 KERNEL_CLASSES = ("generate", "bounds", "collide", "risk")
 
 
@@ -97,7 +98,7 @@ def _load():
     L.mhc_destroy.argtypes = [c_void_p]
     L.mhc_destroy.restype = None
     L.mhc_set_option.argtypes = [c_void_p, c_int, c_longlong]
-    L.mhc_collision_counters.argtypes = [c_void_p, POINTER(c_uint64), c_int, c_void_p]
+    L.mhc_collision_counters.argtypes = [c_void_p, POINTER(c_uint64), c_int32, c_int, c_void_p]
     L.mhc_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]
     L.mhc_transfer_bytes.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int64)]
     L.mhc_layout.argtypes = [POINTER(MhcScenario), POINTER(c_int64), POINTER(c_int32), POINTER(c_int64),
@@ -272,9 +273,19 @@ class Context:
         _check(lib.mhc_set_option(self.h, option, value), "mhc_set_option")
 
     def counters(self, reset: bool = False, stream=None):
-        out = (c_uint64 * 2)()
-        _check(lib.mhc_collision_counters(self.h, out, int(reset), _stream(stream)), "mhc_collision_counters")
-        return int(out[0]), int(out[1])
+        """(broad-phase tests executed, narrow-phase tests) since the last reset."""
+        w = self.work(reset, stream)
+        return w["executed"], w["narrow"]
+
+    def work(self, reset: bool = False, stream=None) -> Dict[str, int]:
+        """All collision work counters: executed broad-phase tests, narrow-phase tests and those by shape
+        class (rect_rect, rect_disc, disc_disc, outline_outline, outline_disc)."""
+        out = (c_uint64 * COUNTER_WORDS)()
+        _check(lib.mhc_collision_counters(self.h, out, COUNTER_WORDS, int(reset), _stream(stream)),
+               "mhc_collision_counters")
+        return dict(zip(("executed", "narrow", "rect_rect", "rect_disc", "disc_disc", "outline_outline",
+                         "outline_disc"),
+                        (int(v) for v in out)))
 
 
     def profile(self, enable: bool = True):

@@ -244,7 +244,7 @@ def test_collision_variants_agree(mhc, ctx, name):
     p = mhc.generate(ctx, sc)
     ref_t, ref_r = None, None
     try:
-        for variant in (1, 2, 3, 4, 5, 6):
+        for variant in (1, 2, 3, 4, 5, 6, 7, 8):
             for cull in (1, 0):
                 ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, variant)
                 ctx.set_option(mhc.MHC_OPT_CULL, cull)
@@ -272,7 +272,7 @@ def test_autotune_picks_a_layout_and_keeps_results(mhc):
         p = mhc.generate(c, sc)
         before = mhc.detect(c, sc, p).clone()
         v, cull = mhc.autotune(c, sc, p)
-        assert v in (1, 2, 3, 4, 5, 6) and cull in (0, 1)
+        assert v in (1, 2, 3, 4, 5, 6, 7, 8) and cull in (0, 1)
         after = mhc.detect(c, sc, p)
         torch.cuda.synchronize()
         assert torch.equal(before, after)
@@ -288,7 +288,7 @@ def test_profiled_and_overlapped_launches_agree(mhc, ctx, name):
     sc = scene(name)
     w = S.random_weights(sc, 17)
     try:
-        for variant in (0, 4, 5, 6):
+        for variant in (0, 4, 5, 6, 7, 8):
             ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, variant)
             ctx.profile(False)
             p1, t1, r1 = mhc.evaluate(ctx, sc, weights=w)
@@ -433,14 +433,23 @@ def test_stress32_sampled(mhc, orc):
         torch.cuda.empty_cache()
 
 
-def test_counters_and_culling_work(mhc, ctx):
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8])
+def test_counters_and_culling_work(mhc, ctx, variant):
+    """Culling leaves fewer executed tests than nominal ones, and the narrow-phase tests by shape class add
+    up to their total (rectangle-rectangle, rectangle-disc and disc-disc pairs all occur in the scene)."""
     sc = S.intersection11(2)
     p = mhc.generate(ctx, sc)
     ctx.counters(reset=True)
-    mhc.detect(ctx, sc, p)
-    executed, narrow = ctx.counters(reset=True)
+    try:
+        ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, variant)
+        mhc.detect(ctx, sc, p)
+    finally:
+        ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, 0)
+    w = ctx.work(reset=True)
     nominal = sc.n_tests()
-    assert 0 < narrow < executed < nominal
+    assert 0 < w["narrow"] < w["executed"] < nominal
+    assert w["rect_rect"] + w["rect_disc"] + w["disc_disc"] + w["outline_outline"] + w["outline_disc"] == w["narrow"]
+    assert w["rect_rect"] > 0 and w["rect_disc"] > 0 and w["outline_outline"] == 0 and w["outline_disc"] == 0
 
 
 def test_errors_leave_context_usable(mhc, ctx):
@@ -454,3 +463,71 @@ def test_errors_leave_context_usable(mhc, ctx):
                    weights=[np.zeros(16), np.ones(16)])
     p = mhc.generate(ctx, sc)
     assert torch.isfinite(p["x"]).all()
+
+
+def _risk_np(r):
+    return {k: (v.detach().cpu().numpy() if hasattr(v, "detach") else np.asarray(v)) for k, v in r.items()}
+
+
+def _check_risk_against_tables(orc, sc, r_gpu, tab_gpu, tab_o, pairs, n_excused):
+    """Risk outputs of the GPU's own table: equal to the oracle's risk from that table (integers exactly,
+    probabilities to 1e-6), and within the excused pairs of the oracle's risk from its own table."""
+    he = int(np.diff(orc.traj_offsets(sc))[sc.ego])
+    check_risk({k: torch.as_tensor(v) for k, v in r_gpu.items()}, orc.risk(sc, tab_gpu, pairs), he)
+    ref = orc.risk(sc, tab_o, pairs)
+    assert int(np.abs(r_gpu["count"] - ref["count"]).sum()) <= n_excused
+    if n_excused == 0:
+        check_risk({k: torch.as_tensor(v) for k, v in r_gpu.items()}, ref, he)
+
+
+def test_benchmarked_calls_full_size(mhc, orc):
+    """The benchmark's own step at full size: mhc_evaluate (generation, fused collision + risk in the
+    layout the autotuner picks, EGO walk) on device buffers, and mhc_run with host inputs and outputs, on
+    the 11-object intersection (1.70e8 pose tests).  The whole table against the oracle's (borderline
+    pairs excused and counted), every risk output against the oracle's; the number of pose tests inside
+    the +-1 mm band is counted beside it."""
+    from oracle import parity
+    sc = S.intersection11(2)
+    cs = mhc.as_c(sc)
+    lay = mhc.layout(cs)
+    ref = orc.generate(sc)
+    tab_o, poff, pairs = orc.table(sc, ref)
+    ctx = mhc.Context(0, 512 << 20)
+    try:
+        poses = mhc.alloc_poses(sc)
+        table = torch.empty(lay["n_entries"], dtype=torch.int16, device="cuda")
+        risk = mhc.alloc_risk(cs)
+        mhc.generate(ctx, cs, poses)
+        tuned = mhc.autotune(ctx, cs, poses, table)
+        results = {}
+        for variant in sorted({tuned[0], 6, 7, 8}):
+            ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, variant)
+            table.fill_(1234)
+            mhc.evaluate(ctx, cs, poses, table, out=risk)
+            torch.cuda.synchronize()
+            results[variant] = (table.cpu().numpy(), _risk_np(risk))
+        ctx.set_option(mhc.MHC_OPT_COLLIDE_VARIANT, 0)
+        g = {k: mhc.poses_by_trajectory(sc, poses[k]).astype(np.float64) for k in ("x", "y", "c", "s")}
+        assert corner_error(sc, ref, g["x"], g["y"], g["c"], g["s"]) < POSE_TOL
+        for variant, (t_host, r_host) in results.items():
+            n_dis, n_exc = check_table(orc, sc, t_host, tab_o, ref, pairs, poff, n_tests=sc.n_tests())
+            _check_risk_against_tables(orc, sc, r_host, t_host, tab_o, pairs, n_exc)
+            print(f"variant {variant}: {n_dis} entries differ from the oracle, {n_exc} excused")
+        # mhc_run: host scenario in, host risk out (its own context, as the end-to-end benchmark runs it)
+        run_ctx = mhc.Context(0, max(lay["run_bytes"] + (64 << 20), 256 << 20))
+        try:
+            host = mhc.alloc_risk(cs, device="cpu", pin=True)
+            mhc.run(run_ctx, cs, out=host)
+            r_run = _risk_np(host)
+        finally:
+            run_ctx.close()
+        t_tuned = results[tuned[0]][0]
+        _check_risk_against_tables(orc, sc, r_run, t_tuned, tab_o, pairs,
+                                   check_table(orc, sc, t_tuned, tab_o, ref, pairs, poff, n_tests=sc.n_tests())[1])
+        for k in ("count", "count_k", "hits", "escape", "n_escape"):
+            np.testing.assert_array_equal(r_run[k], results[tuned[0]][1][k], err_msg=k)
+        band = parity.band_count(sc, ref)
+        print(f"pose tests within +-1 mm of contact (oracle margins): {band} of {sc.n_tests()}")
+        assert band < 1e-4 * sc.n_tests()
+    finally:
+        ctx.close()
