@@ -662,6 +662,20 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         if (e != cudaSuccess) return cuda_fail(e, "risk prepare launch");
         after_kernel = true;
     }
+    // the collision configuration decides where the table's -1s are written: by the collision kernel itself
+    // (variants 5 on small tables, 6); for large tables by fill CTAs of the generation launch when it is
+    // part of the sequence (the HBM-bound fill beside the latency-bound integration); else by the bounds
+    // kernel (variants 7, 8 with culling: small tables, where fill CTAs would take residency from the
+    // generation warps) or a fill kernel
+    int variant = 1, cull = 1;
+    if (coll_in) {
+        pick_collide_config(ctx, L, fused, variant, cull);
+        if (variant == 6 && !items_eligible(L)) variant = 5;
+        if (variant == 8 && !blocklist_eligible(L)) variant = 7;
+    }
+    const bool fill_in_collide = (variant == 5 && L.n_entries <= kFillInCollideMax) || variant == 6;
+    const bool fill_in_gen = coll_in && gen_out && !fill_in_collide && L.n_entries > kFillInCollideMax &&
+                             !L.gen_obj.empty();
     if (gen_out) {
         GenArgs g;
         g.objs = D.objs; g.regimes = D.regimes; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
@@ -682,22 +696,20 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         }
         g.paths = D.paths;
         g.x = gen_out->x; g.y = gen_out->y; g.c = gen_out->c; g.s = gen_out->s;
+        g.fill = fill_in_gen ? table : nullptr;
+        g.n_fill = fill_in_gen ? L.n_entries : 0;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
         cudaError_t e = launch_generate(g, st);
         if (e != cudaSuccess) return cuda_fail(e, "generation kernel launch");
         after_kernel = true;
     }
     if (coll_in) {
-        int variant = 1, cull = 1;
-        pick_collide_config(ctx, L, fused, variant, cull);
-        if (variant == 6 && !items_eligible(L)) variant = 5;
-        if (variant == 8 && !blocklist_eligible(L)) variant = 7;
         float4 *bounds = static_cast<float4 *>(bump.take(sizeof(float4) * (size_t)L.n_bounds));
         if (!bounds) return fail(MHC_E_NOMEM, "arena too small for tile bounds");
         // small tables: the quarter-tile layout writes the -1s of its own blocks (one launch less); large ones
         // are filled by the HBM-rate fill kernel (in-kernel 2-byte row stores cost issue slots there)
-        const bool fill_in_collide = (variant == 5 && L.n_entries <= kFillInCollideMax) || variant == 6;
-        const bool fill_in_bounds = (variant == 7 || variant == 8) && cull && (long long)L.warp_obj.size() * L.max_steps > 0;
+        const bool fill_in_bounds = !fill_in_gen && (variant == 7 || variant == 8) && cull &&
+                                    (long long)L.warp_obj.size() * L.max_steps > 0;
         CollideArgs c{};
         if (variant == 6) {   // the item list and its two counters (zeroed by the bounds kernel, else a memset)
             c.max_items = 4 * L.n_tiles * (long long)L.max_steps;
@@ -718,7 +730,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         }
         bool counts_zeroed = false;
         {
-            const bool fill_alone = !fill_in_collide && !fill_in_bounds;
+            const bool fill_alone = !fill_in_collide && !fill_in_bounds && !fill_in_gen;
             TimedScope ts(ctx, st, MHC_K_BOUNDS, (cull ? 1 : 0) + (fill_alone ? 1 : 0));
             cudaError_t e = fill_alone ? launch_fill_table(table, L.n_entries, st, pdl()) : cudaSuccess;
             if (e != cudaSuccess) return cuda_fail(e, "table fill launch");

@@ -538,14 +538,33 @@ __device__ void vehicle_scan(const ObjDesc &o, float acc, float delta, const Reg
 // instruction fetch was its largest stall).  Bounded to 80 registers (six CTAs per SM), where the
 // integration has no spills: faster than 64 (eight per SM, all of the 11-object scene's CTAs resident)
 // on the 11-object and 32-vehicle scenes.
+// table[0, n) = -1 by CTA b of nb (16-byte stores on the aligned body).
+__device__ __forceinline__ void fill_part(int16_t *table, long long n, long long b, long long nb) {
+    const long long tid = b * blockDim.x + threadIdx.x, stride = nb * blockDim.x;
+    const long long head = min(n, (long long)((16 - ((uintptr_t)table & 15)) & 15) / 2);
+    if (tid < head) table[tid] = (int16_t)-1;
+    const long long body = (n - head) / 8;
+    int4 *v = reinterpret_cast<int4 *>(table + head);
+    const int4 ones = make_int4(-1, -1, -1, -1);
+    for (long long q = tid; q < body; q += stride) v[q] = ones;
+    for (long long q = head + body * 8 + tid; q < n; q += stride) table[q] = (int16_t)-1;
+}
+
+// CTAs [0, fill_blocks) write the table's -1s (HBM-bound, beside the latency-bound integration: the table is
+// read by nothing before the collision kernel), then come the generation CTAs, then the risk preparation.
 template <int LAYOUTS>
 __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
     pdl_start();
-    if ((int)blockIdx.x >= a.gen_blocks) {               // the risk preparation, independent of generation
-        prepare_block(a.prep, blockIdx.x - a.gen_blocks, a.prep_blocks);
+    if ((int)blockIdx.x < a.fill_blocks) {
+        fill_part(a.fill, a.n_fill, blockIdx.x, a.fill_blocks);
         return;
     }
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int bid = (int)blockIdx.x - a.fill_blocks;
+    if (bid >= a.gen_blocks) {                           // the risk preparation, independent of generation
+        prepare_block(a.prep, bid - a.gen_blocks, a.prep_blocks);
+        return;
+    }
+    const int w = bid * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= a.n_warps) return;                          // whole warps leave
     if ((LAYOUTS & 1) && (LAYOUTS == 1 || w < a.n_scan)) {   // one hypothesis by the whole warp
         const int lane = threadIdx.x & 31;
@@ -580,39 +599,38 @@ __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
 }
 
 // Bounding box of the 32 pose centres of each bound tile at each step: one warp per (32-hypothesis group,
-// step), a warp min/max reduction.  The descriptors are read before the wait for the generation kernel,
-// the poses after it.
-// With `fill` set, the CTAs past the bounds write the table's -1s (16-byte stores on the aligned body) before
-// the wait: nothing earlier in the launch sequence reads the table, so the HBM-rate fill overlaps the
-// generation kernel's tail, and the collision kernel stores first hits only.
+// chunk of 8 steps).  Lane i loads hypothesis i's x and y at the chunk's 8 steps (16 loads in flight),
+// then a butterfly reduce-scatter over the 32 values (step s, quantity q = x min, y min, x max, y max;
+// value 4 s + q) halves the values at each of its five levels, so that lane L ends with the finished value
+// L and the 8 boxes go out as one 128-byte store.  The descriptors are read before the wait for the
+// generation kernel, the poses after it.  With `fill` set, the CTAs past the bounds write the table's -1s
+// (16-byte stores on the aligned body) before the wait: nothing earlier in the launch sequence reads the
+// table, so the HBM-rate fill overlaps the generation kernel's tail, and the collision kernel stores first
+// hits only.
 constexpr int kFillCtas = 152 * 4;
+constexpr int kGenFillCtas = 152 * 2;   // fill CTAs of the generation launch (the rest of each SM integrates)
+constexpr int kBoundSteps = 8;          // steps per warp task
+
+__device__ __forceinline__ float box_op(bool is_max, float u, float v) { return is_max ? fmaxf(u, v) : fminf(u, v); }
 
 __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
     pdl_trigger();
-    const long long total = (long long)a.n_warps * a.max_steps;
+    const int chunks = (a.max_steps + kBoundSteps - 1) / kBoundSteps;
+    const long long total = (long long)a.n_warps * chunks;
     const long long bound_ctas = (total + 7) / 8;
     if ((long long)blockIdx.x >= bound_ctas) {   // a fill CTA
-        const long long n = a.n_fill;
-        const long long tid = ((long long)blockIdx.x - bound_ctas) * blockDim.x + threadIdx.x;
-        const long long stride = (long long)(gridDim.x - bound_ctas) * blockDim.x;
-        const long long head = min(n, (long long)((16 - ((uintptr_t)a.fill & 15)) & 15) / 2);
-        if (tid < head) a.fill[tid] = (int16_t)-1;
-        const long long body = (n - head) / 8;
-        int4 *v = reinterpret_cast<int4 *>(a.fill + head);
-        const int4 ones = make_int4(-1, -1, -1, -1);
-        for (long long q = tid; q < body; q += stride) v[q] = ones;
-        for (long long q = head + body * 8 + tid; q < n; q += stride) a.fill[q] = (int16_t)-1;
+        fill_part(a.fill, a.n_fill, (long long)blockIdx.x - bound_ctas, (long long)gridDim.x - bound_ctas);
         pdl_wait();
         return;
     }
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     bool live = g < total;
-    int k = 0, first = 0, h = 0, n_steps = 0;
+    int k0 = 0, first = 0, h = 0, n_steps = 0;
     long long pose_base = 0, bounds_base = 0;
     if (live) {
-        const int w = (int)(g / a.max_steps);
-        k = (int)(g - (long long)w * a.max_steps);
+        const int w = (int)(g / chunks);
+        k0 = (int)(g - (long long)w * chunks) * kBoundSteps;
         const ObjDesc &o = a.objs[a.warp_obj[w]];
         first = a.warp_first[w];
         h = o.h;
@@ -625,22 +643,47 @@ __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
         a.zero_counts[0] = 0ull;
         a.zero_counts[1] = 0ull;
     }
-    if (!live || k >= n_steps) return;
+    if (!live || k0 >= n_steps) return;             // uniform over the warp
     const int i = first + lane;
-    float x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
-    if (i < h) {
-        const long long idx = pose_base + (long long)k * h + i;
-        x0 = x1 = a.x[idx];
-        y0 = y1 = a.y[idx];
-    }
+    float v[4 * kBoundSteps];                       // value 4 s + q of step k0 + s
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, d));
-        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, d));
-        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, d));
-        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, d));
+    for (int s = 0; s < kBoundSteps; ++s) {
+        const bool ok = i < h && k0 + s < n_steps;
+        const long long idx = pose_base + (long long)(k0 + s) * h + i;
+        const float x = ok ? a.x[idx] : INFINITY, y = ok ? a.y[idx] : INFINITY;
+        v[4 * s] = x;
+        v[4 * s + 1] = y;
+        v[4 * s + 2] = ok ? x : -INFINITY;
+        v[4 * s + 3] = ok ? y : -INFINITY;
     }
-    if (lane == 0) a.bounds[bounds_base + (long long)(first / kBoundTile) * n_steps + k] = make_float4(x0, y0, x1, y1);
+    // levels 16, 8, 4: the kept values keep their quantity (q = index mod 4)
+#pragma unroll
+    for (int d = 16, n = 16; d >= 4; d >>= 1, n >>= 1) {
+        const bool upper = lane & d;
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+            const float send = upper ? v[j] : v[j + n], keep = upper ? v[j + n] : v[j];
+            v[j] = box_op((j & 3) >= 2, keep, __shfl_xor_sync(0xffffffffu, send, d));
+        }
+    }
+    {   // level 2: values q = 0, 1 (minima) or 2, 3 (maxima) kept
+        const bool upper = lane & 2;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float send = upper ? v[j] : v[j + 2], keep = upper ? v[j + 2] : v[j];
+            v[j] = box_op(upper, keep, __shfl_xor_sync(0xffffffffu, send, 2));
+        }
+    }
+    {   // level 1
+        const bool upper = lane & 1;
+        const float send = upper ? v[0] : v[1], keep = upper ? v[1] : v[0];
+        v[0] = box_op(lane & 2, keep, __shfl_xor_sync(0xffffffffu, send, 1));
+    }
+    const int s = lane >> 2;                        // lane L holds value L: step k0 + L / 4, quantity L % 4
+    if (k0 + s < n_steps) {
+        float *out = reinterpret_cast<float *>(a.bounds + bounds_base + (long long)(first / kBoundTile) * n_steps + k0);
+        out[lane] = v[0];
+    }
 }
 
 }  // namespace
@@ -652,7 +695,8 @@ cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
     // preparation CTAs (if any) then have 128 threads as well
     const int warps_per_block = a.n_warps < 4 * 152 ? 1 : 4;
     a.gen_blocks = (a.n_warps + warps_per_block - 1) / warps_per_block;
-    const long long blocks = (long long)a.gen_blocks + (a.prep_blocks > 0 ? a.prep_blocks : 0);
+    a.fill_blocks = a.fill && a.n_fill > 0 ? (int)std::min((long long)kGenFillCtas, (a.n_fill / 8 + 127) / 128 + 1) : 0;
+    const long long blocks = (long long)a.fill_blocks + a.gen_blocks + (a.prep_blocks > 0 ? a.prep_blocks : 0);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a.n_scan >= a.n_warps)
         gen_kernel<1><<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
@@ -664,7 +708,7 @@ cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
 }
 
 cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st, bool pdl) {
-    const long long total = (long long)a.n_warps * a.max_steps;
+    const long long total = (long long)a.n_warps * ((a.max_steps + kBoundSteps - 1) / kBoundSteps);
     if (total <= 0) return cudaSuccess;
     long long blocks = (total + 7) / 8;
     if (a.fill && a.n_fill > 0) blocks += std::min((long long)kFillCtas, (a.n_fill / 8 + 255) / 256 + 1);

@@ -134,6 +134,9 @@ struct GenArgs {
                               // the hypothesis); the rest: `lanes` hypotheses each, one thread per hypothesis
     const float *paths;       // path sections of the vehicles that follow paths (ObjDesc::path_off)
     float *x, *y, *c, *s;
+    int16_t *fill;            // if set: the launch's first fill_blocks CTAs write table[0, n_fill) = -1
+    long long n_fill;
+    int fill_blocks;          // set by launch_generate
 };
 
 struct BoundsArgs {
