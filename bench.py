@@ -558,102 +558,114 @@ def arrivals(rate: float, seconds: float, large_share: float, seed: int = 5):
 
 def measure_serving(mhc, torch, dev, seconds: float, rates: str = "", rate: float = 2000.0, large_share: float = 0.05):
     """Served requests (continuous batching, mhc_submit / mhc_poll) against the plain path (one synchronous
-    mhc_run per request in arrival order) at the same offered load: Poisson arrivals at `rate`, 95 % shaped
-    like the 11-object scene (64 placements, cycled) and 5 % like the 32-vehicle scene (4 placements).
-    Latency = arrival (submission) to the risk outputs on the host; the queue of the plain path counts."""
+    mhc_run per request in arrival order) at the same offered load: Poisson arrivals, 95 % shaped like the
+    11-object scene (64 placements, cycled) and 5 % like the 32-vehicle scene (4 placements).  The main
+    window runs `seconds` at `rate`; the sweep runs 2 s windows at each further rate in `rates`.  Latency =
+    arrival (submission) to the risk outputs on the host; the queue of the plain path counts.  Sustained
+    load = requests / (last completion - first arrival)."""
     import threading
     from paper_2005_06773_gb300 import scenarios as S
     small = [mhc.as_c(S.intersection11(100 + q)) for q in range(64)]
     large = [mhc.as_c(S.stress32(200 + q)) for q in range(4)]
-    plan = arrivals(rate, seconds, large_share)
-    reqs = [(t, kind, (large[q % 4] if kind else small[q % 64])) for q, (t, kind) in enumerate(plan)]
     ctx = mhc.Context(dev.index or 0, 256 << 20)
-    # the collision layouts for both shapes, then the serving loop
-    for cs in (small[0], large[0]):
-        lay = mhc.layout(cs)
-        p = mhc.alloc_poses(cs.sc, dev)
-        tb = torch.empty(lay["n_entries"], dtype=torch.int16, device=dev)
-        mhc.generate(ctx, cs, p)
-        mhc.autotune(ctx, cs, p, tb)
-        del p, tb
+    run_ctx = mhc.Context(dev.index or 0, max(mhc.layout(large[0])["run_bytes"], mhc.layout(small[0])["run_bytes"]) + (64 << 20))
+    for c in (ctx, run_ctx):   # the collision layouts of both shapes, tuned once per context
+        for cs in (small[0], large[0]):
+            p = mhc.alloc_poses(cs.sc, dev)
+            tb = torch.empty(mhc.layout(cs)["n_entries"], dtype=torch.int16, device=dev)
+            mhc.generate(c, cs, p)
+            mhc.autotune(c, cs, p, tb)
+            del p, tb
     torch.cuda.empty_cache()
+    outs = {id(cs): mhc.alloc_risk(cs, device="cpu", pin=True) for cs in small + large}
+    for cs in small[:4] + large[:1]:
+        mhc.run(run_ctx, cs, out=outs[id(cs)])
     srv = mhc.Server(ctx, 48 << 30)
     for cs in small[:8] + large[:1]:                    # warm-up (stream, pinned buffers, module load)
         t = srv.submit(cs)
         if not srv.poll(t, None, timeout_us=120_000_000):
             raise RuntimeError("warm-up request not finished after 120 s")
         srv.release(t)
-    tickets = [None] * len(reqs)
-    t0 = time.perf_counter()
-
-    def submitter():
-        for q, (t, kind, cs) in enumerate(reqs):
-            d = t0 + t - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            tickets[q] = srv.submit(cs)
-
-    th = threading.Thread(target=submitter)
-    th.start()
-    lat = {0: [], 1: []}
-    first_sub, last_done = None, 0
-    batch_sizes = []
-    for q in range(len(reqs)):
-        while tickets[q] is None:
-            time.sleep(0.0001)
-        if not srv.poll(tickets[q], None, timeout_us=120_000_000):
-            raise RuntimeError(f"served request {q} not finished after 120 s")
-        ns, bs = srv.times(tickets[q])
-        srv.release(tickets[q])
-        lat[reqs[q][1]].append((ns[2] - ns[0]) / 1e6)
-        first_sub = ns[0] if first_sub is None else min(first_sub, ns[0])
-        last_done = max(last_done, ns[2])
-        batch_sizes.append(bs)
-    th.join()
-    stats = srv.stats()
-    srv.stop()
-    served_s = (last_done - first_sub) / 1e9
-
-    # plain path: one mhc_run per request, in arrival order, on one host thread
-    run_ctx = mhc.Context(dev.index or 0, max(mhc.layout(large[0])["run_bytes"], mhc.layout(small[0])["run_bytes"]) + (64 << 20))
-    for cs in (small[0], large[0]):
-        run_ctx_p = mhc.alloc_poses(cs.sc, dev)
-        run_ctx_t = torch.empty(mhc.layout(cs)["n_entries"], dtype=torch.int16, device=dev)
-        mhc.generate(run_ctx, cs, run_ctx_p)
-        mhc.autotune(run_ctx, cs, run_ctx_p, run_ctx_t)
-        del run_ctx_p, run_ctx_t
-    torch.cuda.empty_cache()
-    outs = {id(cs): mhc.alloc_risk(cs, device="cpu", pin=True) for cs in small + large}
-    for cs in small[:4] + large[:1]:
-        mhc.run(run_ctx, cs, out=outs[id(cs)])
-    plat = {0: [], 1: []}
-    t0 = time.perf_counter()
-    for t, kind, cs in reqs:
-        d = t0 + t - time.perf_counter()
-        if d > 0:
-            time.sleep(d)
-        mhc.run(run_ctx, cs, out=outs[id(cs)])
-        plat[kind].append(1e3 * (time.perf_counter() - (t0 + t)))
-    plain_s = time.perf_counter() - t0 - reqs[0][0]
-    run_ctx.close()
-    ctx.close()
-    torch.cuda.empty_cache()
 
     def summary(v):
         return {"n": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99), "max_ms": max(v) if v else None}
 
-    n = len(reqs)
-    return {
-        "offered": {"rate_per_s": rate, "seconds": seconds, "requests": n, "large_share": large_share,
-                    "small": "11-object intersection shape (1.70e8 tests), 64 placements",
-                    "large": "32-vehicle shape (1.04e11 tests, 4.2 GB table), 4 placements"},
-        "served": {"scenarios_per_s": n / served_s, "small": summary(lat[0]), "large": summary(lat[1]),
-                   "all": summary(lat[0] + lat[1]), "batches": stats["batches"],
-                   "mean_batch": statistics.mean(batch_sizes) if batch_sizes else None},
-        "plain": {"scenarios_per_s": n / plain_s, "small": summary(plat[0]), "large": summary(plat[1]),
-                  "all": summary(plat[0] + plat[1]),
-                  "path": "mhc_run per request in arrival order (host in, host out, synchronous)"},
-    }
+    def one_rate(r, secs, seed):
+        plan = arrivals(r, secs, large_share, seed)
+        reqs = [(t, kind, (large[q % 4] if kind else small[q % 64])) for q, (t, kind) in enumerate(plan)]
+        tickets = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for q, (t, kind, cs) in enumerate(reqs):
+                d = t0 + t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[q] = srv.submit(cs)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat = {0: [], 1: []}
+        first_sub, last_done, batch_sizes = None, 0, []
+        # finished results are released per kind in arrival order (each lane of the server admits its queue in
+        # order): a finished request holds its resident table until released, so waiting on all of them in
+        # arrival order could leave the pool full of finished small requests while a queued large one waits
+        # for memory
+        import collections
+        pending = {0: collections.deque(), 1: collections.deque()}
+        nxt, idle_since = 0, time.perf_counter()
+        while nxt < len(reqs) or pending[0] or pending[1]:
+            while nxt < len(reqs) and tickets[nxt] is not None:
+                pending[reqs[nxt][1]].append(nxt)
+                nxt += 1
+            progressed = False
+            for kind in (0, 1):
+                dq = pending[kind]
+                while dq and srv.poll(tickets[dq[0]], None, timeout_us=0):
+                    q = dq.popleft()
+                    ns, bs = srv.times(tickets[q])
+                    srv.release(tickets[q])
+                    lat[kind].append((ns[2] - ns[0]) / 1e6)
+                    first_sub = ns[0] if first_sub is None else min(first_sub, ns[0])
+                    last_done = max(last_done, ns[2])
+                    batch_sizes.append(bs)
+                    progressed = True
+            if progressed:
+                idle_since = time.perf_counter()
+            elif time.perf_counter() - idle_since > 60.0:
+                raise RuntimeError(f"{len(pending[0]) + len(pending[1])} served requests made no progress for 60 s")
+            else:
+                time.sleep(0.0002)
+        th.join()
+        served_s = (last_done - first_sub) / 1e9
+        # plain path: one mhc_run per request, in arrival order, on one host thread
+        plat = {0: [], 1: []}
+        t0 = time.perf_counter()
+        for t, kind, cs in reqs:
+            d = t0 + t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            mhc.run(run_ctx, cs, out=outs[id(cs)])
+            plat[kind].append(1e3 * (time.perf_counter() - (t0 + t)))
+        plain_s = time.perf_counter() - t0 - reqs[0][0]
+        n = len(reqs)
+        return {"offered_per_s": r, "window_s": secs, "requests": n,
+                "served": {"sustained_per_s": n / served_s, "small": summary(lat[0]), "large": summary(lat[1]),
+                           "mean_batch": statistics.mean(batch_sizes) if batch_sizes else None},
+                "plain": {"sustained_per_s": n / plain_s, "small": summary(plat[0]), "large": summary(plat[1])}}
+
+    out = {"shape": "95 % 11-object scenes (1.70e8 tests, 64 placements), 5 % 32-vehicle scenes (1.04e11 tests, "
+                    "4.2 GB table, 4 placements); plain = mhc_run per request in arrival order, synchronous",
+           "main": one_rate(rate, seconds, 5)}
+    sweep = [float(x) for x in rates.split(",") if x.strip()]
+    if sweep:
+        out["sweep"] = [one_rate(r, 2.0, 6 + q) for q, r in enumerate(sweep)]
+    out["batches"] = srv.stats()["batches"]
+    srv.stop()
+    run_ctx.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def aggregate(units: float, seconds: float, world: int, device):

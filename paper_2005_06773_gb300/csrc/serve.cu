@@ -1,14 +1,17 @@
 // serve.cu -- continuous batching of scenario requests (mhc_submit / mhc_poll / mhc_release).
 //
-// A scheduler thread owns the admission: while a stream slot is idle and its lane's queue is not empty it
-// takes requests from the queue head as long as their device memory fits the pool (first fit, checked
-// exactly after the batch is laid out) and the batch limits hold, lays them out as one batch, and enqueues
-// on the slot's stream: descriptor upload, the fused batch kernels, the copy of the batch's risk outputs to
-// the slot's pinned buffer and a host callback.  The callback (a CUDA driver thread; no CUDA calls) copies
-// the outputs into the batch's host memory, frees the batch's scratch block and wakes pollers and the
-// scheduler.  Poses, table and device risk outputs stay resident in the batch's block until every request
-// of the batch is released.  Small requests run on high-priority streams of their own, so the thread-block
-// scheduler starts their CTAs ahead of those of a large batch in flight.
+// Each lane (small and large requests) has a scheduler thread that owns its admission: while a stream slot
+// of the lane is idle and the lane's queue is not empty it takes requests from the queue head as long as
+// the batch limits hold and the largest free pool block could hold them, lays them out as one batch
+// without the lock (a batch of one request reuses the layout built at submission), allocates its blocks
+// first fit (putting the requests back if the pool has no room), and enqueues on the slot's stream:
+// descriptor upload, the fused batch kernels, the copy of the batch's risk outputs to the slot's pinned
+// buffer and a host callback.  The callback (a CUDA driver thread; no CUDA calls) copies the outputs into
+// the batch's host memory, frees the batch's scratch block and wakes pollers and the schedulers.  Poses,
+// table and device risk outputs stay resident in the batch's block until every request of the batch is
+// released.  Small requests run on high-priority streams of their own, so the thread-block scheduler starts
+// their CTAs ahead of those of a large batch in flight, and the host work of a large batch does not hold
+// up the small lane.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -44,7 +47,9 @@ struct Request {
     long long tests = 0;
     size_t bytes = 0;                             // device bytes alone (resident + scratch)
     bool small = true;
-    enum State { kQueued, kRunning, kDone, kFailed } state = kQueued;
+    Layout L;                                     // the request's own layout (built at submission), reused by a
+    bool has_layout = false;                      // batch of this request alone
+    enum State { kQueued, kTaken, kRunning, kDone, kFailed } state = kQueued;   // kTaken: being laid out
     Batch *batch = nullptr;
     int index = 0;
     int64_t t_submit = 0, t_launch = 0, t_done = 0;
@@ -91,7 +96,7 @@ struct Server {
     std::deque<Request *> q_small, q_large;
     std::unordered_map<uint64_t, Request *> reqs;
     std::vector<Slot> slots;
-    std::thread th;
+    std::thread th_small, th_large;               // one scheduler per lane
     bool stopping = false, paused = false;
     uint64_t next_ticket = 1;
     long long n_submitted = 0, n_completed = 0, n_batches = 0;
@@ -150,8 +155,10 @@ size_t resident_bytes(const Layout &L) {
            risk_output_bytes(L) + kAlign;
 }
 
-// Takes requests for an idle slot from its lane's queue and allocates the batch's blocks (holds mu).
-Batch *form_batch(Server *S, Slot &sl) {
+// Takes requests for an idle slot from the head of its lane's queue (holds mu): as many as the batch limits
+// allow and the largest free pool block could hold.  They are marked taken, so a release meanwhile only
+// flags them.
+std::vector<Request *> take_requests(Server *S, const Slot &sl) {
     std::deque<Request *> &q = sl.small ? S->q_small : S->q_large;
     std::vector<Request *> take;
     size_t need = 0;
@@ -163,41 +170,64 @@ Batch *form_batch(Server *S, Slot &sl) {
         if (need + r->bytes > largest) break;
         take.push_back(r);
         q.pop_front();
+        r->state = Request::kTaken;
         need += r->bytes;
         tests += r->tests;
     }
-    if (take.empty()) return nullptr;
+    return take;
+}
+
+// Puts taken requests back at the head of their queue, in order (holds mu); those released meanwhile go.
+void untake(Server *S, std::vector<Request *> &take, bool small) {
+    std::deque<Request *> &q = small ? S->q_small : S->q_large;
+    for (auto it = take.rbegin(); it != take.rend(); ++it) {
+        Request *r = *it;
+        if (r->released) { delete r; continue; }
+        r->state = Request::kQueued;
+        q.push_front(r);
+    }
+    take.clear();
+}
+
+// The batch of taken requests laid out (without mu: the host work of a large scenario does not hold up
+// the other lane, submissions or polls).  A batch of one request reuses the layout built at submission.
+Batch *build_batch(Server *S, std::vector<Request *> &take) {
     Batch *b = new Batch();
     b->srv = S;
-    std::vector<mhc_scenario> scs;
     std::vector<const float *> wp;
     bool any_w = false;
-    for (Request *r : take) {
-        scs.push_back(r->sc);
+    for (Request *r : take)
         for (size_t o = 0; o < r->objs.size(); ++o) {
             wp.push_back(r->has_w && !r->weights[o].empty() ? r->weights[o].data() : nullptr);
             any_w |= wp.back() != nullptr;
         }
+    bool ok;
+    if (take.size() == 1 && take[0]->has_layout) {
+        b->L = take[0]->L;
+        ok = true;
+    } else {
+        std::vector<mhc_scenario> scs;
+        for (Request *r : take) scs.push_back(r->sc);
+        ok = build_layout(scs.data(), (int)scs.size(), b->L) == MHC_OK;
+        if (ok) plan_generation(b->L, S->shadow.n_sm, S->shadow.gen_scan);
     }
-    bool ok = build_layout(scs.data(), (int)scs.size(), b->L) == MHC_OK;
-    if (ok) {
-        plan_generation(b->L, S->shadow.n_sm, S->shadow.gen_scan);
-        ok = gather_weights(b->L, any_w ? wp.data() : nullptr, b->w) == MHC_OK;
-    }
+    if (ok) ok = gather_weights(b->L, any_w ? wp.data() : nullptr, b->w) == MHC_OK;
     if (ok) {
         b->res_bytes = resident_bytes(b->L);
         b->scr_bytes = scratch_of(b->L, !b->w.empty()).total + kAlign;
-        ok = pool_alloc(S->pool, b->res_bytes, &b->res_off);
-        if (ok && !(b->scr_held = pool_alloc(S->pool, b->scr_bytes, &b->scr_off))) {
-            pool_free(S->pool, b->res_off);
-            ok = false;
-        }
-        if (!ok) b->res_bytes = 0;
     }
-    if (!ok) {   // fragmentation (or, never for validated requests, a layout error): back to the queue
-        for (auto it = take.rbegin(); it != take.rend(); ++it) q.push_front(*it);
-        delete b;
-        return nullptr;
+    if (!ok) { delete b; return nullptr; }
+    return b;
+}
+
+// The batch's pool blocks and its requests' states (holds mu).  False: the pool has no room (the caller
+// puts the requests back).
+bool admit_batch(Server *S, Batch *b, std::vector<Request *> &take) {
+    if (!pool_alloc(S->pool, b->res_bytes, &b->res_off)) { b->res_bytes = 0; return false; }
+    if (!(b->scr_held = pool_alloc(S->pool, b->scr_bytes, &b->scr_off))) {
+        pool_free(S->pool, b->res_off);
+        b->res_bytes = 0;
+        return false;
     }
     b->reqs = take;
     b->live = (int)take.size();
@@ -209,7 +239,7 @@ Batch *form_batch(Server *S, Slot &sl) {
         take[q2]->t_launch = t;
         if (take[q2]->released) --b->live;
     }
-    return b;
+    return true;
 }
 
 // Host work and enqueue of one batch on its slot (without mu).  Returns false if the callback was not
@@ -262,13 +292,15 @@ bool launch_batch(Server *S, Batch *b, Slot &sl) {
     return false;
 }
 
-void scheduler(Server *S) {
+// One scheduler thread per lane: while a slot of its lane is idle and the lane's queue is not empty it
+// takes requests, lays them out, admits them into the pool and enqueues the batch.
+void scheduler(Server *S, bool small_lane) {
     cudaSetDevice(S->ctx->device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stopping) {
         // a batch whose stream reports an error never gets its callback: fail it here
         for (Slot &sl : S->slots) {
-            if (!sl.busy) continue;
+            if (sl.small != small_lane || !sl.busy) continue;
             const cudaError_t q = cudaStreamQuery(sl.st);
             if (q != cudaSuccess && q != cudaErrorNotReady) fail_batch(S, sl.busy);
         }
@@ -276,9 +308,17 @@ void scheduler(Server *S) {
         if (!S->paused) {
             for (size_t s = 0; s < S->slots.size(); ++s) {
                 Slot &sl = S->slots[s];
-                if (sl.busy) continue;
-                Batch *b = form_batch(S, sl);
-                if (!b) continue;
+                if (sl.small != small_lane || sl.busy) continue;
+                std::vector<Request *> take = take_requests(S, sl);
+                if (take.empty()) continue;
+                lk.unlock();
+                Batch *b = build_batch(S, take);
+                lk.lock();
+                if (S->stopping || !b || !admit_batch(S, b, take)) {   // no room (or stopping): back to the queue
+                    delete b;
+                    untake(S, take, small_lane);
+                    break;
+                }
                 b->slot = (int)s;
                 sl.busy = b;
                 ++S->n_batches;
@@ -384,7 +424,8 @@ int mhc_serve_start(mhc_ctx *ctx, void *pool, size_t pool_bytes, const mhc_serve
         }
     }
     ctx->server = S;
-    S->th = std::thread(scheduler, S);
+    S->th_small = std::thread(scheduler, S, true);
+    S->th_large = std::thread(scheduler, S, false);
     return MHC_OK;
 }
 
@@ -396,7 +437,8 @@ int mhc_serve_stop(mhc_ctx *ctx) {
         S->stopping = true;
     }
     S->cv.notify_all();
-    S->th.join();
+    S->th_small.join();
+    S->th_large.join();
     for (Slot &sl : S->slots) cudaStreamSynchronize(sl.st);   // callbacks of the batches in flight run
     std::lock_guard<std::mutex> lk(S->mu);
     std::vector<Batch *> batches;
@@ -459,6 +501,9 @@ int mhc_submit(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_
     for (const PairDesc &p : L.pairs) r->tests += (long long)L.objs[p.a].h * L.objs[p.b].h * p.n_steps;
     r->bytes = resident_bytes(L) + scratch_of(L, r->has_w).total + 2 * kAlign;
     r->small = r->tests <= S->cfg.small_tests;
+    plan_generation(L, S->shadow.n_sm, S->shadow.gen_scan);
+    r->L = std::move(L);
+    r->has_layout = true;
     std::lock_guard<std::mutex> lk(S->mu);
     if (r->bytes > S->pool_bytes) {
         delete r;
@@ -512,6 +557,7 @@ int mhc_release(mhc_ctx *ctx, uint64_t ticket) {
         delete r;
         return MHC_OK;
     }
+    if (r->state == Request::kTaken) return MHC_OK;   // its scheduler admits it (or puts it back) and counts the flag
     Batch *b = r->batch;
     --b->live;
     maybe_retire(S, b);
