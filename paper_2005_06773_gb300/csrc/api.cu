@@ -255,6 +255,7 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
         if (outline[la] || outline[lb]) p.combo = p.combo == 0 ? 4 : (p.combo == 1 ? 5 : 6);
         p.poly_a = A.poly_off; p.nv_a = A.n_poly;
         p.poly_b = B.poly_off; p.nv_b = B.n_poly;
+        copy_object_fields(p, A, B);
         p.ego_side = la == sc->ego ? 0 : (lb == sc->ego ? 1 : -1);
         p.n_steps = N;
         p.scen = si;

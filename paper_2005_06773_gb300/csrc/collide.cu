@@ -123,8 +123,16 @@ __device__ __forceinline__ bool outline_disc(float dx, float dy, float c, float 
 // The exact test of one broad-phase candidate: d = p_b - p_a, (ca, sa) / (cb, sb) the body axes, la / wa
 // and lb / wb the half extents of rectangles, ra / rb the radii of discs.  OUTL: the batch has outlines
 // (combos 4..6); the kernels without them keep the short rectangle and disc tests alone.
+// The shape combination of a pair and its outlines, copied out of the descriptor once per block: a field read
+// through the descriptor in a loop with atomics would be read again after every atomic.
+struct PairShape {
+    int combo, poly_a, nv_a, poly_b, nv_b;
+};
+
+__device__ __forceinline__ PairShape shape_of(const PairDesc &P) { return {P.combo, P.poly_a, P.nv_a, P.poly_b, P.nv_b}; }
+
 template <bool OUTL>
-__device__ __forceinline__ bool narrow_hit(const PairDesc &P, const PolyVertex *polys, float dx, float dy,
+__device__ __forceinline__ bool narrow_hit(const PairShape P, const PolyVertex *polys, float dx, float dy,
                                            float2 qa, float2 qb, float la, float wa, float lb, float wb,
                                            float ra, float rb) {
     if (!OUTL) {
@@ -212,20 +220,25 @@ __device__ __forceinline__ void for_each_candidate(unsigned cand, int lane, Fn &
     }
 }
 
-// The pair of collision tile g: the last pair (in collision-grid order) whose first tile is <= g.  A 32-way
-// search by the whole warp (every lane must call it with the same g): each round the lanes probe 32
-// evenly spaced pairs at once and keep the span between the last probe <= g and the next, so 55 pairs take
-// one round of loads and 32,768 take three (a binary search is a chain of log2 n dependent loads).
+// The pair of collision tile g: the last pair (in collision-grid order) whose first tile is <= g.  A 64-way
+// search by the whole warp (every lane must call it with the same g): each round the lanes probe 64
+// evenly spaced pairs at once (two each) and keep the span between the last probe <= g and the next, so up
+// to 64 pairs take one round of loads and 4,096 two (a binary search is a chain of log2 n dependent loads).
 __device__ __forceinline__ int pair_of_tile(const CollideArgs &a, long long g) {
     const int lane = threadIdx.x & 31;
     int lo = 0, hi = a.n_pairs - 1;
-    while (lo < hi) {
+    while (lo < hi) {   // 64 probes per round (two per lane): a scene of up to 64 pairs in one round of loads
         const long long span = hi - lo + 1;
-        const bool le = a.pairs[lo + (int)(span * lane / 32)].tile_start <= g;
-        const unsigned m = __ballot_sync(0xffffffffu, le);           // lane 0 always: pairs[lo] <= g
-        const int L = 31 - __clz(m);
-        const int nlo = lo + (int)(span * L / 32);
-        hi = L == 31 ? hi : lo + (int)(span * (L + 1) / 32) - 1;
+        const bool le0 = a.pairs[lo + (int)(span * (2 * lane) / 64)].tile_start <= g;
+        const bool le1 = a.pairs[lo + (int)(span * (2 * lane + 1) / 64)].tile_start <= g;
+        const unsigned long long m = (unsigned long long)__ballot_sync(0xffffffffu, le0) |
+                                     (unsigned long long)__ballot_sync(0xffffffffu, le1) << 32;
+        // probe q = 2 lane + (0 | 1) sits at bit lane + 32 (q & 1); probe 0 always holds: pairs[lo] <= g
+        const unsigned even = (unsigned)m, odd = (unsigned)(m >> 32);
+        const int le = 31 - __clz(even), lo2 = odd ? 31 - __clz(odd) : -1;   // last true even / odd probe
+        const int L = 2 * lo2 + 1 > 2 * le ? 2 * lo2 + 1 : 2 * le;           // the true probes form a prefix
+        const int nlo = lo + (int)(span * L / 64);
+        hi = L == 63 ? hi : lo + (int)(span * (L + 1) / 64) - 1;
         lo = nlo;
     }
     return lo;
@@ -274,6 +287,7 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
     if (g >= a.n_tiles) return;
     const int lo = pair_of_tile(a, g);
     const PairDesc P = a.pairs[lo];
+    const PairShape shape = shape_of(P);
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
     const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
@@ -446,7 +460,7 @@ __global__ void __launch_bounds__(THREADS) collide_kernel(const CollideArgs a) {
                 const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                 const float2 qa = s_ra[c * kTile + i], qb = s_rb[c * kTile + j];
-                const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
+                const bool hit = narrow_hit<OUTL>(shape, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                 if (!hit) continue;
                 atomicOr(s_found + owner, 1ull << bit);
                 a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
@@ -593,6 +607,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
     if (g >= a.n_tiles) return;
     const int lo = pair_of_tile(a, g);
     const PairDesc P = a.pairs[lo];
+    const PairShape shape = shape_of(P);
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
     const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
@@ -742,7 +757,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
                     const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                     const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                     const float2 qa = s_ra[c * kTile + i], qb = s_rb[c * kTile + j];
-                    const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
+                    const bool hit = narrow_hit<OUTL>(shape, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                     if (hit) atomicMin(s_first + i * kTile + j, k);
                 }
                 __syncwarp();
@@ -856,6 +871,7 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
     const int quarter = (int)(gw - g * (SUB * SUB));
     const int lo = pair_of_tile(a, g);
     const PairDesc &P = a.pairs[lo];   // fields read where used (fewer live registers)
+    const PairShape shape = shape_of(P);
     const ObjDesc &A = a.objs[P.a];
     const ObjDesc &B = a.objs[P.b];
     const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
@@ -1011,7 +1027,7 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
                     const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                     const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                     const float2 qa = ra_s[i], qb = rb_s[j];
-                    const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
+                    const bool hit = narrow_hit<OUTL>(shape, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                     if (hit) {
                         any_hit = true;
                         atomicOr(s_new[owner] + (bit >> 6), 1ull << (bit & 63));
@@ -1279,6 +1295,7 @@ __global__ void __launch_bounds__(32 * kItemWarps, 32 / kItemWarps) items_kernel
         }
         if (!__ballot_sync(0xffffffffu, cand != 0u)) continue;
         const PairDesc &P = a.pairs[bk.pair];
+        const PairShape shape = shape_of(P);
         const float la = bk.la, wa = bk.wa, ra = bk.ra, lb = bk.lb, wb = bk.wb, rb = bk.rb;
         for (;;) {                              // rounds of at most 8 candidates per lane
             const int cnt = min(__popc(cand), 8);
@@ -1299,7 +1316,7 @@ __global__ void __launch_bounds__(32 * kItemWarps, 32 / kItemWarps) items_kernel
                 const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                 const float2 qa = ra_s[i], qb = rb_s[j];
-                const bool hit = narrow_hit<OUTL>(P, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
+                const bool hit = narrow_hit<OUTL>(shape, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
                 if (hit) atomicMin(a.first32 + bk.entry0 + (long long)i * bk.h_b + j, k);
             }
             __syncwarp();
@@ -1487,6 +1504,7 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
     constexpr int kNone = 0x7fffffff;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, lr = lane >> 2, lc = lane & 3;
     const PairDesc &P = *J.P;
+    const PairShape shape = shape_of(P);
     const int N = J.N, rows = J.rows, cols = J.cols;
     const bool col_ok = lane < cols;
     for (int q = threadIdx.x; q < 32 * 32; q += W * 32) s_first[q] = kNone;
@@ -1559,7 +1577,7 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
                 ++narrow;
                 const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
-                if (narrow_hit<OUTL>(P, a.polys, dx, dy, ra_s[i], rb_s[j], J.la, J.wa, J.lb, J.wb, J.ra, J.rb))
+                if (narrow_hit<OUTL>(shape, a.polys, dx, dy, ra_s[i], rb_s[j], J.la, J.wa, J.lb, J.wb, J.ra, J.rb))
                     atomicMin(first, k);
             });
         }
@@ -1583,7 +1601,10 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
     for (int u = 0; u < ROWS; ++u)
         if (r0 + u < rows && col_ok && s_first[32 * (r0 + u) + lane] != kNone) hits |= 1u << u;
     if (!__ballot_sync(0xffffffffu, hits != 0u)) return;
-    const int ego_side = P.ego_side;
+    // the pair's risk fields in registers (read through the descriptor they would be read again after
+    // every atomic)
+    const int ego_side = P.ego_side, n_obj_s = P.n_obj_s, co_local = P.co_local, pidx = P.index;
+    const long long kofs = P.kofs, lsum_base = P.lsum_base, mass_base = P.mass_base, hits_base = P.hits_base;
     unsigned long long cnt = 0, mass = 0;
     int16_t *tab = a.table + J.entry0 + (long long)r0 * hb;
     for_each_candidate(hits, lane, [&](int col, int u) {
@@ -1594,25 +1615,26 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
         const unsigned long long wt = to_fixed(s_prow[r] * s_pcol[col], kFixProb);
         ++cnt;
         mass += wt;
-        atomicAdd(a.acc.count_k + P.kofs + kk, 1ull);
-        atomicAdd(a.acc.H + P.kofs + kk, wt);
+        atomicAdd(a.acc.count_k + kofs + kk, 1ull);
+        atomicAdd(a.acc.H + kofs + kk, wt);
         if (ego_side >= 0) {
             const long long e = ego_side == 0 ? J.i0 + r : J.j0 + col;                // EGO hypothesis
             const long long co = ego_side == 0 ? J.traj_b + col : J.traj_a + r;       // CO hypothesis
-            atomicAdd(a.acc.lsum + P.lsum_base + (e * N + kk) * P.n_obj_s + P.co_local, a.lfix[co]);
-            atomicAdd(a.acc.mass + P.mass_base + e * P.n_obj_s + P.co_local, a.pfix[co]);
-            atomicAdd(a.acc.hits + P.hits_base + e, 1ull);
+            atomicAdd(a.acc.lsum + lsum_base + (e * N + kk) * n_obj_s + co_local, a.lfix[co]);
+            atomicAdd(a.acc.mass + mass_base + e * n_obj_s + co_local, a.pfix[co]);
+            atomicAdd(a.acc.hits + hits_base + e, 1ull);
         }
     });
-    if (!FUSED) return;
+    if constexpr (FUSED) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-        mass += __shfl_xor_sync(0xffffffffu, mass, d);
-    }
-    if (lane == 0 && cnt) {
-        atomicAdd(a.acc.count + P.index, cnt);
-        atomicAdd(a.acc.P + P.index, mass);
+        for (int d = 16; d > 0; d >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+            mass += __shfl_xor_sync(0xffffffffu, mass, d);
+        }
+        if (lane == 0 && cnt) {
+            atomicAdd(a.acc.count + pidx, cnt);
+            atomicAdd(a.acc.P + pidx, mass);
+        }
     }
 }
 
@@ -1621,30 +1643,28 @@ __device__ __forceinline__ BlockJob block_job(const CollideArgs &a, long long gw
     const long long g = gw >> 2;
     const int quarter = (int)(gw & 3);
     const int pidx = pair_of_tile(a, g);
-    const PairDesc &P = a.pairs[pidx];
-    const ObjDesc &A = a.objs[P.a];
-    const ObjDesc &B = a.objs[P.b];
+    const PairDesc &P = a.pairs[pidx];              // carries the objects' fields: no further load
     const int t = (int)(g - P.tile_start);          // < tiles_a x tiles_b <= n_tiles < 2^31
     const int ta = t / P.tiles_b, tb = t - ta * P.tiles_b;
     BlockJob J;
     J.P = &P;
     J.i0 = (ta * 2 + (quarter >> 1)) * 32;
     J.j0 = (tb * 2 + (quarter & 1)) * 32;
-    J.ha = A.h;
-    J.hb = B.h;
+    J.ha = P.h_a;
+    J.hb = P.h_b;
     J.rows = min(32, J.ha - J.i0);
     J.cols = min(32, J.hb - J.j0);
     J.N = P.n_steps;
     J.entry0 = P.off + (long long)J.i0 * J.hb + J.j0;
-    J.pose_a = A.pose_base + J.i0;
-    J.pose_b = B.pose_base + J.j0;
-    J.traj_a = A.traj_off + J.i0;
-    J.traj_b = B.traj_off + J.j0;
-    J.bA0 = a.bounds + A.bounds_base + (long long)(J.i0 / kBoundTile) * J.N;
-    J.bB0 = a.bounds + B.bounds_base + (long long)(J.j0 / kBoundTile) * J.N;
+    J.pose_a = P.pose_a + J.i0;
+    J.pose_b = P.pose_b + J.j0;
+    J.traj_a = P.traj_a + J.i0;
+    J.traj_b = P.traj_b + J.j0;
+    J.bA0 = a.bounds + P.bounds_a + (long long)(J.i0 / kBoundTile) * J.N;
+    J.bB0 = a.bounds + P.bounds_b + (long long)(J.j0 / kBoundTile) * J.N;
     J.rcull = P.r_cull;
     J.rc2 = P.rc2;
-    J.la = A.hl; J.wa = A.hw; J.ra = A.rad; J.lb = B.hl; J.wb = B.hw; J.rb = B.rad;
+    J.la = P.hl_a; J.wa = P.hw_a; J.ra = P.rad_a; J.lb = P.hl_b; J.wb = P.hw_b; J.rb = P.rad_b;
     return J;
 }
 

@@ -80,6 +80,12 @@ struct PairDesc {
     int poly_a, nv_a;         // combos 4..6: the outlines' vertices (ObjDesc::poly_off, n_poly)
     int poly_b, nv_b;
     int pad_;
+    // copies of the two objects' fields the collision kernels read (one load less on their chain)
+    long long pose_a, pose_b;     // ObjDesc::pose_base
+    long long bounds_a, bounds_b; // ObjDesc::bounds_base
+    long long traj_a, traj_b;     // ObjDesc::traj_off
+    int h_a, h_b;                 // hypotheses
+    float hl_a, hw_a, rad_a, hl_b, hw_b, rad_b;   // half extents, disc radii
 };
 
 // Per-scenario descriptor of a batch (device; risk stage).

@@ -27,6 +27,16 @@ constexpr long long kFillInCollideMax = 1LL << 25;   // table entries up to whic
 constexpr long long kItemsMax = 1LL << 22;             // step items (8 B each) up to which variant 6 applies
 constexpr long long kItemsMaxEntries = 1LL << 26;      // and table entries (4 B of first-step scratch each)
 constexpr long long kBlockListMax = 1LL << 19;         // 32 x 32 blocks (128 B records) up to which variant 8 applies
+
+// The object fields a pair descriptor carries for the collision kernels.
+inline void copy_object_fields(PairDesc &p, const ObjDesc &A, const ObjDesc &B) {
+    p.pose_a = A.pose_base; p.pose_b = B.pose_base;
+    p.bounds_a = A.bounds_base; p.bounds_b = B.bounds_base;
+    p.traj_a = A.traj_off; p.traj_b = B.traj_off;
+    p.h_a = A.h; p.h_b = B.h;
+    p.hl_a = A.hl; p.hw_a = A.hw; p.rad_a = A.rad;
+    p.hl_b = B.hl; p.hw_b = B.hw; p.rad_b = B.rad;
+}
 constexpr long long kGenScanMaxTraj = 4096;           // a scenario's hypotheses up to which generation is parallel in time
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }

@@ -25,6 +25,7 @@
 
 #include "../../include/mhc.h"
 #include "mhc_internal.cuh"
+#include "runtime.h"
 
 namespace mhc {
 void set_last_error(const char *why);   // api.cu
@@ -153,6 +154,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
             p.ego_side = a == sc->ego ? 0 : (b == sc->ego ? 1 : -1);
             p.n_steps = N;
             p.index = n_pairs - 1;
+            mhc::host::copy_object_fields(p, A, B);
             entries += (long long)A.h * B.h;
             tiles += (long long)p.tiles_a * p.tiles_b;
         }
