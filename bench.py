@@ -36,7 +36,8 @@ METRIC = "pose-pair tests/s"
 UNIT = "tests/s"
 # committed ncu summaries of the collision stage on the benchmark scene, per collision layout
 PROFILE_NOTES = {5: os.path.join(ROOT, "profiles", "collide_tile_kernel_intersection11.md"),
-                 6: os.path.join(ROOT, "profiles", "items_kernels_intersection11.md")}
+                 6: os.path.join(ROOT, "profiles", "items_kernels_intersection11.md"),
+                 7: os.path.join(ROOT, "profiles", "block_kernel_intersection11.md")}
 COLLIDE_SRC = [os.path.join(ROOT, "paper_2005_06773_gb300", "csrc", f) for f in ("collide.cu", "mhc_internal.cuh")]
 # Algorithmic lane instructions (FP32 pipe + ALU) per unit of collision work:
 #   broad-phase test: dx, dy (2 FADD), d^2 (FMUL + FFMA), compare = 4 FP32 + 1 ALU = 5;

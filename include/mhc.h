@@ -377,7 +377,12 @@ int mhc_autotune_batch(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, 
  * caller-owned, at least mhc_batch_info.plan_bytes, 256-byte aligned; used by the plan only) and keeps a
  * pinned host copy of the descriptors.  With flags MHC_PLAN_GRAPH it runs the launch sequence once and
  * captures it (descriptor upload from the pinned copy + the mhc_evaluate_batch kernels) as a CUDA graph;
- * each mhc_plan_launch is then one cudaGraphLaunch on `stream`.  The collision configuration (autotuned
+ * each mhc_plan_launch is then one cudaGraphLaunch on `stream`.  With MHC_PLAN_PIPELINE a plan of at
+ * least 8 scenarios is pipelined: its scenarios form 4 runs of about equal collision work, each laid out on
+ * its own, and the runs alternate between `stream` and a second stream of the plan, run g's generation
+ * waiting for run g - 1's generation only, so that generations and table fills may run beside the
+ * collision kernels of earlier runs (the launch ends with both streams joined on `stream`).  The results
+ * are those of the batch: integer outputs bit for bit, FP64 scalar totals to rounding.  The collision configuration (autotuned
  * or forced) is the one in force at creation.  mhc_plan_update replaces the scenarios by ones of the same
  * structure (objects, grid sizes, steps, pairs; initial states, grid values and shapes may change): it
  * waits for the plan's previous launch to finish, then rewrites the pinned copy, which the next launch
@@ -387,6 +392,7 @@ int mhc_autotune_batch(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, 
  */
 typedef struct mhc_plan mhc_plan;
 #define MHC_PLAN_GRAPH 1
+#define MHC_PLAN_PIPELINE 2
 int mhc_plan_create(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, const float *const *traj_weights,
                     const mhc_poses *poses, int16_t *table, const mhc_risk *out, void *scratch,
                     size_t scratch_bytes, int32_t flags, mhc_plan **plan);

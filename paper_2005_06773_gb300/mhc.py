@@ -66,6 +66,7 @@ class MhcBatchSlice(ctypes.Structure):
 
 
 MHC_PLAN_GRAPH = 1
+MHC_PLAN_PIPELINE = 2
 
 
 class MhcServeConfig(ctypes.Structure):
@@ -574,7 +575,7 @@ class Plan:
     sequence captured as a CUDA graph; launch() replays it, update() swaps in scenarios of the same
     structure (new initial states)."""
 
-    def __init__(self, ctx: Context, scenarios, weights=None, graph: bool = True, buffers=None):
+    def __init__(self, ctx: Context, scenarios, weights=None, graph: bool = True, buffers=None, pipeline: bool = False):
         self.ctx = ctx
         self.batch = as_batch(scenarios)
         self.info, _ = batch_layout(self.batch)
@@ -589,7 +590,9 @@ class Plan:
         h = c_void_p()
         _check(lib.mhc_plan_create(ctx.h, self.batch.ref, self.batch.n, self._w.ptr, ctypes.byref(ps),
                                    self.table.data_ptr(), ctypes.byref(rs), base + off,
-                                   self.scratch.numel() - off, MHC_PLAN_GRAPH if graph else 0, ctypes.byref(h)),
+                                   self.scratch.numel() - off,
+                                   (MHC_PLAN_GRAPH if graph else 0) | (MHC_PLAN_PIPELINE if pipeline else 0),
+                                   ctypes.byref(h)),
                "mhc_plan_create")
         self.h = h
 

@@ -279,3 +279,39 @@ def test_full_batch_256_graph(mhc, orc):
             plan.close()
         c.close()
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_pipelined_plan_equals_serial_plan(mhc, ctx, graph):
+    """A plan of 12 uneven scenarios asked to pipeline (four runs of scenarios on two streams) and the serial
+    plan give, with caller weights, the same poses, table and risk outputs, before and after an update with
+    new initial states (FP64 scalar totals to rounding)."""
+    batch = mixed_batch()
+    w = _weights(batch, 7)
+    pipe = mhc.Plan(ctx, batch, weights=w, graph=graph, pipeline=True)
+    ser = mhc.Plan(ctx, batch, weights=w, graph=graph)
+    try:
+        for rnd in range(2):
+            if rnd == 1:
+                moved = copy.deepcopy(batch)
+                for sc in moved:
+                    for o in sc.objects:
+                        o.x0 -= 0.5
+                        o.v0 = o.v0 * 0.97 + 0.2
+                pipe.update(moved)
+                ser.update(moved)
+            p1, t1, o1 = pipe.launch()
+            p2, t2, o2 = ser.launch()
+            torch.cuda.synchronize()
+            assert torch.equal(t1, t2)
+            for k in p1:
+                assert torch.equal(p1[k], p2[k]), k
+            for k in o1:
+                if k == "scalars":
+                    np.testing.assert_allclose(o1[k].cpu().numpy(), o2[k].cpu().numpy(), rtol=1e-12, atol=1e-18)
+                else:
+                    assert torch.equal(o1[k], o2[k]), (rnd, k)
+            assert int((t1 >= 0).sum()) > 0
+    finally:
+        pipe.close()
+        ser.close()
