@@ -1,7 +1,7 @@
 // collide.cu -- collision recognition (Section IV-C): first overlapping step of every hypothesis pair.
 //
 // Work decomposition: the hypothesis pairs of each object pair form 64 x 64 tiles, listed pair after pair
-// in collision-grid order (closest pairs first).  Six thread layouts share one result:
+// in collision-grid order (closest pairs first).  Eight thread layouts share one result:
 //   1, 2  one CTA per tile (256 threads with 4 x 4 register micro-tiles, or 64 threads with 8 x 8); the
 //         tile's active steps are staged into shared memory a chunk at a time and tested in any order, the
 //         earliest hit kept with a shared atomicMin;
@@ -12,9 +12,12 @@
 //         poses with the next step's loads in flight, and loops over blocks when the grid is capped;
 //   6     step items: (32 x 32 block, active step) pairs listed by one kernel and taken in any order by a
 //         persistent kernel that keeps each pair's earliest step with a global atomicMin; a third kernel
-//         writes the int16 table (and the fused risk terms) for the blocks with active steps.
-// The table is -1 outside first hits: a fill kernel writes it first, or variant 5 writes its own blocks
-// (small tables) and variant 6 its active blocks.
+//         writes the int16 table (and the fused risk terms) for the blocks with active steps;
+//   7     one 128-thread CTA per 32 x 32 block, the block's active steps spread over its four warps, first
+//         hits kept in shared memory (the small-scene default);
+//   8     as 7 for the blocks with an active step only, listed first by one warp per block.
+// The table is -1 outside first hits: a fill kernel (or fill CTAs of the generation or bounds launch) writes
+// it first, or variant 5 writes its own blocks (small tables) and variant 6 its active blocks.
 //
 // Broad phase (per test, 3 FP32 instructions): with h_a = (1 - eps)|p_a|^2 / 2 and
 // h_b = ((1 - eps)|p_b|^2 - R^2 - eps0) / 2 precomputed at staging, the pair is a candidate iff
@@ -861,8 +864,7 @@ __global__ void __launch_bounds__(WARPS * 32) collide_warp_kernel(const CollideA
 // One TE x TE block (warp task gw) walked by the calling warp; pa_s .. s_new are the warp's own slots.
 template <int TE, bool FUSED, bool OUTL>
 __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, int lane, float4 *pa_s, float4 *pb_s,
-                                           float2 *ra_s, float2 *rb_s, unsigned short *queue,
-                                           unsigned long long (*s_new)[2], float *prob_s) {
+                                           float2 *ra_s, float2 *rb_s, float *prob_s) {
     static_assert(TE == 64 || TE == 32, "block edge");
     constexpr int MI = TE / 8, MJ = TE / 4;       // micro-block of a lane
     constexpr int SUB = kTile / TE;               // blocks per tile edge
@@ -889,8 +891,6 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
     const float rc2 = P.rc2 + kEps0;
     const float ka = 0.5f * (1.0f - kEps);
     const float r_cull = P.r_cull;
-    unsigned long long *newf = s_new[lane];
-    newf[0] = newf[1] = 0ull;
     if (TE == 32 && a.fill_blocks) {   // this block's table entries start as -1 (coalesced 64-byte row stores)
         int16_t *row = a.table + P.off + (long long)i0 * B.h + j0;
         for (int r = 0; r < rows; ++r, row += B.h)
@@ -1006,56 +1006,41 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
         if (__ballot_sync(0xffffffffu, (c_lo | c_hi) != 0ull)) {
             bool any_hit = false;
             unsigned long long step_cnt = 0, step_mass = 0;
-            // compact and test one candidate per lane, in rounds of at most 8 per lane
-            for (;;) {
-                const int cnt = min(__popcll(c_lo) + __popcll(c_hi), 8);
-                int off, total;
-                if (!queue_offsets(cnt, lane, off, total)) break;
-                for (int q = 0; q < cnt; ++q) {
-                    int bit;
-                    if (c_lo) { bit = __ffsll((long long)c_lo) - 1; c_lo &= c_lo - 1ull; }
-                    else { bit = 64 + __ffsll((long long)c_hi) - 1; c_hi &= c_hi - 1ull; }
-                    queue[off + q] = (unsigned short)((lane << 7) | bit);
-                }
-                __syncwarp();
-                narrow += total;
-                for (int e = lane; e < total; e += 32) {
-                    const int ent = queue[e];
-                    const int owner = ent >> 7, bit = ent & 127;
+            // each lane tests the candidates of its own micro-block (a loop as long as the lane with the most;
+            // measured faster than compacting them into a warp queue first), so a hit sets its own mask bit
+            for (int h = 0; h < 2; ++h) {
+                unsigned long long cm = h ? c_hi : c_lo;
+                while (cm) {
+                    const int bit = 64 * h + __ffsll((long long)cm) - 1;
+                    cm &= cm - 1ull;
+                    ++narrow;
                     const int m = bit / MJ, n = bit % MJ;
-                    const int i = (owner >> 2) + 8 * m, j = (owner & 3) + 4 * n;
+                    const int i = lr + 8 * m, j = lc + 4 * n;
                     const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                     const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                     const float2 qa = ra_s[i], qb = rb_s[j];
-                    const bool hit = narrow_hit<OUTL>(shape, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb);
-                    if (hit) {
-                        any_hit = true;
-                        atomicOr(s_new[owner] + (bit >> 6), 1ull << (bit & 63));
-                        a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
-                        if (FUSED) {
-                            const float pa_ = prob_s[i], pb_ = prob_s[TE + j];
-                            const unsigned long long w = to_fixed(pa_ * pb_, kFixProb);
-                            ++step_cnt;
-                            step_mass += w;
-                            if (P.ego_side >= 0) {
-                                const int e = P.ego_side == 0 ? i0 + i : j0 + j;     // the EGO hypothesis
-                                const float pco = P.ego_side == 0 ? pb_ : pa_;       // the CO hypothesis
-                                atomicAdd(a.acc.mass + P.mass_base + (long long)e * P.n_obj_s + P.co_local,
-                                          to_fixed(pco, kFixProb));
-                                atomicAdd(a.acc.hits + P.hits_base + e, 1ull);
-                                atomicAdd(a.acc.lsum + P.lsum_base + ((long long)e * N + k) * P.n_obj_s + P.co_local,
-                                          to_fixed(neg_log_survival(pco), kFixLog));
-                            }
+                    if (!narrow_hit<OUTL>(shape, a.polys, dx, dy, qa, qb, la, wa, lb, wb, ra, rb)) continue;
+                    any_hit = true;
+                    if (h) found_hi |= 1ull << (bit - 64); else found_lo |= 1ull << bit;
+                    a.table[P.off + (long long)(i0 + i) * B.h + j0 + j] = (int16_t)k;
+                    if (FUSED) {
+                        const float pa_ = prob_s[i], pb_ = prob_s[TE + j];
+                        const unsigned long long w = to_fixed(pa_ * pb_, kFixProb);
+                        ++step_cnt;
+                        step_mass += w;
+                        if (P.ego_side >= 0) {
+                            const int e = P.ego_side == 0 ? i0 + i : j0 + j;     // the EGO hypothesis
+                            const float pco = P.ego_side == 0 ? pb_ : pa_;       // the CO hypothesis
+                            atomicAdd(a.acc.mass + P.mass_base + (long long)e * P.n_obj_s + P.co_local,
+                                      to_fixed(pco, kFixProb));
+                            atomicAdd(a.acc.hits + P.hits_base + e, 1ull);
+                            atomicAdd(a.acc.lsum + P.lsum_base + ((long long)e * N + k) * P.n_obj_s + P.co_local,
+                                      to_fixed(neg_log_survival(pco), kFixLog));
                         }
                     }
                 }
-                __syncwarp();
             }
             if (__any_sync(0xffffffffu, any_hit)) {
-                __syncwarp();
-                found_lo |= newf[0];
-                found_hi |= newf[1];
-                newf[0] = newf[1] = 0ull;
                 if (FUSED) {
 #pragma unroll
                     for (int d = 16; d > 0; d >>= 1) {
@@ -1073,6 +1058,10 @@ __device__ __forceinline__ void tile_block(const CollideArgs &a, long long gw, i
         }
         k = kn;
     }
+    if (a.counters) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) narrow += __shfl_xor_sync(0xffffffffu, narrow, d);
+    }
     if (a.counters && lane == 0) {
         if (narrow) count_narrow(a, P.combo, narrow);
         if (active_steps) atomicAdd(a.counters, (unsigned long long)active_steps * TE * TE);
@@ -1089,19 +1078,15 @@ template <int WARPS, int TE, bool FUSED, bool OUTL>
 __global__ void __launch_bounds__(WARPS * 32, (TE == 64 ? 16 : 24) / WARPS) collide_tile_kernel(const CollideArgs a) {
     pdl_start();
     constexpr int SUB = kTile / TE;
-    constexpr int QCAP = 256;
     __shared__ float4 s_pa[WARPS][TE];            // x, y, h_a
     __shared__ float4 s_pb[WARPS][TE];            // x, y, h_b
     __shared__ float2 s_ra[WARPS][TE];            // c, s
     __shared__ float2 s_rb[WARPS][TE];
-    __shared__ unsigned short s_queue[WARPS][QCAP];       // candidates: owner lane << 7 | bit
-    __shared__ unsigned long long s_new[WARPS][32][2];     // pairs found in this step, in owner-lane layout
     __shared__ float s_prob[WARPS][FUSED ? 2 * TE : 1];    // fused: the block's row and column probabilities
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long total = a.n_tiles * (SUB * SUB);
     for (long long gw = (long long)blockIdx.x * WARPS + warp; gw < total; gw += (long long)gridDim.x * WARPS)
-        tile_block<TE, FUSED, OUTL>(a, gw, lane, s_pa[warp], s_pb[warp], s_ra[warp], s_rb[warp], s_queue[warp],
-                              s_new[warp], s_prob[warp]);
+        tile_block<TE, FUSED, OUTL>(a, gw, lane, s_pa[warp], s_pb[warp], s_ra[warp], s_rb[warp], s_prob[warp]);
 }
 
 // ---- step-item layout (variant 6): the active (block, step) pairs of a small scene in parallel ----------
@@ -1449,9 +1434,10 @@ __global__ void __launch_bounds__(128) items_table_kernel(const CollideArgs a) {
 // (one ballot per 32 steps over the tile bounds: the same loads and the same result in every warp, so no
 // barrier is needed for it).  Warp w then takes the active steps of rank w, w + W, w + 2W, ... in
 // ascending order: the step's 32 + 32 poses staged in its own shared slot (its next step's poses in flight
-// meanwhile), the broad phase on a 4 x 8 micro-block per lane, the candidates then taken one per lane by a
-// warp-wide selection (for_each_candidate: no queue).  The block's first hits live in shared memory (atomicMin per hit); a candidate whose pair already
-// holds a step <= k there -- an earlier hit of this warp, or of another warp that got there first -- is
+// meanwhile), the broad phase on a 4 x 8 micro-block per lane, then each lane tests its own candidates (a
+// loop as long as the lane with the most: 34.8 us against 37.0 us for a warp-wide selection that hands
+// them out one per lane).  The block's first hits live in shared memory (atomicMin per hit); a candidate
+// whose pair already holds a step <= k there -- an earlier hit of this warp, or of another warp that got there first -- is
 // dropped before its narrow test.  After one barrier the CTA writes the block's int16 table rows and,
 // fused, adds the risk terms of its first hits, again one hit per lane (the per-hypothesis fixed-point
 // terms come precomputed by the risk preparation).  One launch does what the step-item layout does in three,
@@ -1570,16 +1556,19 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
                 if (fmaf(ax[m], qb.x, fmaf(ay[m], qb.y, -qb.z)) >= ah[m]) cand |= 1u << (MJ * m + n);
         }
         if (__ballot_sync(0xffffffffu, cand != 0u)) {
-            for_each_candidate(cand, lane, [&](int owner, int bit) {
-                const int i = (owner >> 2) + 8 * (bit / MJ), j = (owner & 3) + 4 * (bit % MJ);
+            while (cand) {                          // each lane its own candidates, in bit order
+                const int bit = __ffs(cand) - 1;
+                cand &= cand - 1u;
+                const int i = lr + 8 * (bit / MJ), j = lc + 4 * (bit % MJ);
                 int *first = s_first + 32 * i + j;
-                if (*first <= k) return;            // the pair already hit at this step or earlier
+                if (*first <= k) continue;          // the pair already hit at this step or earlier
                 ++narrow;
                 const float4 qa4 = pa_s[i], qb4 = pb_s[j];
                 const float dx = qb4.x - qa4.x, dy = qb4.y - qa4.y;
                 if (narrow_hit<OUTL>(shape, a.polys, dx, dy, ra_s[i], rb_s[j], J.la, J.wa, J.lb, J.wb, J.ra, J.rb))
                     atomicMin(first, k);
-            });
+            }
+            __syncwarp();
         }
         k = kn;
     }
