@@ -132,26 +132,29 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
         const mhc_object &src = sc->objects[o];
         ObjDesc d;
         std::memset(&d, 0, sizeof d);
-        char where[80];
-        std::snprintf(where, sizeof where, "%sobject %d: ", pre.c_str(), o);
-        if (src.kind != MHC_VEHICLE && src.kind != MHC_PEDESTRIAN) return fail(MHC_E_INVALID, std::string(where) + "bad kind");
+        auto where = [&]() {   // the message prefix, formatted only on a failure
+            char w[80];
+            std::snprintf(w, sizeof w, "%sobject %d: ", pre.c_str(), o);
+            return std::string(w);
+        };
+        if (src.kind != MHC_VEHICLE && src.kind != MHC_PEDESTRIAN) return fail(MHC_E_INVALID, where() + "bad kind");
         if (src.n_a < 1 || src.n_b < 1 || !src.grid_a || !src.grid_b)
-            return fail(MHC_E_INVALID, std::string(where) + "grids must be non-empty and non-NULL");
-        if ((long long)src.n_a * src.n_b > (1LL << 30)) return fail(MHC_E_INVALID, std::string(where) + "too many hypotheses");
+            return fail(MHC_E_INVALID, where() + "grids must be non-empty and non-NULL");
+        if ((long long)src.n_a * src.n_b > (1LL << 30)) return fail(MHC_E_INVALID, where() + "too many hypotheses");
         if (!finite(src.x0) || !finite(src.y0) || !finite(src.psi0) || !finite(src.v0) || !(src.v0 >= 0.f))
-            return fail(MHC_E_INVALID, std::string(where) + "initial state must be finite with v0 >= 0");
+            return fail(MHC_E_INVALID, where() + "initial state must be finite with v0 >= 0");
         if (L.grids.size() + (size_t)src.n_a + src.n_b > (size_t)0x7fffffff)
-            return fail(MHC_E_INVALID, std::string(where) + "grids too large");
+            return fail(MHC_E_INVALID, where() + "grids too large");
         d.kind = src.kind; d.flags = src.flags; d.n_a = src.n_a; d.n_b = src.n_b; d.h = src.n_a * src.n_b;
         d.grid_off = (int)L.grids.size();
         for (int q = 0; q < src.n_a; ++q) {
-            if (!finite(src.grid_a[q])) return fail(MHC_E_INVALID, std::string(where) + "grid_a not finite");
+            if (!finite(src.grid_a[q])) return fail(MHC_E_INVALID, where() + "grid_a not finite");
             if (src.kind == MHC_PEDESTRIAN && !(src.flags & MHC_PED_ACCEL_GRID) && src.grid_a[q] < 0.f)
-                return fail(MHC_E_INVALID, std::string(where) + "pedestrian speeds must be >= 0");
+                return fail(MHC_E_INVALID, where() + "pedestrian speeds must be >= 0");
             L.grids.push_back(src.grid_a[q]);
         }
         for (int q = 0; q < src.n_b; ++q) {
-            if (!finite(src.grid_b[q])) return fail(MHC_E_INVALID, std::string(where) + "grid_b not finite");
+            if (!finite(src.grid_b[q])) return fail(MHC_E_INVALID, where() + "grid_b not finite");
             L.grids.push_back(src.grid_b[q]);
         }
         d.traj_off = L.n_traj;
@@ -167,10 +170,10 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
         d.x0 = src.x0; d.y0 = src.y0; d.psi0 = src.psi0; d.v0 = src.v0; d.v_max = src.v_max;
         if (src.kind == MHC_VEHICLE) {
             if (!(src.length > 0.f) || !(src.width > 0.f) || !finite(src.length) || !finite(src.width))
-                return fail(MHC_E_INVALID, std::string(where) + "vehicle needs positive length and width");
+                return fail(MHC_E_INVALID, where() + "vehicle needs positive length and width");
             const float *pp = src.veh_params ? src.veh_params : kDefault;
             for (int q = 0; q < 6; ++q)
-                if (!(pp[q] > 0.f) || !finite(pp[q])) return fail(MHC_E_INVALID, std::string(where) + "vehicle parameters must be positive");
+                if (!(pp[q] > 0.f) || !finite(pp[q])) return fail(MHC_E_INVALID, where() + "vehicle parameters must be positive");
             d.m = pp[0]; d.Iz = pp[1]; d.lf = pp[2]; d.lr = pp[3]; d.caf = pp[4]; d.car = pp[5];
             d.hl = 0.5f * src.length; d.hw = 0.5f * src.width; d.rad = 0.f;
             d.circ = (float)std::sqrt((double)d.hl * d.hl + (double)d.hw * d.hw);
@@ -178,7 +181,7 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
                 d.poly_off = (int)L.polys.size();
                 if (src.n_vertices != 0) {
                     const std::string why = append_outline(src.vertices, src.n_vertices, L.polys, d.circ);
-                    if (!why.empty()) return fail(MHC_E_INVALID, std::string(where) + why);
+                    if (!why.empty()) return fail(MHC_E_INVALID, where() + why);
                     outline[o] = 1;
                 } else {
                     append_rectangle(d.hl, d.hw, L.polys);
@@ -186,8 +189,8 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
                 d.n_poly = (int)L.polys.size() - d.poly_off;
             }
         } else {
-            if (src.n_vertices != 0) return fail(MHC_E_INVALID, std::string(where) + "pedestrians take no outline");
-            if (!(src.radius > 0.f) || !finite(src.radius)) return fail(MHC_E_INVALID, std::string(where) + "pedestrian needs a positive radius");
+            if (src.n_vertices != 0) return fail(MHC_E_INVALID, where() + "pedestrians take no outline");
+            if (!(src.radius > 0.f) || !finite(src.radius)) return fail(MHC_E_INVALID, where() + "pedestrian needs a positive radius");
             d.rad = src.radius; d.circ = src.radius;
         }
         d.scen = si; d.n_steps = N; d.substeps = sc->substeps; d.model = sc->model; d.tau = sc->tau;
@@ -199,12 +202,12 @@ int append_scenario(const mhc_scenario *sc, int si, bool batch, Layout &L) {
         }
         d.path_off = -1;
         if (src.paths) {   // path hypotheses (Section IV-B.2b): n_b paths of three sections (x, y, psi)
-            if (src.kind != MHC_VEHICLE) return fail(MHC_E_INVALID, std::string(where) + "pedestrians take no paths");
+            if (src.kind != MHC_VEHICLE) return fail(MHC_E_INVALID, where() + "pedestrians take no paths");
             if (L.paths.size() / 9 + (size_t)src.n_b > (size_t)0x7fffffff)
-                return fail(MHC_E_INVALID, std::string(where) + "too many paths in the batch");
+                return fail(MHC_E_INVALID, where() + "too many paths in the batch");
             d.path_off = (int)(L.paths.size() / 9);
             for (long long q = 0; q < 9LL * src.n_b; ++q) {
-                if (!finite(src.paths[q])) return fail(MHC_E_INVALID, std::string(where) + "path sections must be finite");
+                if (!finite(src.paths[q])) return fail(MHC_E_INVALID, where() + "path sections must be finite");
                 L.paths.push_back(src.paths[q]);
             }
             // the sections switch at t = n tau_i >= 1.0 s and >= 1.5 s, decided in FP64
@@ -324,7 +327,8 @@ int build_layout(const mhc_scenario *sc, int n_scen, Layout &L) {
     std::vector<std::pair<float, int>> key(L.pairs.size());
     for (size_t p = 0; p < L.pairs.size(); ++p) {
         const ObjDesc &A = L.objs[L.pairs[p].a], &B = L.objs[L.pairs[p].b];
-        key[p] = {std::hypot(A.x0 - B.x0, A.y0 - B.y0) - A.circ - B.circ, (int)p};
+        const float dx = A.x0 - B.x0, dy = A.y0 - B.y0;
+        key[p] = {std::sqrt(dx * dx + dy * dy) - A.circ - B.circ, (int)p};
     }
     std::stable_sort(key.begin(), key.end());
     L.pairs_c.resize(L.pairs.size());
@@ -345,8 +349,6 @@ int build_layout(const mhc_scenario *sc, Layout &L) { return build_layout(sc, 1,
 void plan_generation(Layout &L, int n_sm, int mode) {
     L.gen_obj.clear();
     L.gen_first.clear();
-    L.gen_obj.reserve((size_t)L.n_traj + L.n_obj);
-    L.gen_first.reserve((size_t)L.n_traj + L.n_obj);
     // one warp per hypothesis (parallel in time) for the objects of scenarios with few hypotheses, so that
     // a scenario gets the same poses alone and in any batch
     std::vector<char> scan(L.n_obj, 0);
@@ -357,12 +359,16 @@ void plan_generation(Layout &L, int n_sm, int mode) {
         for (int o = S.obj0; o < S.obj0 + S.n_obj; ++o) scan[o] = sc && L.objs[o].path_off < 0;   // controller
                                                                      // feedback: a path hypothesis runs in order
     }
-    long long seq_traj = 0;
+    // the warp-per-hypothesis objects as ranges of warps: entry k = (object, its first warp)
+    long long seq_traj = 0, warps = 0;
     for (int o = 0; o < L.n_obj; ++o) {
         if (!scan[o]) { seq_traj += L.objs[o].h; continue; }
-        for (int q = 0; q < L.objs[o].h; ++q) { L.gen_obj.push_back(o); L.gen_first.push_back(q); }
+        L.gen_obj.push_back(o);
+        L.gen_first.push_back((int)warps);
+        warps += L.objs[o].h;
     }
-    L.n_gen_scan = (int)L.gen_obj.size();
+    L.n_gen_scan = (int)warps;
+    L.n_gen_scan_objs = (int)L.gen_obj.size();
     // the others: one thread per hypothesis, `lanes` per warp; with fewer hypotheses than warp schedulers
     // (4 per SM) each warp takes fewer of them (down to 4) to occupy every scheduler (more, smaller warps
     // measured slower on large scenes, where the sub-steps' instructions fill the issue slots)
@@ -370,9 +376,17 @@ void plan_generation(Layout &L, int n_sm, int mode) {
     int lanes = 32;
     while (lanes > 4 && (seq_traj + lanes - 1) / lanes < schedulers) lanes >>= 1;
     L.gen_lanes = lanes;
+    long long tasks = 0;
+    for (int o = 0; o < L.n_obj; ++o)
+        if (!scan[o]) tasks += (L.objs[o].h + lanes - 1) / lanes;
+    const size_t base = L.gen_obj.size();
+    L.gen_obj.resize(base + (size_t)tasks);
+    L.gen_first.resize(base + (size_t)tasks);
+    int *go = L.gen_obj.data() + base, *gf = L.gen_first.data() + base;
     for (int o = 0; o < L.n_obj; ++o)
         if (!scan[o])
-            for (int q = 0; q < L.objs[o].h; q += lanes) { L.gen_obj.push_back(o); L.gen_first.push_back(q); }
+            for (int q = 0; q < L.objs[o].h; q += lanes) { *go++ = o; *gf++ = q; }
+    L.n_gen_warps = L.n_gen_scan + (int)tasks;
 }
 
 // The step-item layout (collision variant 6) applies while its item list (4 x tiles x steps entries) stays
@@ -680,8 +694,9 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
     if (gen_out) {
         GenArgs g;
         g.objs = D.objs; g.regimes = D.regimes; g.grids = D.grids; g.warp_obj = D.gen_obj; g.warp_first = D.gen_first;
-        g.n_warps = (int)L.gen_obj.size(); g.lanes = L.gen_lanes;
+        g.n_warps = L.n_gen_warps; g.lanes = L.gen_lanes;
         g.n_scan = L.n_gen_scan;
+        g.n_scan_objs = L.n_gen_scan_objs;
         g.gen_blocks = 0;
         g.prep_blocks = 0;
         std::memset(&g.prep, 0, sizeof g.prep);

@@ -552,6 +552,25 @@ __device__ __forceinline__ void fill_part(int16_t *table, long long n, long long
 
 // CTAs [0, fill_blocks) write the table's -1s (HBM-bound, beside the latency-bound integration: the table is
 // read by nothing before the collision kernel), then come the generation CTAs, then the risk preparation.
+// The last k in [0, n) with v[k] <= x (v ascending, v[0] <= x), by the whole warp: each round the lanes
+// probe 64 evenly spaced entries (two each) and keep the span between the last probe <= x and the next, so
+// up to 64 entries take one round of loads.
+__device__ __forceinline__ int last_le(const int *v, int n, int x, int lane) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const long long span = hi - lo + 1;
+        const bool le0 = v[lo + (int)(span * (2 * lane) / 64)] <= x;
+        const bool le1 = v[lo + (int)(span * (2 * lane + 1) / 64)] <= x;
+        const unsigned even = __ballot_sync(0xffffffffu, le0), odd = __ballot_sync(0xffffffffu, le1);
+        const int le = 31 - __clz(even), lo2 = odd ? 31 - __clz(odd) : -1;   // last true even / odd probe
+        const int L = 2 * lo2 + 1 > 2 * le ? 2 * lo2 + 1 : 2 * le;           // the true probes form a prefix
+        const int nlo = lo + (int)(span * L / 64);
+        hi = L == 63 ? hi : lo + (int)(span * (L + 1) / 64) - 1;
+        lo = nlo;
+    }
+    return lo;
+}
+
 template <int LAYOUTS>
 __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
     pdl_start();
@@ -568,8 +587,9 @@ __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
     if (w >= a.n_warps) return;                          // whole warps leave
     if ((LAYOUTS & 1) && (LAYOUTS == 1 || w < a.n_scan)) {   // one hypothesis by the whole warp
         const int lane = threadIdx.x & 31;
-        const ObjDesc &o = a.objs[a.warp_obj[w]];
-        const int i = a.warp_first[w];
+        const int k = last_le(a.warp_first, a.n_scan_objs, w, lane);
+        const ObjDesc &o = a.objs[a.warp_obj[k]];
+        const int i = w - a.warp_first[k];
         const int ia = i / o.n_b, ib = i - ia * o.n_b;
         const float ga = a.grids[o.grid_off + ia];
         const float gb = a.grids[o.grid_off + o.n_a + ib];
@@ -582,8 +602,9 @@ __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
     }
     if (!(LAYOUTS & 2)) return;
     if ((threadIdx.x & 31) >= a.lanes) return;
-    const ObjDesc &o = a.objs[a.warp_obj[w]];
-    const int i = a.warp_first[w] + (threadIdx.x & 31);
+    const int e = a.n_scan_objs + (w - a.n_scan);
+    const ObjDesc &o = a.objs[a.warp_obj[e]];
+    const int i = a.warp_first[e] + (threadIdx.x & 31);
     if (i >= o.h) return;
     const int ia = i / o.n_b, ib = i - ia * o.n_b;
     const float ga = a.grids[o.grid_off + ia];

@@ -136,8 +136,11 @@ struct GenArgs {
     int gen_blocks;           // set by launch_generate: CTAs of the generation tasks
     int prep_blocks;          // > 0: that many further CTAs run the risk preparation `prep` (fused path)
     PrepArgs prep;
-    int n_scan;               // warp tasks [0, n_scan): one hypothesis each, parallel in time (warp_first =
-                              // the hypothesis); the rest: `lanes` hypotheses each, one thread per hypothesis
+    int n_scan;               // warps [0, n_scan): one hypothesis each, parallel in time: warp w belongs to
+                              // the last entry k < n_scan_objs with warp_first[k] <= w (object warp_obj[k],
+                              // hypothesis w - warp_first[k]); warp w >= n_scan: entry n_scan_objs + w -
+                              // n_scan, `lanes` hypotheses from warp_first of object warp_obj, a thread each
+    int n_scan_objs;
     const float *paths;       // path sections of the vehicles that follow paths (ObjDesc::path_off)
     float *x, *y, *c, *s;
     int16_t *fill;            // if set: the launch's first fill_blocks CTAs write table[0, n_fill) = -1

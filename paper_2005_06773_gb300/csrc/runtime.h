@@ -56,11 +56,15 @@ struct Layout {
     std::vector<PolyVertex> polys;                   // vehicles' outlines in scenarios that have convex outlines
     std::vector<float> paths;                        // path sections of the vehicles that follow paths
     std::vector<int> warp_obj, warp_first;          // 32-hypothesis bound tiles
-    std::vector<int> gen_obj, gen_first;            // generation warp tasks of gen_lanes hypotheses
+    std::vector<int> gen_obj, gen_first;            // generation tasks: n_gen_scan_objs (object, first warp)
+                                                     // ranges of a warp per hypothesis, then (object, first
+                                                     // hypothesis) tasks of gen_lanes hypotheses
     std::vector<int> pair0;                         // first pair of each scenario (n_scen + 1 entries)
     std::vector<long long> entry0;                  // first table entry of each scenario
     int gen_lanes = 32;
-    int n_gen_scan = 0;                              // the first n_gen_scan generation tasks: a warp per hypothesis
+    int n_gen_scan = 0;                              // the first n_gen_scan generation warps: a warp per hypothesis
+    int n_gen_scan_objs = 0;                         // objects those warps cover
+    int n_gen_warps = 0;                             // generation warps in all
     long long n_traj = 0, n_pose = 0, n_entries = 0, n_tiles = 0, n_bounds = 0;
     long long h_e = 0, n_kofs = 0, n_steps_total = 0, n_lsum = 0, n_mass = 0;
     int n_tiles32 = 0;
