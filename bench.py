@@ -457,7 +457,7 @@ def measure_workload(mhc, torch, sc, dev, steps, flush, peak):
     ops = collide_ops(work, mean_vertices(sc)) / max(coll_n, 1)
     out = {"tests_per_step": sc.n_tests(), "ms_per_step": ms, "tests_per_s": sc.n_tests() / (ms / 1e3),
            "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
-           "work_per_step": {k: v / steps for k, v in work.items() if v},
+           "work_per_step": {k: work[k] / steps for k in ("executed", "narrow")},
            "collide_roofline_frac": ops / coll_s / 1e12 / peak, "collide_achieved": ops / coll_s / 1e12,
            "collide_layout": [tuned[0], tuned[1]]}
     ctx.close()
@@ -537,7 +537,7 @@ def measure_batch(mhc, torch, dev, steps, flush, batch_peak, count=256):
         "batch_call": {"ms_per_batch": b_ms, "scenarios_per_s": count / (b_ms / 1e3),
                        "tests_per_s": tests / (b_ms / 1e3), "host_ms_per_call": b_host,
                        "kernels_ms_per_batch": {k: v[0] / n_calls for k, v in prof.items()},
-                       "work_per_batch": {k: v / n_calls for k, v in work.items() if v},
+                       "work_per_batch": {k: work[k] / n_calls for k in ("executed", "narrow")},
                        "collide_roofline_frac": collide_ops(work) / n_calls / (prof["collide"][0] / n_calls / 1e3) / 1e12
                                                 / batch_peak},
         "plain_per_scenario": {"ms_per_batch": p_ms, "scenarios_per_s": count / (p_ms / 1e3),
@@ -855,7 +855,11 @@ def run_mhc(args):
         line["parity"] = parity_vs_oracle(sc, table, risk, oracle_out)
         line["cpu_baseline"] = base
     if rank == 0:
-        print(json.dumps(compact(line)), flush=True)
+        # the per-workload and batch figures and the parity check last, where a tail of the output keeps them
+        tail = ("serving", "cpu_oracle_cores", "extra_workloads", "batch", "parity", "cpu_baseline")
+        ordered = {k: v for k, v in line.items() if k not in tail}
+        ordered.update((k, line[k]) for k in tail if k in line)
+        print(json.dumps(compact(ordered)), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
