@@ -1501,17 +1501,24 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
     __syncthreads();
 
     // ---- the warp's active steps: ranks w, w + W, ... in ascending step order ----
-    int rank = 0;                                   // rank of the lowest bit left in `mask`
+    int rank0 = 0;                                  // active steps before the chunk k0 .. k0 + 31
+    auto my_bits = [&](unsigned m) -> unsigned {    // this warp's steps of a chunk (lane b: step k0 + b)
+        const bool own = ((m >> lane) & 1u) && (((rank0 + __popc(m & ((1u << lane) - 1u))) & (W - 1)) == w);
+        return __ballot_sync(0xffffffffu, own);
+    };
+    unsigned mine = my_bits(mask);
     auto next_mine = [&]() -> int {                 // warp-uniform; -1 when none is left
         for (;;) {
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                if ((rank++ & (W - 1)) == w) return k0 + b;
+            if (mine) {
+                const int b = __ffs(mine) - 1;
+                mine &= mine - 1u;
+                return k0 + b;
             }
+            rank0 += __popc(mask);
             k0 += 32;
             if (k0 >= N) return -1;
             mask = block_chunk_mask(a, J, k0);
+            mine = my_bits(mask);
         }
     };
     const bool oka = lane < rows, okb = col_ok;
