@@ -629,7 +629,13 @@ __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
 // table, so the HBM-rate fill overlaps the generation kernel's tail, and the collision kernel stores first
 // hits only.
 constexpr int kFillCtas = 152 * 4;
-constexpr int kGenFillCtas = 152 * 2;   // fill CTAs of the generation launch (the rest of each SM integrates)
+// Fill CTAs of the generation launch (the rest of each SM integrates).  Two per SM spread the fill's stores
+// over every SM, which a table much larger than the generation work needs to reach the HBM rate (32-vehicle
+// scene: 0.74 ms at two per SM, 0.94 ms at one); when the generation work is comparable, half an SM's worth
+// leaves it more room and both finish sooner (256-scenario batch: 1.68 ms against 2.01 ms).
+constexpr int kGenFillCtas = 152 * 2;
+constexpr int kGenFillCtasShared = 76;
+constexpr long long kFillPerHypothesis = 8192;   // table entries per hypothesis above which the fill dominates
 constexpr int kBoundSteps = 8;          // steps per warp task
 
 __device__ __forceinline__ float box_op(bool is_max, float u, float v) { return is_max ? fmaxf(u, v) : fminf(u, v); }
@@ -716,7 +722,9 @@ cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
     // preparation CTAs (if any) then have 128 threads as well
     const int warps_per_block = a.n_warps < 4 * 152 ? 1 : 4;
     a.gen_blocks = (a.n_warps + warps_per_block - 1) / warps_per_block;
-    a.fill_blocks = a.fill && a.n_fill > 0 ? (int)std::min((long long)kGenFillCtas, (a.n_fill / 8 + 127) / 128 + 1) : 0;
+    const long long hyps = (long long)a.n_scan + (long long)(a.n_warps - a.n_scan) * a.lanes;
+    const long long cap = a.n_fill > kFillPerHypothesis * std::max(1LL, hyps) ? kGenFillCtas : kGenFillCtasShared;
+    a.fill_blocks = a.fill && a.n_fill > 0 ? (int)std::min(cap, (a.n_fill / 8 + 127) / 128 + 1) : 0;
     const long long blocks = (long long)a.fill_blocks + a.gen_blocks + (a.prep_blocks > 0 ? a.prep_blocks : 0);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a.n_scan >= a.n_warps)
