@@ -1468,6 +1468,18 @@ struct BlockJob {
     float rcull, rc2, la, wa, ra, lb, wb, rb;
 };
 
+// Asynchronous 4- and 8-byte copies global -> shared (both addresses aligned to the size); cp_async_wait()
+// returns once the calling thread's copies have landed (a barrier then shows them to the CTA).
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Active steps k0 .. k0 + 31 of a block (one ballot over the two bound tiles' boxes; every lane calls it).
 __device__ __forceinline__ unsigned block_chunk_mask(const CollideArgs &a, const BlockJob &J, int k0) {
     const int k = k0 + (threadIdx.x & 31);
@@ -1485,7 +1497,8 @@ __device__ __forceinline__ unsigned block_chunk_mask(const CollideArgs &a, const
 template <int W, bool FUSED, bool OUTL>
 __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob &J, int k0, unsigned mask,
                                            float4 (*s_pa)[32], float4 (*s_pb)[32], float2 (*s_ra)[32],
-                                           float2 (*s_rb)[32], int *s_first, float *s_prow, float *s_pcol) {
+                                           float2 (*s_rb)[32], int *s_first, float *s_prow, float *s_pcol,
+                                           unsigned long long *s_lfix, unsigned long long *s_pfix) {
     constexpr int MI = 4, MJ = 8, ROWS = 32 / W;
     constexpr int kNone = 0x7fffffff;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, lr = lane >> 2, lc = lane & 3;
@@ -1494,11 +1507,20 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
     const int N = J.N, rows = J.rows, cols = J.cols;
     const bool col_ok = lane < cols;
     for (int q = threadIdx.x; q < 32 * 32; q += W * 32) s_first[q] = kNone;
+    // the epilogue's per-hypothesis inputs, copied asynchronously (their latency hides under the step loop):
+    // the row and column probabilities and, for an EGO pair, the CO side's fixed-point terms
     if (FUSED && w == 0) {
-        s_prow[lane] = lane < rows ? a.probf[J.traj_a + lane] : 0.0f;
-        s_pcol[lane] = col_ok ? a.probf[J.traj_b + lane] : 0.0f;
+        if (lane < rows) cp_async4(s_prow + lane, a.probf + J.traj_a + lane); else s_prow[lane] = 0.0f;
+        if (col_ok) cp_async4(s_pcol + lane, a.probf + J.traj_b + lane); else s_pcol[lane] = 0.0f;
     }
-    __syncthreads();
+    if (FUSED && w == (W > 1 ? 1 : 0) && P.ego_side >= 0) {
+        const bool co_ok = P.ego_side == 0 ? col_ok : lane < rows;
+        const long long co = (P.ego_side == 0 ? J.traj_b : J.traj_a) + lane;
+        if (co_ok) {
+            cp_async8(s_lfix + lane, a.lfix + co);
+            cp_async8(s_pfix + lane, a.pfix + co);
+        }
+    }
 
     // ---- the warp's active steps: ranks w, w + W, ... in ascending step order ----
     int rank0 = 0;                                  // active steps before the chunk k0 .. k0 + 31
@@ -1537,7 +1559,8 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
     unsigned narrow = 0;                            // this lane's narrow tests
     int steps = 0;
     int k = next_mine();
-    if (k >= 0) load(k);
+    if (k >= 0) load(k);                            // in flight across the barrier
+    __syncthreads();                                // s_first initialised
     while (k >= 0) {
         __syncwarp();                               // the previous step's slot is no longer read
         pa_s[lane] = make_float4(xa, ya, ka * fmaf(xa, xa, ya * ya), 0.0f);
@@ -1587,7 +1610,8 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
             if (steps) atomicAdd(a.counters, (unsigned long long)steps * 32 * 32);
         }
     }
-    __syncthreads();                                // every first hit of the block is in s_first
+    if (FUSED) cp_async_wait();
+    __syncthreads();                                // every first hit of the block is in s_first (and the copies)
 
     // ---- the first hits of this warp's rows, one hit per lane: the table entry and (fused) the risk terms ----
     const int r0 = w * ROWS;
@@ -1615,9 +1639,9 @@ __device__ __forceinline__ void block_work(const CollideArgs &a, const BlockJob 
         atomicAdd(a.acc.H + kofs + kk, wt);
         if (ego_side >= 0) {
             const long long e = ego_side == 0 ? J.i0 + r : J.j0 + col;                // EGO hypothesis
-            const long long co = ego_side == 0 ? J.traj_b + col : J.traj_a + r;       // CO hypothesis
-            atomicAdd(a.acc.lsum + lsum_base + (e * N + kk) * n_obj_s + co_local, a.lfix[co]);
-            atomicAdd(a.acc.mass + mass_base + e * n_obj_s + co_local, a.pfix[co]);
+            const int co = ego_side == 0 ? col : r;                                  // CO hypothesis (block-local)
+            atomicAdd(a.acc.lsum + lsum_base + (e * N + kk) * n_obj_s + co_local, s_lfix[co]);
+            atomicAdd(a.acc.mass + mass_base + e * n_obj_s + co_local, s_pfix[co]);
             atomicAdd(a.acc.hits + hits_base + e, 1ull);
         }
     });
@@ -1676,6 +1700,7 @@ __global__ void __launch_bounds__(W * 32, kBlockMinCtas) block_kernel(const Coll
     __shared__ float2 s_ra[W][32], s_rb[W][32];     // c, s
     __shared__ int s_first[32 * 32];                // first overlapping step of pair (i, j) at 32 i + j
     __shared__ float s_prow[32], s_pcol[32];        // fused: the block's row and column probabilities
+    __shared__ unsigned long long s_lfix[32], s_pfix[32];   // fused EGO pair: the CO side's fixed-point terms
     const BlockJob J = block_job(a, (long long)blockIdx.x);
     pdl_wait();
     if (J.rows <= 0 || J.cols <= 0) return;         // a quarter past a ragged edge (whole CTA)
@@ -1686,7 +1711,7 @@ __global__ void __launch_bounds__(W * 32, kBlockMinCtas) block_kernel(const Coll
         mask = block_chunk_mask(a, J, k0);
     }
     if (!mask) return;                              // the block never comes close: its entries keep the -1
-    block_work<W, FUSED, OUTL>(a, J, k0, mask, s_pa, s_pb, s_ra, s_rb, s_first, s_prow, s_pcol);
+    block_work<W, FUSED, OUTL>(a, J, k0, mask, s_pa, s_pb, s_ra, s_rb, s_first, s_prow, s_pcol, s_lfix, s_pfix);
 }
 
 // ---- block-list layout (variant 8): active blocks listed first, then a CTA per listed block ----
@@ -1741,6 +1766,7 @@ __global__ void __launch_bounds__(W * 32, kBlockMinCtas) block_rec_kernel(const 
     __shared__ float2 s_ra[W][32], s_rb[W][32];
     __shared__ int s_first[32 * 32];
     __shared__ float s_prow[32], s_pcol[32];
+    __shared__ unsigned long long s_lfix[32], s_pfix[32];
     const unsigned long long listed = *a.active_count;
     const ActiveBlock r = a.recs[blockIdx.x];       // within the array even past the list's end
     if ((unsigned long long)blockIdx.x >= listed) return;
@@ -1750,7 +1776,7 @@ __global__ void __launch_bounds__(W * 32, kBlockMinCtas) block_rec_kernel(const 
     J.bA0 = a.bounds + r.bounds_a; J.bB0 = a.bounds + r.bounds_b;
     J.ha = r.h_a; J.hb = r.h_b; J.N = r.n_steps; J.rows = r.rows; J.cols = r.cols; J.i0 = r.i0; J.j0 = r.j0;
     J.rcull = r.rcull; J.rc2 = r.rc2; J.la = r.la; J.wa = r.wa; J.ra = r.ra; J.lb = r.lb; J.wb = r.wb; J.rb = r.rb;
-    block_work<W, FUSED, OUTL>(a, J, r.k0, r.mask, s_pa, s_pb, s_ra, s_rb, s_first, s_prow, s_pcol);
+    block_work<W, FUSED, OUTL>(a, J, r.k0, r.mask, s_pa, s_pb, s_ra, s_rb, s_first, s_prow, s_pcol, s_lfix, s_pfix);
 }
 
 // table[0, n) = -1 (no collision), 16-byte stores on the aligned body
