@@ -236,10 +236,12 @@ int mhc_collision_counters(mhc_ctx *ctx, uint64_t *out, int32_t n_out, int reset
 
 /* Kernel timing (mhc_set_option(ctx, MHC_OPT_PROFILE, 1)): the library records a CUDA event pair on the
    launching stream around every kernel it launches.  mhc_profile_read synchronises those events and
-   returns, per kernel class (MHC_K_GENERATE, which on the fused mhc_evaluate / mhc_run path also runs the
-   risk preparation in extra CTAs; MHC_K_BOUNDS = the table fill (unless the collision kernel fills) and the
+   returns, per kernel class (MHC_K_GENERATE = the descriptor upload (a copy kernel reading mapped pinned
+   host memory) and generation, which on the fused mhc_evaluate / mhc_run path also runs the risk
+   preparation in extra CTAs; MHC_K_BOUNDS = the table fill (unless the collision kernel fills) and the
    tile-bounds kernel; MHC_K_COLLIDE; MHC_K_RISK = the risk kernels: prepare (unfused path), table scan
-   (unfused path), the EGO walk and, for large batches, the totals conversion), the summed milliseconds and
+   (unfused path), the EGO walk and, for large batches, the totals conversion, and mhc_run's copy of its
+   outputs into mapped pinned host memory), the summed milliseconds and
    the launch counts since the last reset; reset != 0 clears them.  Disabled by default (no events
    recorded); the events add GPU time, so time steps with it off. */
 #define MHC_OPT_PROFILE 2

@@ -513,14 +513,17 @@ int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, cha
     MHC_CUDA(cudaEventSynchronize(ctx->stage_ev[s]));
     if (ctx->stage_cap[s] < total) {
         if (ctx->stage[s]) MHC_CUDA(cudaFreeHost(ctx->stage[s]));
-        ctx->stage[s] = nullptr;
+        ctx->stage[s] = ctx->stage_dev[s] = nullptr;
         ctx->stage_cap[s] = 0;
         size_t cap = total < (1u << 20) ? (1u << 20) : total * 2;
-        MHC_CUDA(cudaHostAlloc(&ctx->stage[s], cap, cudaHostAllocDefault));
+        MHC_CUDA(alloc_mapped(cap, &ctx->stage[s], &ctx->stage_dev[s]));
         ctx->stage_cap[s] = cap;
     }
-    pack_descriptors(L, weights, static_cast<char *>(ctx->stage[s]), dev, out);
-    MHC_CUDA(cudaMemcpyAsync(dev, ctx->stage[s], total, cudaMemcpyHostToDevice, st));
+    pack_descriptors(L, weights, ctx->stage[s], dev, out);
+    {
+        TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
+        MHC_CUDA(launch_copy(dev, ctx->stage_dev[s], total, st));   // a kernel: no copy-engine hand-off
+    }
     MHC_CUDA(cudaEventRecord(ctx->stage_ev[s], st));
     ctx->h2d = (long long)total;
     ctx->d2h = 0;
@@ -658,7 +661,7 @@ size_t risk_output_bytes(const Layout &L) {
 // pass over the table): prepare -> generate -> fill + bounds -> collide -> ego walk + finish.
 int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, const mhc_poses *gen_out,
                const mhc_poses *coll_in, int16_t *table, bool risk, const mhc_risk *rout, cudaStream_t st,
-               bool fused) {
+               bool fused, bool after_upload) {
     RiskArgs r;
     fused = fused && risk && coll_in;
     if (risk) {
@@ -715,7 +718,7 @@ int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, cons
         g.fill = fill_in_gen ? table : nullptr;
         g.n_fill = fill_in_gen ? L.n_entries : 0;
         TimedScope ts(ctx, st, MHC_K_GENERATE, 1);
-        cudaError_t e = launch_generate(g, st);
+        cudaError_t e = launch_generate(g, st, after_upload && !ctx->profile);
         if (e != cudaSuccess) return cuda_fail(e, "generation kernel launch");
         after_kernel = true;
     }
@@ -967,7 +970,7 @@ int mhc_generate_trajectories(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_
     if (int r = begin_call(ctx, st)) return r;
     DevDesc D;
     if (int r = upload(ctx, L, nullptr, dev, st, D)) return r;
-    if (int r = launch_all(ctx, L, D, bump, out, nullptr, nullptr, false, nullptr, st)) return r;
+    if (int r = launch_all(ctx, L, D, bump, out, nullptr, nullptr, false, nullptr, st, false, true)) return r;
     return end_call(ctx, st);
 }
 
@@ -1043,7 +1046,7 @@ int evaluate_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const floa
     if (int r = begin_call(ctx, st)) return r;
     DevDesc D;
     if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
-    if (int r = launch_all(ctx, L, D, bump, poses, poses, table, true, out, st, true)) return r;
+    if (int r = launch_all(ctx, L, D, bump, poses, poses, table, true, out, st, true, true)) return r;
     return end_call(ctx, st);
 }
 
@@ -1083,7 +1086,7 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
                     if ((rc = begin_call(ctx, st))) break;
                     DevDesc D;
                     if ((rc = upload(ctx, L, nullptr, dev, st, D))) break;
-                    if ((rc = launch_all(ctx, L, D, bump, poses, poses, table, true, &R, st, true))) break;
+                    if ((rc = launch_all(ctx, L, D, bump, poses, poses, table, true, &R, st, true, true))) break;
                     if ((rc = end_call(ctx, st))) break;
                 } else {
                     Scratch S = scratch_of(L, false);
@@ -1166,18 +1169,21 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     if (int r = begin_call(ctx, st)) return r;
     DevDesc D;
     if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
-    if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st, true)) return r;
+    if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st, true, true)) return r;
     // the outputs are contiguous in the arena: one copy into pinned staging, then to the caller's arrays
     const size_t out_bytes = risk_output_bytes(L);
     if (ctx->out_stage_cap < out_bytes) {
         if (ctx->out_stage) MHC_CUDA(cudaFreeHost(ctx->out_stage));
-        ctx->out_stage = nullptr;
+        ctx->out_stage = ctx->out_stage_dev = nullptr;
         ctx->out_stage_cap = 0;
         const size_t cap = out_bytes < (1u << 20) ? (1u << 20) : 2 * out_bytes;
-        MHC_CUDA(cudaHostAlloc(&ctx->out_stage, cap, cudaHostAllocDefault));
+        MHC_CUDA(alloc_mapped(cap, &ctx->out_stage, &ctx->out_stage_dev));
         ctx->out_stage_cap = cap;
     }
-    MHC_CUDA(cudaMemcpyAsync(ctx->out_stage, R.count, out_bytes, cudaMemcpyDeviceToHost, st));
+    {
+        TimedScope ts(ctx, st, MHC_K_RISK, 1);
+        MHC_CUDA(launch_copy(ctx->out_stage_dev, R.count, out_bytes, st));   // written into mapped host memory
+    }
     ctx->d2h = (long long)out_bytes;
     if (int r = end_call(ctx, st)) return r;
     MHC_CUDA(cudaStreamSynchronize(st));

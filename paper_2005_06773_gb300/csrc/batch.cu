@@ -35,7 +35,8 @@ struct mhc_plan {
     bool has_w = false;
     char *dev = nullptr;               // caller's device scratch
     size_t dev_bytes = 0;
-    char *host = nullptr;              // pinned copy of the descriptors (source of each launch's upload)
+    char *host = nullptr;              // mapped pinned copy of the descriptors (source of each launch's upload)
+    char *host_dev = nullptr;          // its device address
     size_t desc_bytes = 0;
     DevDesc D{};
     mhc_poses poses{};
@@ -120,10 +121,10 @@ size_t plan_scratch_bytes(const mhc_scenario *scens, const Layout &L, bool with_
 // faster (15.26 ms against 14.87 ms as graphs): the large-scene collision kernel holds every SM's
 // register file, so the generation CTAs wait for its CTAs to retire; it stays an option (MHC_PLAN_PIPELINE).
 int plan_enqueue(mhc_plan *p, cudaStream_t st) {
-    MHC_CUDA(cudaMemcpyAsync(p->dev, p->host, p->desc_bytes, cudaMemcpyHostToDevice, st));
+    MHC_CUDA(launch_copy(p->dev, p->host_dev, p->desc_bytes, st));
     if (p->groups.size() <= 1) {
         Bump bump{p->dev, p->dev_bytes, align_up(p->desc_bytes)};
-        return launch_all(p->ctx, p->L, p->D, bump, &p->poses, &p->poses, p->table, true, &p->out, st, true);
+        return launch_all(p->ctx, p->L, p->D, bump, &p->poses, &p->poses, p->table, true, &p->out, st, true, true);
     }
     cudaEvent_t fork = p->ev[0], join = p->ev[1];
     MHC_CUDA(cudaEventRecord(fork, st));
@@ -319,7 +320,7 @@ int mhc_plan_create(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, con
         p->desc_bytes = pack_descriptors(p->L, p->has_w ? &p->w : nullptr, nullptr, p->dev, p->D);
     }
     cudaError_t e = cudaSetDevice(ctx->device);
-    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&p->host), p->desc_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = alloc_mapped(p->desc_bytes, &p->host, &p->host_dev);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess && p->groups.size() > 1) {

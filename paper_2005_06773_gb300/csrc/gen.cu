@@ -573,7 +573,10 @@ __device__ __forceinline__ int last_le(const int *v, int n, int x, int lane) {
 
 template <int LAYOUTS>
 __global__ void __launch_bounds__(128, 6) gen_kernel(const GenArgs a) {
-    pdl_start();
+    // wait first: launched as a dependent of the descriptor copy kernel, this kernel lets its own dependents
+    // (which read descriptors before their wait) start only once the copy is complete
+    pdl_wait();
+    pdl_trigger();
     if ((int)blockIdx.x < a.fill_blocks) {
         fill_part(a.fill, a.n_fill, blockIdx.x, a.fill_blocks);
         return;
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(256) bounds_kernel(const BoundsArgs a) {
 
 }  // namespace
 
-cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
+cudaError_t launch_generate(const GenArgs &args, cudaStream_t st, bool pdl) {
     GenArgs a = args;
     if (a.n_warps <= 0 && a.prep_blocks <= 0) return cudaSuccess;
     // few warps: one warp per block so that the latency-bound integration spreads over all SMs; the
@@ -727,13 +730,8 @@ cudaError_t launch_generate(const GenArgs &args, cudaStream_t st) {
     a.fill_blocks = a.fill && a.n_fill > 0 ? (int)std::min(cap, (a.n_fill / 8 + 127) / 128 + 1) : 0;
     const long long blocks = (long long)a.fill_blocks + a.gen_blocks + (a.prep_blocks > 0 ? a.prep_blocks : 0);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (a.n_scan >= a.n_warps)
-        gen_kernel<1><<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
-    else if (a.n_scan <= 0)
-        gen_kernel<2><<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
-    else
-        gen_kernel<3><<<(unsigned)blocks, 32 * warps_per_block, 0, st>>>(a);
-    return cudaGetLastError();
+    auto kernel = a.n_scan >= a.n_warps ? gen_kernel<1> : (a.n_scan <= 0 ? gen_kernel<2> : gen_kernel<3>);
+    return launch_kernel(kernel, dim3((unsigned)blocks), dim3(32 * warps_per_block), 0, st, pdl, a);
 }
 
 cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st, bool pdl) {

@@ -330,7 +330,7 @@ __device__ __forceinline__ float neg_log_survival(float p) {
 
 // pdl: the launch follows another kernel of the library on the same stream with nothing in between, so
 // it may use programmatic dependent launch (see launch_kernel).
-cudaError_t launch_generate(const GenArgs &a, cudaStream_t st);
+cudaError_t launch_generate(const GenArgs &a, cudaStream_t st, bool pdl = false);
 cudaError_t launch_bounds(const BoundsArgs &a, cudaStream_t st, bool pdl = false);
 cudaError_t launch_fill_table(int16_t *table, long long n, cudaStream_t st, bool pdl = false);   // table[0, n) = -1
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st, bool pdl = false);  // stores first hits only

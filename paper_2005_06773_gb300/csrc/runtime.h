@@ -12,6 +12,11 @@ namespace mhc {
 namespace host {
 
 int fail(int code, const std::string &why);
+// Copies `bytes` with a kernel on `st` between addresses the device can use (device memory or the device
+// address of mapped pinned host memory), both 16-byte aligned.
+cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st);
+// Mapped pinned host memory: its host address and the address kernels use.
+cudaError_t alloc_mapped(size_t bytes, char **host, char **dev);
 int cuda_fail(cudaError_t e, const char *what);
 
 #define MHC_CUDA(call)                                            \
@@ -121,7 +126,8 @@ struct mhc_ctx {
     char *arena = nullptr;
     size_t arena_bytes = 0;
     bool owns = false;
-    void *stage[mhc::host::kSlots] = {};
+    char *stage[mhc::host::kSlots] = {};
+    char *stage_dev[mhc::host::kSlots] = {};     // the same buffers as kernels address them (mapped)
     size_t stage_cap[mhc::host::kSlots] = {};
     cudaEvent_t stage_ev[mhc::host::kSlots] = {};
     int slot = 0;
@@ -147,7 +153,8 @@ struct mhc_ctx {
     long long prof_n[MHC_K_COUNT] = {};
     long long h2d = 0, d2h = 0;
     void *server = nullptr;          // the serving loop (serve.cu), if started
-    void *out_stage = nullptr;       // pinned staging of mhc_run's outputs
+    char *out_stage = nullptr;       // mapped pinned staging of mhc_run's outputs
+    char *out_stage_dev = nullptr;   // its device address
     size_t out_stage_cap = 0;
 };
 
@@ -191,7 +198,9 @@ bool take_risk_outputs(Bump &bump, const Layout &L, mhc_risk &R);
 size_t risk_output_bytes(const Layout &L);
 int launch_all(mhc_ctx *ctx, const Layout &L, const DevDesc &D, Bump &bump, const mhc_poses *gen_out,
                const mhc_poses *coll_in, int16_t *table, bool risk, const mhc_risk *rout, cudaStream_t st,
-               bool fused = false);
+               bool fused = false, bool after_upload = false);
+// after_upload: the last operation on `st` is the descriptor copy kernel (launch_copy), so the generation
+// kernel may be a programmatic dependent launch of it
 int evaluate_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const float *const *traj_weights,
                   const mhc_poses *poses, int16_t *table, const mhc_risk *out, void *stream);
 int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_poses *poses, int16_t *table,

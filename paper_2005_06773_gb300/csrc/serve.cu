@@ -78,8 +78,9 @@ struct Slot {
     cudaStream_t st = nullptr;
     bool small = true;
     Batch *busy = nullptr;
-    char *stage = nullptr;   size_t stage_cap = 0;     // pinned: descriptors of the batch
-    char *pinned = nullptr;  size_t pinned_cap = 0;    // pinned: risk outputs of the batch
+    char *stage = nullptr;   size_t stage_cap = 0;     // mapped pinned: descriptors of the batch
+    char *pinned = nullptr;  size_t pinned_cap = 0;    // mapped pinned: risk outputs of the batch
+    char *stage_dev = nullptr, *pinned_dev = nullptr;  // their device addresses
     std::vector<char *> retired;                        // outgrown pinned buffers (freed at stop)
 };
 
@@ -263,29 +264,30 @@ bool launch_batch(Server *S, Batch *b, Slot &sl) {
     // pinned buffers only grow, and a replaced one is freed at mhc_serve_stop: cudaFreeHost waits for the
     // device, which would hold this thread (and every admission) behind the batches in flight
     if (sl.stage_cap < desc) {
-        char *nb = nullptr;
-        if (cudaHostAlloc(reinterpret_cast<void **>(&nb), desc * 2, cudaHostAllocDefault) != cudaSuccess) return false;
+        char *nb = nullptr, *nd = nullptr;
+        if (alloc_mapped(desc * 2, &nb, &nd) != cudaSuccess) return false;
         if (sl.stage) sl.retired.push_back(sl.stage);
         sl.stage = nb;
+        sl.stage_dev = nd;
         sl.stage_cap = desc * 2;
     }
     if (sl.pinned_cap < b->out_bytes) {
-        char *nb = nullptr;
-        if (cudaHostAlloc(reinterpret_cast<void **>(&nb), b->out_bytes * 2, cudaHostAllocDefault) != cudaSuccess)
-            return false;
+        char *nb = nullptr, *nd = nullptr;
+        if (alloc_mapped(b->out_bytes * 2, &nb, &nd) != cudaSuccess) return false;
         if (sl.pinned) sl.retired.push_back(sl.pinned);
         sl.pinned = nb;
+        sl.pinned_dev = nd;
         sl.pinned_cap = b->out_bytes * 2;
     }
     pack_descriptors(b->L, w, sl.stage, scr, D);
-    e = cudaMemcpyAsync(scr, sl.stage, desc, cudaMemcpyHostToDevice, sl.st);
+    e = launch_copy(scr, sl.stage_dev, desc, sl.st);
     if (e == cudaSuccess) {
         Bump sb{scr, b->scr_bytes, align_up(desc)};
         rc = launch_all(sl.small ? &S->shadow : &S->shadow_large, b->L, D, sb, &b->poses, &b->poses, b->table, true,
-                        &b->dev, sl.st, true);
+                        &b->dev, sl.st, true, true);
     }
     if (e == cudaSuccess && rc == MHC_OK)
-        e = cudaMemcpyAsync(sl.pinned, b->dev.count, b->out_bytes, cudaMemcpyDeviceToHost, sl.st);
+        e = launch_copy(sl.pinned_dev, b->dev.count, b->out_bytes, sl.st);
     if (e == cudaSuccess && rc == MHC_OK) e = cudaLaunchHostFunc(sl.st, on_batch_done, b);
     if (e == cudaSuccess && rc == MHC_OK) return true;
     cudaStreamSynchronize(sl.st);
@@ -408,9 +410,9 @@ int mhc_serve_start(mhc_ctx *ctx, void *pool, size_t pool_bytes, const mhc_serve
         sl.small = (int)s < c.small_slots;
         cudaError_t e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.small ? greatest : least);
         // pinned staging sized for typical batches up front (growth allocates, see launch_batch)
-        if (e == cudaSuccess && (e = cudaHostAlloc(reinterpret_cast<void **>(&sl.stage), kSlotPinned, 0)) == cudaSuccess)
+        if (e == cudaSuccess && (e = alloc_mapped(kSlotPinned, &sl.stage, &sl.stage_dev)) == cudaSuccess)
             sl.stage_cap = kSlotPinned;
-        if (e == cudaSuccess && (e = cudaHostAlloc(reinterpret_cast<void **>(&sl.pinned), kSlotPinned, 0)) == cudaSuccess)
+        if (e == cudaSuccess && (e = alloc_mapped(kSlotPinned, &sl.pinned, &sl.pinned_dev)) == cudaSuccess)
             sl.pinned_cap = kSlotPinned;
         if (e != cudaSuccess) {
             for (Slot &x : S->slots) {
