@@ -1182,7 +1182,8 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     }
     {
         TimedScope ts(ctx, st, MHC_K_RISK, 1);
-        MHC_CUDA(launch_copy(ctx->out_stage_dev, R.count, out_bytes, st));   // written into mapped host memory
+        // written into mapped host memory; a dependent of the risk walk, the sequence's last kernel
+        MHC_CUDA(launch_copy(ctx->out_stage_dev, R.count, out_bytes, st, !ctx->profile));
     }
     ctx->d2h = (long long)out_bytes;
     if (int r = end_call(ctx, st)) return r;

@@ -16,8 +16,9 @@ constexpr int kCopyMaxCtas = 152;
 
 // dst / src 16-byte aligned; n16 16-byte words, then `tail` (< 16) bytes
 __global__ void __launch_bounds__(kCopyThreads) copy_kernel(uint4 *__restrict__ dst, const uint4 *__restrict__ src,
-                                                            long long n16, int tail) {
+                                                            long long n16, int tail, int wait) {
     pdl_trigger();   // a dependent (the generation kernel) may take its SM slots now; it waits for the copy
+    if (wait) pdl_wait();   // launched as a dependent: the source is the previous kernel's output
     const long long stride = (long long)gridDim.x * kCopyThreads;
     for (long long i = (long long)blockIdx.x * kCopyThreads + threadIdx.x; i < n16; i += stride) dst[i] = src[i];
     if (blockIdx.x == 0 && (int)threadIdx.x < tail) {
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(uint4 *__restrict__ 
 
 namespace host {
 
-cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st, bool pdl) {
     if (bytes == 0) return cudaSuccess;
     if ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15u) return cudaErrorMisalignedAddress;
     const long long n16 = (long long)(bytes / 16);
@@ -39,9 +40,8 @@ cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t s
     long long ctas = (n16 + kCopyThreads - 1) / kCopyThreads;
     if (ctas < 1) ctas = 1;
     if (ctas > kCopyMaxCtas) ctas = kCopyMaxCtas;
-    copy_kernel<<<(unsigned)ctas, kCopyThreads, 0, st>>>(static_cast<uint4 *>(dst), static_cast<const uint4 *>(src),
-                                                        n16, tail);
-    return cudaGetLastError();
+    return launch_kernel(copy_kernel, dim3((unsigned)ctas), dim3(kCopyThreads), 0, st, pdl, static_cast<uint4 *>(dst),
+                         static_cast<const uint4 *>(src), n16, tail, pdl ? 1 : 0);
 }
 
 cudaError_t alloc_mapped(size_t bytes, char **host, char **dev) {

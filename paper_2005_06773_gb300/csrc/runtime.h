@@ -13,8 +13,9 @@ namespace host {
 
 int fail(int code, const std::string &why);
 // Copies `bytes` with a kernel on `st` between addresses the device can use (device memory or the device
-// address of mapped pinned host memory), both 16-byte aligned.
-cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st);
+// address of mapped pinned host memory), both 16-byte aligned.  pdl: launched as a programmatic dependent
+// of the kernel just before it on `st` (the copy waits for that kernel before it reads).
+cudaError_t launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st, bool pdl = false);
 // Mapped pinned host memory: its host address and the address kernels use.
 cudaError_t alloc_mapped(size_t bytes, char **host, char **dev);
 int cuda_fail(cudaError_t e, const char *what);

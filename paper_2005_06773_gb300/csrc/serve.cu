@@ -287,7 +287,7 @@ bool launch_batch(Server *S, Batch *b, Slot &sl) {
                         &b->dev, sl.st, true, true);
     }
     if (e == cudaSuccess && rc == MHC_OK)
-        e = launch_copy(sl.pinned_dev, b->dev.count, b->out_bytes, sl.st);
+        e = launch_copy(sl.pinned_dev, b->dev.count, b->out_bytes, sl.st, !(sl.small ? S->shadow : S->shadow_large).profile);
     if (e == cudaSuccess && rc == MHC_OK) e = cudaLaunchHostFunc(sl.st, on_batch_done, b);
     if (e == cudaSuccess && rc == MHC_OK) return true;
     cudaStreamSynchronize(sl.st);
