@@ -1,5 +1,6 @@
 // api.cu -- host runtime behind the C ABI of mhc.h: scenario validation and layout, the context arena,
-// descriptor upload through a ring of pinned staging buffers, and the launch sequence of each entry point.
+// descriptor upload through a ring of mapped pinned staging buffers (read by a copy kernel), and the launch
+// sequence of each entry point.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -1170,7 +1171,7 @@ int mhc_run(mhc_ctx *ctx, const mhc_scenario *scen, const float *const *traj_wei
     DevDesc D;
     if (int r = upload(ctx, L, w.empty() ? nullptr : &w, dev, st, D)) return r;
     if (int r = launch_all(ctx, L, D, bump, &P, &P, table, true, &R, st, true, true)) return r;
-    // the outputs are contiguous in the arena: one copy into pinned staging, then to the caller's arrays
+    // the outputs are contiguous in the arena: one copy into mapped pinned staging, then to the caller's arrays
     const size_t out_bytes = risk_output_bytes(L);
     if (ctx->out_stage_cap < out_bytes) {
         if (ctx->out_stage) MHC_CUDA(cudaFreeHost(ctx->out_stage));

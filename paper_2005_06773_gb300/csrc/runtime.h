@@ -103,7 +103,7 @@ struct Bump {
     }
 };
 
-// Pack the descriptors into a pinned staging slot and copy them to `dev` on `st`.
+// Pack the descriptors into a mapped pinned staging slot and copy them to `dev` on `st` with the copy kernel.
 struct DevDesc {
     ObjDesc *objs;
     PairDesc *pairs;

@@ -32,7 +32,7 @@ int64_t now_ns() {
         .count();
 }
 
-constexpr size_t kSlotPinned = 4u << 20;   // initial pinned staging per slot and direction
+constexpr size_t kSlotPinned = 4u << 20;   // initial mapped pinned staging per slot and direction
 
 struct Server;
 struct Batch;
