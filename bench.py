@@ -313,6 +313,73 @@ def _oracle_pool_task(chunk):
     return int((o.first_steps(_ORACLE_STATE["sc"], _ORACLE_STATE["poses"], *chunk) >= 0).sum())
 
 
+def _oracle_batch_init(root, scens):
+    sys.path.insert(0, root)
+    from oracle import oracle
+    _ORACLE_STATE.update(oracle=oracle, scens=scens, poses=[oracle.generate(sc) for sc in scens])
+
+
+def _oracle_batch_task(chunk):
+    o = _ORACLE_STATE["oracle"]
+    q = chunk[0]
+    return int((o.first_steps(_ORACLE_STATE["scens"][q], _ORACLE_STATE["poses"][q], *chunk[1:]) >= 0).sum())
+
+
+def cpu_oracle_batch(batch, target_tests: float = 1e8, n_scen: int = 16, seed: int = 11):
+    """The oracle (its functions unchanged) on a fixed sample of the uneven batch: n_scen scenarios drawn
+    by their share of the batch's pose tests, their trajectories generated, then random trajectory pairs of
+    those scenarios (drawn by pair size) up to about target_tests pose tests, on one host thread and on
+    every core (spawned workers generate the same scenarios); the rates extrapolated to the whole batch."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import oracle
+    oracle.build()
+    tests_s = np.array([sc.n_tests() for sc in batch], dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    pick = sorted(rng.choice(len(batch), size=min(n_scen, len(batch)), replace=False, p=tests_s / tests_s.sum()).tolist())
+    scens = [batch[q] for q in pick]
+    t0 = time.perf_counter()
+    poses = [oracle.generate(sc) for sc in scens]
+    t_gen = time.perf_counter() - t0
+    hyps = sum(int(oracle.traj_offsets(sc)[-1]) for sc in scens)
+    share = tests_s[pick] / tests_s[pick].sum()
+    chunks, tests = [], 0
+    for q, sc in enumerate(scens):
+        off = oracle.traj_offsets(sc)
+        pairs = oracle.pair_list(sc)
+        h = np.diff(off)
+        sizes = np.array([h[a] * h[b] for a, b in pairs], dtype=np.float64)
+        n = max(1, int(target_tests * share[q] / sc.n_steps))
+        k = rng.choice(len(pairs), size=n, p=sizes / sizes.sum())
+        oa = np.array([pairs[x][0] for x in k]); ob = np.array([pairs[x][1] for x in k])
+        ta = off[oa] + (rng.random(n) * h[oa]).astype(np.int64)
+        tb = off[ob] + (rng.random(n) * h[ob]).astype(np.int64)
+        tests += n * sc.n_steps
+        for s in np.array_split(np.arange(n), max(1, n // 100_000)):
+            chunks.append((q, oa[s], ta[s], ob[s], tb[s]))
+    t0 = time.perf_counter()
+    for c in chunks:
+        oracle.first_steps(scens[c[0]], poses[c[0]], *c[1:])
+    t1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"),
+                                initializer=_oracle_batch_init, initargs=(ROOT, scens)) as ex:
+        list(ex.map(_oracle_batch_task, chunks[:cores]))          # workers started, scenarios generated
+        t0 = time.perf_counter()
+        list(ex.map(_oracle_batch_task, chunks))
+        tn = time.perf_counter() - t0
+    all_tests = float(tests_s.sum())
+    all_hyps = sum(sc_h for sc_h in (sum(o.n_hyp for o in sc.objects) for sc in batch))
+    gen_s = t_gen * all_hyps / max(hyps, 1)
+    return {"tests": tests, "sample": f"{len(scens)} of {len(batch)} scenarios (drawn by their share of the tests), "
+                                      f"{sum(len(c[1]) for c in chunks)} random trajectory pairs (first-collision steps only)",
+            "one_thread_tests_per_s": tests / t1, "all_cores_tests_per_s": tests / tn, "cores": cores,
+            "batch_tests": all_tests, "generation_s_one_thread": gen_s,
+            "batch_s_one_thread": all_tests * t1 / tests + gen_s, "batch_s_all_cores": all_tests * tn / tests + gen_s / cores,
+            "cpu": cpu_model()}
+
+
 def cpu_model() -> str:
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -848,9 +915,10 @@ def run_mhc(args):
         base, oracle_out = cpu_baseline(sc, args.cpu_seconds)
         # the oracle on every host core as well (the whole table of the scene), and on a sample of the
         # 32-vehicle stress scene
+        scen_mod = __import__("paper_2005_06773_gb300.scenarios", fromlist=["x"])
         line["cpu_oracle_cores"] = {"intersection11": cpu_oracle_cores(sc, 1 << 40),
-                                    "stress32": cpu_oracle_cores(__import__("paper_2005_06773_gb300.scenarios",
-                                                                            fromlist=["x"]).stress32(4), 2_000_000)}
+                                    "stress32": cpu_oracle_cores(scen_mod.stress32(4), 2_000_000),
+                                    "batch256": cpu_oracle_batch(scen_mod.batch_scenarios(seed=3, count=256))}
         # the benchmarked step's own outputs (the last timed step's table and risk) against the oracle's
         line["parity"] = parity_vs_oracle(sc, table, risk, oracle_out)
         line["cpu_baseline"] = base

@@ -1,6 +1,6 @@
 """Host logic of bench.py on CPU: the DRAM traffic of an ncu summary is reported only for the collision code
 and layout it was captured on; the clock samplers fail over cleanly without NVML or nvidia-smi; the
-percentile helper."""
+percentile helper; the oracle timing of the uneven batch."""
 import os
 import sys
 
@@ -65,3 +65,16 @@ def test_percentiles():
     v = list(range(1, 101))
     assert bench.pct(v, 50) == 50 and bench.pct(v, 99) == 99 and bench.pct(v, 100) == 100
     assert bench.pct([], 50) is None
+
+
+def test_oracle_batch_sample_extrapolates():
+    """The uneven batch's oracle timing: a sample of whole scenarios and trajectory pairs, timed on one
+    thread and on every core, extrapolated to the batch's pose tests (small sizes here)."""
+    from paper_2005_06773_gb300 import scenarios as S
+    batch = S.batch_scenarios(seed=3, count=6)
+    r = bench.cpu_oracle_batch(batch, target_tests=2e5, n_scen=2)
+    assert 1e5 <= r["tests"] <= 3e5
+    assert r["batch_tests"] == sum(sc.n_tests() for sc in batch)
+    assert r["one_thread_tests_per_s"] > 0 and r["all_cores_tests_per_s"] > 0 and r["cores"] >= 1
+    assert r["batch_s_one_thread"] >= r["batch_tests"] / r["one_thread_tests_per_s"]
+    assert r["batch_s_all_cores"] >= r["batch_tests"] / r["all_cores_tests_per_s"]
