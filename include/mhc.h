@@ -172,9 +172,10 @@ const char *mhc_version(void);
 
 /*
  * Create a context on CUDA device `device`.  `arena` is a device buffer of `arena_bytes` bytes owned by the
- * caller (e.g. a framework allocation) that the library sub-allocates scratch from; with arena == NULL the
- * library allocates `arena_bytes` itself with cudaMalloc and frees it in mhc_destroy.
- * Errors: MHC_E_INVALID (bad device, arena_bytes < 1 MiB), MHC_E_CUDA, MHC_E_NOMEM.
+ * caller (e.g. a framework allocation; 256-byte aligned) that the library sub-allocates scratch from; with
+ * arena == NULL the library allocates `arena_bytes` itself with cudaMalloc and frees it in mhc_destroy.
+ * Errors: MHC_E_INVALID (bad device, arena_bytes < 1 MiB, arena not 256-byte aligned), MHC_E_CUDA,
+ * MHC_E_NOMEM.
  */
 int mhc_create(mhc_ctx **out, int device, void *arena, size_t arena_bytes);
 /* Wait for the context's outstanding work and release it (and the arena if the library allocated it). */

@@ -827,6 +827,8 @@ int mhc_create(mhc_ctx **out, int device, void *arena, size_t arena_bytes) {
     if (!out) return fail(MHC_E_INVALID, "out is NULL");
     *out = nullptr;
     if (arena_bytes < (1u << 20)) return fail(MHC_E_INVALID, "arena_bytes must be at least 1 MiB");
+    // the arena holds float4 bounds, 8-byte counters and the 16-byte words of the descriptor copy
+    if (reinterpret_cast<uintptr_t>(arena) % kAlign) return fail(MHC_E_INVALID, "arena must be 256-byte aligned");
     int n = 0;
     MHC_CUDA(cudaGetDeviceCount(&n));
     if (device < 0 || device >= n) return fail(MHC_E_INVALID, "device out of range");

@@ -209,3 +209,12 @@ def test_lane_paths_errors(mhc):
         mhc.lane_paths(rep, 0, 0, 0, 10)
     with pytest.raises(mhc.MhcError):
         mhc.lane_paths(flat, 0, 0, 0, -1.0)
+
+
+def test_misaligned_arena_rejected_before_any_device_call(mhc):
+    """A caller's arena must be 256-byte aligned (it holds float4 bounds and the descriptor copy's 16-byte
+    words); a misaligned one is an MHC_E_INVALID, decided before the library touches a device."""
+    h = ctypes.c_void_p()
+    assert mhc.lib.mhc_create(ctypes.byref(h), 0, ctypes.c_void_p(0x10000010), 1 << 20) == -1   # MHC_E_INVALID
+    assert b"256-byte aligned" in mhc.lib.mhc_last_error()
+    assert not h.value
