@@ -12,6 +12,9 @@
  *   - "host" pointers are read during the call only; the library copies what it needs.  "device"
  *     pointers are global-memory pointers of the context's device; they are owned by the caller, must
  *     stay valid until the work enqueued on `stream` has completed, and must not overlap each other.
+ *     Device arrays are aligned to their element size (4 bytes for the FP32 pose planes and int32 outputs,
+ *     8 bytes for int64 and double outputs, 2 bytes for the int16 table); a misaligned one is an
+ *     MHC_E_INVALID.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is enqueued
  *     asynchronously; the caller synchronises.  Calls on one context may use different streams: the
  *     library orders its internal scratch memory between them on the device.

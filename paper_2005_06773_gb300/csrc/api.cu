@@ -533,6 +533,20 @@ int upload(mhc_ctx *ctx, const Layout &L, const std::vector<float> *weights, cha
 
 int check_ctx(mhc_ctx *ctx) { return ctx ? MHC_OK : fail(MHC_E_INVALID, "context is NULL"); }
 
+// The caller's device arrays at their elements' natural alignment (the kernels read and write whole
+// elements; a misaligned one would fault on the device).  Any argument may be NULL (not checked here).
+int check_device_arrays(const mhc_poses *p, const int16_t *table, const mhc_risk *r) {
+    auto bad = [](const void *q, uintptr_t a) { return q && (reinterpret_cast<uintptr_t>(q) % a) != 0; };
+    if (p && (bad(p->x, 4) || bad(p->y, 4) || bad(p->c, 4) || bad(p->s, 4)))
+        return fail(MHC_E_INVALID, "pose planes must be 4-byte aligned");
+    if (bad(table, 2)) return fail(MHC_E_INVALID, "table must be 2-byte aligned");
+    if (r && (bad(r->count, 8) || bad(r->count_k, 8) || bad(r->P, 8) || bad(r->H, 8) || bad(r->naive, 8) ||
+              bad(r->cond, 8) || bad(r->indep, 8) || bad(r->hits, 4) || bad(r->attr_obj, 8) ||
+              bad(r->attr_step, 8) || bad(r->scalars, 8) || bad(r->escape, 4) || bad(r->n_escape, 4)))
+        return fail(MHC_E_INVALID, "risk outputs must be aligned to their element size");
+    return MHC_OK;
+}
+
 // Validated host weights (ones where a pointer is NULL); empty when all uniform.
 int gather_weights(const Layout &L, const float *const *w, std::vector<float> &out) {
     out.clear();
@@ -962,6 +976,7 @@ int mhc_pair_table(const mhc_scenario *scen, int32_t *pair_a, int32_t *pair_b, i
 int mhc_generate_trajectories(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_poses *out, void *stream) {
     if (int r = check_ctx(ctx)) return r;
     if (!out || !out->x || !out->y || !out->c || !out->s) return fail(MHC_E_INVALID, "pose planes must be non-NULL");
+    if (int r = check_device_arrays(out, nullptr, nullptr)) return r;
     Layout L;
     if (int r = build_layout(scen, L)) return r;
     plan_generation(L, ctx->n_sm, ctx->gen_scan);
@@ -982,6 +997,7 @@ int mhc_detect_collisions(mhc_ctx *ctx, const mhc_scenario *scen, const mhc_pose
     if (int r = check_ctx(ctx)) return r;
     if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table)
         return fail(MHC_E_INVALID, "poses and table must be non-NULL");
+    if (int r = check_device_arrays(poses, table, nullptr)) return r;
     Layout L;
     if (int r = build_layout(scen, L)) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1000,6 +1016,7 @@ int mhc_assess_risk(mhc_ctx *ctx, const mhc_scenario *scen, const int16_t *table
                     const mhc_risk *out, void *stream) {
     if (int r = check_ctx(ctx)) return r;
     if (!table || !out) return fail(MHC_E_INVALID, "table and out must be non-NULL");
+    if (int r = check_device_arrays(nullptr, table, out)) return r;
     Layout L;
     if (int r = build_layout(scen, L)) return r;
     std::vector<float> w;
@@ -1036,6 +1053,7 @@ int evaluate_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const floa
     if (int r = check_ctx(ctx)) return r;
     if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table || !out)
         return fail(MHC_E_INVALID, "poses, table and out must be non-NULL");
+    if (int r = check_device_arrays(poses, table, out)) return r;
     Layout L;
     if (int r = build_layout(scen, n_scen, L)) return r;
     plan_generation(L, ctx->n_sm, ctx->gen_scan);
@@ -1058,6 +1076,7 @@ int autotune_impl(mhc_ctx *ctx, const mhc_scenario *scen, int n_scen, const mhc_
     if (int r = check_ctx(ctx)) return r;
     if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table)
         return fail(MHC_E_INVALID, "poses and table must be non-NULL");
+    if (int r = check_device_arrays(poses, table, nullptr)) return r;
     Layout L;
     if (int r = build_layout(scen, n_scen, L)) return r;
     plan_generation(L, ctx->n_sm, ctx->gen_scan);

@@ -271,6 +271,7 @@ int mhc_plan_create(mhc_ctx *ctx, const mhc_scenario *scens, int32_t n_scen, con
     if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table || !out || !scratch)
         return fail(MHC_E_INVALID, "poses, table, out and scratch must be non-NULL");
     if (reinterpret_cast<uintptr_t>(scratch) % kAlign) return fail(MHC_E_INVALID, "scratch must be 256-byte aligned");
+    if (int r = check_device_arrays(poses, table, out)) return r;
     if (flags & ~(MHC_PLAN_GRAPH | MHC_PLAN_PIPELINE)) return fail(MHC_E_INVALID, "unknown plan flags");
     mhc_plan *p = new mhc_plan();
     p->ctx = ctx;

@@ -12,6 +12,7 @@ namespace mhc {
 namespace host {
 
 int fail(int code, const std::string &why);
+int check_device_arrays(const mhc_poses *p, const int16_t *table, const mhc_risk *r);
 // Copies `bytes` with a kernel on `st` between addresses the device can use (device memory or the device
 // address of mapped pinned host memory), both 16-byte aligned.  pdl: launched as a programmatic dependent
 // of the kernel just before it on `st` (the copy waits for that kernel before it reads).

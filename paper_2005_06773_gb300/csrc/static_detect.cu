@@ -80,6 +80,7 @@ extern "C" int mhc_detect_collisions_static(const mhc_scenario *sc, const mhc_po
     if (!sc || !sc->objects) return fail(MHC_E_INVALID, "scenario is NULL");
     if (!poses || !poses->x || !poses->y || !poses->c || !poses->s || !table)
         return fail(MHC_E_INVALID, "poses and table must be non-NULL");
+    if (int r = mhc::host::check_device_arrays(poses, table, nullptr)) return r;
     if (sc->n_objects < 1 || sc->n_objects > kMaxObjects)
         return fail(MHC_E_INVALID, "the allocation-free entry point takes 1 to 64 objects");
     if (sc->n_steps < 1 || sc->n_steps > MHC_MAX_STEPS) return fail(MHC_E_INVALID, "n_steps must be in [1, 32767]");

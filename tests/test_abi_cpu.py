@@ -218,3 +218,27 @@ def test_misaligned_arena_rejected_before_any_device_call(mhc):
     assert mhc.lib.mhc_create(ctypes.byref(h), 0, ctypes.c_void_p(0x10000010), 1 << 20) == -1   # MHC_E_INVALID
     assert b"256-byte aligned" in mhc.lib.mhc_last_error()
     assert not h.value
+
+
+def test_misaligned_device_arrays_rejected_before_any_device_call(mhc):
+    """Caller device arrays at less than their elements' alignment are an MHC_E_INVALID, decided on the
+    host before any launch (the addresses below are never dereferenced)."""
+    cs = mhc.as_c(S.tiny_crossing())
+    fake_ctx = ctypes.c_void_p(0x1000)        # not dereferenced: the argument checks come first
+    good = [0x20000000 + 0x100000 * q for q in range(4)]
+
+    def poses(addrs):
+        return mhc.MhcPoses(*addrs)
+
+    p_bad = poses([good[0], good[1] + 2, good[2], good[3]])
+    assert mhc.lib.mhc_generate_trajectories(fake_ctx, cs.ref, ctypes.byref(p_bad), None) == -1
+    assert b"4-byte aligned" in mhc.lib.mhc_last_error()
+    p_ok = poses(good)
+    assert mhc.lib.mhc_detect_collisions(fake_ctx, cs.ref, ctypes.byref(p_ok), ctypes.c_void_p(0x30000001), None) == -1
+    assert b"2-byte aligned" in mhc.lib.mhc_last_error()
+    assert mhc.lib.mhc_detect_collisions_static(cs.ref, ctypes.byref(p_bad), ctypes.c_void_p(0x30000000), None) == -1
+    assert b"4-byte aligned" in mhc.lib.mhc_last_error()
+    risk = mhc.MhcRisk()
+    risk.P = 0x40000004
+    assert mhc.lib.mhc_assess_risk(fake_ctx, cs.ref, ctypes.c_void_p(0x30000000), None, ctypes.byref(risk), None) == -1
+    assert b"element size" in mhc.lib.mhc_last_error()
